@@ -1,0 +1,302 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these compare the oracle with itself: the references are brute-force
+determinant-space evaluation of the defining matrix elements, exact FCI for
+two electrons, exact rational order conditions, printed values from the paper,
+closed forms and textbook routines.
+"""
+import json
+import os
+from fractions import Fraction as Fr
+
+import numpy as np
+import pytest
+
+from oracle import brute, closed, fci, rk, spectrum, spinorb
+from paper_2205_05175_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _system(o, v, seed=7, offdiag=0.1):
+    f, B, mu = synth.make_system(o, v, seed=seed)
+    f = f + synth.random_symmetric(synth.rng_for(seed + 1), o + v, offdiag)  # f_ov != 0 as under a field
+    return f, B, mu
+
+
+# --- residual equations ------------------------------------------------------------
+
+@pytest.mark.parametrize("o,v", [(1, 3), (2, 2), (2, 3)])
+def test_spin_orbital_residual_matches_brute_force(o, v):
+    """Eq. derivT: Omega_mu = <mu|e^-T H e^T|0> for general complex spin-orbital amplitudes."""
+    f, B, _ = _system(o, v)
+    fso, w = spinorb.spin_orbital_operators(f, spinorb.eri_chemist(B))
+    t1, t2 = synth.random_general_so_amplitudes(2 * o, 2 * v, seed=11, s1=0.1, s2=0.1)
+    bc = brute.BruteCC(fso, w, 2 * o)
+    b1, b2, be = bc.omega(t1, t2)
+    s1, s2, se = spinorb.omega(fso, w, 2 * o, t1, t2)
+    assert np.abs(b1 - s1).max() < 1e-13
+    assert np.abs(b2 - s2).max() < 1e-13
+    assert abs(be - se) < 1e-13
+    assert np.abs(b2).max() > 0.1  # non-trivial values
+
+
+@pytest.mark.parametrize("o,v", [(1, 3), (2, 3), (3, 4)])
+def test_closed_shell_residual_matches_spin_orbital(o, v):
+    """The closed-shell residual is the (a a) / (a b a b) spin block of the spin-orbital one,
+    and the spin-orbital residual of embedded amplitudes is the embedding of it."""
+    f, B, _ = _system(o, v)
+    fso, w = spinorb.spin_orbital_operators(f, spinorb.eri_chemist(B))
+    t1, t2 = synth.random_amplitudes(o, v, seed=11, s1=0.1, s2=0.1)
+    c1, c2, ce = closed.omega(t1, t2, f, closed.Integrals(B, o))
+    s1, s2, se = spinorb.omega(fso, w, 2 * o, *spinorb.embed_amplitudes(t1, t2))
+    e1, e2 = spinorb.embed_amplitudes(c1, c2)
+    assert np.abs(e1 - s1).max() < 1e-13
+    assert np.abs(e2 - s2).max() < 1e-13
+    assert abs(ce - se) < 1e-13
+
+
+@pytest.mark.parametrize("o,v", [(1, 3), (2, 2)])
+def test_lambda_residual_matches_brute_force(o, v):
+    """Eq. derivL: <0|(1+Lambda)[Hbar, tau_mu]|0> by explicit matrices equals the
+    closed-shell R mapped through the multiplier embedding (so the closed-shell
+    Lambda dynamics is the restriction of the spin-orbital one)."""
+    f, B, _ = _system(o, v)
+    fso, w = spinorb.spin_orbital_operators(f, spinorb.eri_chemist(B))
+    t1, t2 = synth.random_amplitudes(o, v, seed=11, s1=0.1, s2=0.1)
+    l1, l2 = synth.random_amplitudes(o, v, seed=12, s1=0.1, s2=0.1)
+    bc = brute.BruteCC(fso, w, 2 * o)
+    R1s, R2s = bc.lambda_residual(*spinorb.embed_amplitudes(t1, t2), *spinorb.embed_multipliers(l1, l2))
+    R1, R2 = closed.lambda_residual(t1, t2, l1, l2, f, closed.Integrals(B, o))
+    Q1, Q2 = spinorb.embed_multipliers(R1, R2)
+    assert np.abs(R1s - Q1).max() < 1e-13
+    assert np.abs(R2s - Q2).max() < 1e-13
+    assert np.abs(R2s).max() > 0.1
+
+
+@pytest.mark.parametrize("o,v", [(1, 3), (2, 2)])
+def test_dipole_matches_brute_force_density(o, v):
+    """Eq. dipole: mu_x = <0|(1+Lambda)e^-T mu_x e^T|0> = Tr(rho mu_x)."""
+    f, B, mu = _system(o, v)
+    fso, w = spinorb.spin_orbital_operators(f, spinorb.eri_chemist(B))
+    t1, t2 = synth.random_amplitudes(o, v, seed=11, s1=0.1, s2=0.1)
+    l1, l2 = synth.random_amplitudes(o, v, seed=12, s1=0.1, s2=0.1)
+    bc = brute.BruteCC(fso, w, 2 * o)
+    ts, ls = spinorb.embed_amplitudes(t1, t2), spinorb.embed_multipliers(l1, l2)
+    rho = bc.density(*ts, *ls)
+    d_b = np.array([np.sum(rho * spinorb.spin_orbital_one_body(mu[x])) for x in range(3)])
+    d_c = closed.dipole(t1, t2, l1, l2, mu, o)
+    assert np.abs(d_b - d_c).max() < 1e-13
+
+
+def test_lambda_is_exact_gradient_five_point():
+    """R(t,l).u equals dL/ds along a pair-symmetric direction u; the five-point
+    stencil is exact for the (at most quartic) Lagrangian."""
+    o, v = 3, 5
+    f, B, _ = _system(o, v)
+    V = closed.Integrals(B, o)
+    t1, t2 = synth.random_amplitudes(o, v, seed=21, s1=0.1, s2=0.1)
+    l1, l2 = synth.random_amplitudes(o, v, seed=22, s1=0.1, s2=0.1)
+    u1, u2 = synth.random_amplitudes(o, v, seed=23, s1=1.0, s2=1.0)
+    R1, R2 = closed.lambda_residual(t1, t2, l1, l2, f, V)
+    L = lambda s: closed.lagrangian(t1 + s * u1, t2 + s * u2, l1, l2, f, V)
+    h = 0.3
+    d = (L(-2 * h) - 8 * L(-h) + 8 * L(h) - L(2 * h)) / (12 * h)
+    assert abs(d - (np.sum(R1 * u1) + np.sum(R2 * u2))) < 1e-12 * max(1.0, abs(d))
+
+
+# --- two-electron exactness, Jacobian, stationarity ---------------------------------
+
+@pytest.fixture(scope="module")
+def two_electron():
+    o, v = 1, 4
+    f, B, mu = synth.make_system(o, v, seed=5)
+    s = rk.RTCC(f, B, mu, o)
+    y0, ec, _ = s.ground_state()
+    F = fci.FCI(f, B, mu, o)
+    e0, psi0, w, _ = F.ground()
+    return s, y0, ec, F, e0, psi0, w
+
+
+def test_two_electron_ground_state_is_fci(two_electron):
+    s, y0, ec, F, e0, psi0, _ = two_electron
+    assert abs(ec - (e0 - F.bc.Eref)) < 1e-11
+    assert np.abs(s.dipole(y0) - F.dipole(psi0)).max() < 1e-11
+
+
+def test_two_electron_dipole_follows_fci_with_h4_error(two_electron):
+    """CCSD is exact for two electrons: RT-CC mu(t) -> FCI mu(t), error ~ h^4 (RK4), Im mu -> 0."""
+    s, y0, _, F, _, psi0, _ = two_electron
+    fld = rk.Field(E0=0.05, omega=0.5, sigma=0.5, t0=1.0)
+    T = 2.0
+    _, mf = F.propagate(psi0, fld, T, 1e-4, 1000)
+    errs = []
+    for h in (0.1, 0.05):
+        _, mm, _, _ = rk.propagate(s, y0, fld, rk.Integrator(method="rk4", h=h, nsteps=int(round(T / h))))
+        errs.append(np.abs(mm[-1] - mf[-1]).max())
+        assert np.abs(mm[-1].imag).max() < 1e-8
+    assert errs[1] < 1e-6
+    assert 10.0 < errs[0] / errs[1] < 25.0
+
+
+def test_jacobian_eigenvalues_are_fci_singlet_excitations(two_electron):
+    s, y0, _, F, e0, _, w = two_electron
+    t1, t2, _, _ = rk.unpack(y0, s.o, s.v)
+    J = fci.jacobian(t1, t2, s.f, s.V)
+    ev = np.sort(np.linalg.eigvals(J).real)
+    exc = np.sort(w - e0)
+    for e in ev:
+        assert np.min(np.abs(exc - e)) < 1e-9
+
+
+def test_zero_field_stationarity_monomer_shape():
+    """At zero field the converged ground state is a fixed point: y(t) = y0, mu(t) = mu0."""
+    o, v = 5, 19
+    f, B, mu = synth.make_system(o, v, seed=synth.SEED_BASE + 0)
+    s = rk.RTCC(f, B, mu, o)
+    y0, _, _ = s.ground_state(tol=1e-12)
+    fld = rk.Field(E0=0.0)
+    _, mm, y, _ = rk.propagate(s, y0, fld, rk.Integrator(method="rk4", h=0.05, nsteps=6))
+    assert np.abs(y - y0).max() < 1e-10
+    assert np.abs(mm - mm[0]).max() < 1e-10
+
+
+# --- integrators -------------------------------------------------------------------
+
+def _fr(s):
+    return Fr(s)
+
+
+def test_cash_karp_printed_coefficients_need_two_sign_fixes():
+    g = json.load(open(os.path.join(GOLDEN, "cash_karp_printed.json")))
+    a = [[_fr(x) for x in row] for row in g["a_printed"]]
+    sums = [sum(row, Fr(0)) for row in a]
+    # printed rows 4 and 6 do not sum to any consistent node; the corrected ones do
+    assert sums[3] == Fr(12, 5) and sums[5] != Fr(7, 8)
+    tab = rk.CK_TABLE
+    for i, row in enumerate(tab["a"]):
+        assert sum(row, Fr(0)) == tab["c"][i]
+    assert [_fr(x) for x in g["b_37_378"]] == tab["b5"]
+    assert [_fr(x) for x in g["b_2825_27648"]] == tab["b4"]
+
+
+def _order_conditions(tab, bkey):
+    """Highest order p such that the quadrature conditions sum b_i c_i^k = 1/(k+1), k < p hold,
+    together with the order-3/4 tree conditions."""
+    b, c, a = tab[bkey], tab["c"], tab["a"]
+    s = len(b)
+    A = [[(a[i][j] if j < len(a[i]) else Fr(0)) for j in range(s)] for i in range(s)]
+    conds = {1: [sum(b, Fr(0)) - 1],
+             2: [sum(b[i] * c[i] for i in range(s)) - Fr(1, 2)],
+             3: [sum(b[i] * c[i] ** 2 for i in range(s)) - Fr(1, 3),
+                 sum(b[i] * A[i][j] * c[j] for i in range(s) for j in range(s)) - Fr(1, 6)],
+             4: [sum(b[i] * c[i] ** 3 for i in range(s)) - Fr(1, 4),
+                 sum(b[i] * c[i] * A[i][j] * c[j] for i in range(s) for j in range(s)) - Fr(1, 8),
+                 sum(b[i] * A[i][j] * c[j] ** 2 for i in range(s) for j in range(s)) - Fr(1, 12),
+                 sum(b[i] * A[i][j] * A[j][k] * c[k] for i in range(s) for j in range(s) for k in range(s)) - Fr(1, 24)],
+             5: [sum(b[i] * c[i] ** 4 for i in range(s)) - Fr(1, 5)]}
+    p = 0
+    for k in range(1, 6):
+        if all(x == 0 for x in conds[k]):
+            p = k
+        else:
+            break
+    return p
+
+
+def test_butcher_orders():
+    assert _order_conditions(rk.RK4_TABLE, "b") == 4
+    assert _order_conditions(rk.CK_TABLE, "b5") == 5   # 37/378: fifth order (paper calls it fourth)
+    assert _order_conditions(rk.CK_TABLE, "b4") == 4
+
+
+def test_rk4_global_error_scales_as_h4_on_linear_ode():
+    lam = -0.3 + 1.7j
+    class Lin(rk.RTCC):
+        def __init__(self):
+            pass
+        def rhs(self, tt, y, fld):
+            return lam * y
+    s = Lin()
+    errs = []
+    for h in (0.1, 0.05):
+        y = np.array([1.0 + 0j])
+        for n in range(int(round(2.0 / h))):
+            y = s.rk4_step(n * h, y, h, None)
+        errs.append(abs(y[0] - np.exp(lam * 2.0)))
+    assert 14.0 < errs[0] / errs[1] < 17.0
+
+
+def test_ck_local_error_orders_on_linear_ode():
+    lam = -0.3 + 1.7j
+    class Lin(rk.RTCC):
+        def __init__(self):
+            pass
+        def rhs(self, tt, y, fld):
+            return lam * y
+    s = Lin()
+    e5, e4 = [], []
+    tab = rk.as_float(rk.CK_TABLE)
+    for h in (0.2, 0.1):
+        ks = s.stages(tab, 0.0, np.array([1.0 + 0j]), h, None)
+        y5 = 1 + h * sum(b * k for b, k in zip(tab["b5"], ks))
+        y4 = 1 + h * sum(b * k for b, k in zip(tab["b4"], ks))
+        ex = np.exp(lam * h)
+        e5.append(abs(y5[0] - ex))
+        e4.append(abs(y4[0] - ex))
+    assert 50 < e5[0] / e5[1] < 80     # h^6 local error
+    assert 25 < e4[0] / e4[1] < 40     # h^5 local error
+
+
+def test_ck_controller_formula():
+    acc, hn = rk.ck_controller(0.01, 1e-7, 1e-6)
+    assert acc and abs(hn - 0.01 * 0.84 * 10 ** 0.2) < 1e-15
+    acc, hn = rk.ck_controller(0.01, 1e-5, 1e-6)
+    assert (not acc) and abs(hn - 0.01 * 0.84 * 0.1 ** 0.25) < 1e-15
+    assert rk.ck_controller(0.01, 0.0, 1e-6) == (True, 0.05)
+    assert rk.ck_controller(0.01, 1.0, 1e-6)[1] == pytest.approx(0.002)
+
+
+def test_field_matches_printed_values():
+    g = json.load(open(os.path.join(GOLDEN, "field_envelope.json")))
+    fld = rk.Field(E0=g["E0"], omega=0.0, sigma=g["sigma"], t0=g["t0"], carrier="cos", sign=-1.0)
+    for p in g["points"]:
+        val = abs(fld.amplitude(p["t"]))
+        if p.get("order_of_magnitude"):
+            assert 1e-11 < val < 1e-9
+        else:
+            assert abs(val - p["abs_E"]) / p["abs_E"] < p["rel_tol"]
+    assert fld.amplitude(g["t0"]) == -g["E0"]
+
+
+# --- spectrum post-processing ------------------------------------------------------
+
+def test_spline_reproduces_cubic_with_natural_ends_and_line():
+    x = np.sort(np.random.default_rng(0).uniform(0, 3, 12))
+    x[0], x[-1] = 0.0, 3.0
+    xn = np.linspace(0, 3, 50)
+    lin = 0.3 - 1.2 * x
+    assert np.abs(spectrum.natural_cubic_spline(x, lin, xn) - (0.3 - 1.2 * xn)).max() < 1e-12
+    yv = np.sin(x)
+    assert np.abs(spectrum.natural_cubic_spline(x, yv, x) - yv).max() < 1e-14
+
+
+def test_delta_pulse_spectrum_peaks_at_oscillation_frequencies():
+    dt = 0.05
+    t = dt * np.arange(4000)
+    w1, w2 = 0.7, 1.3
+    mu = np.zeros((len(t), 3))
+    mu[:, 2] = 0.4 * np.sin(w1 * t) + 0.2 * np.sin(w2 * t)
+    om = np.linspace(0.2, 2.0, 3601)
+    I = spectrum.spectrum(t, mu, om, (0, 0, 1), kappa=1.0, gamma=0.01)
+    peaks = [om[k] for k in range(1, len(om) - 1) if I[k] > I[k - 1] and I[k] > I[k + 1] and I[k] > 0.2 * I.max()]
+    assert len(peaks) == 2
+    assert abs(peaks[0] - w1) < 2e-3 and abs(peaks[1] - w2) < 2e-3
+
+
+def test_matrix_pencil_recovers_frequencies():
+    dt = 0.1
+    k = np.arange(400)
+    y = 0.3 * np.exp(-1j * 0.81 * k * dt) + 0.1 * np.exp(-1j * 1.37 * k * dt) + 0.05 * np.exp(1j * 0.81 * k * dt)
+    w = np.sort(spectrum.matrix_pencil(y, dt, 3).real)
+    assert np.allclose(w, [-0.81, 0.81, 1.37], atol=1e-9)
