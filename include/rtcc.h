@@ -1,0 +1,194 @@
+/*
+ * rtcc.h — C-ABI of the GB300 (sm_103a) real-time CCSD propagation library.
+ *
+ * The library evaluates the closed-shell RT-CCSD equations of motion
+ *     i dt_mu/dt      = <mu| e^{-T} H(t) e^{T} |0>            (Sec. 2, Eq. derivT)
+ *    -i dlambda_mu/dt = <0|(1+Lambda)[Hbar(t), tau_mu]|0>      (Sec. 2, Eq. derivL)
+ * with H(t) = H0 - mu.E(t) in frozen molecular orbitals (Sec. 2.2), propagates them
+ * with explicit Runge-Kutta integrators (Sec. 2.1 Eqs. rk_y/rk_k; Sec. 4.2 RK4,
+ * Cash-Karp Eqs. ck-k/ck-y/ck-h-final, mixed-step RK4) and records the dipole
+ * mu_x(t) = <0|(1+Lambda) e^{-T} mu_x e^{T}|0> (Sec. 2.2, Eq. dipole).
+ *
+ * Conventions shared by every call
+ *  - Orbitals are ordered occupied (o) then virtual (v); nmo = o + v.
+ *  - Matrices are row-major float64.  Complex numbers are interleaved (re, im) float64.
+ *  - One "state" of a trajectory is the complex vector
+ *        y = [ t1[o][v] | t2[o][o][v][v] | l1[o][v] | l2[o][o][v][v] ]
+ *    of length rtcc_state_size(); t2 and l2 obey x[i][j][a][b] == x[j][i][b][a].
+ *    t2[i][j][a][b] is the (i alpha, j beta -> a alpha, b beta) amplitude; the
+ *    multipliers l are paired with the residual by a plain (unconjugated) dot product.
+ *  - A handle holds ntraj independent trajectories that share one integral set and
+ *    are stacked into the same GEMMs.
+ *  - Ownership: the caller owns every buffer it passes.  The library copies inputs on
+ *    entry and keeps no caller pointer after a call returns.  Output buffers are
+ *    caller-allocated.  Pointers documented "host or device" may be either; the
+ *    library inspects them with cudaPointerGetAttributes.
+ *  - A handle is bound to the CUDA device that was current at rtcc_create and to a
+ *    stream owned by the library; it is not thread-safe.  Every call is synchronous
+ *    with respect to the host unless stated otherwise.
+ *  - Errors: every call returns an rtcc_status_t; rtcc_last_error() returns a
+ *    thread-local message describing the most recent failure.  No call aborts the
+ *    process.  There is no CPU fallback: without a usable sm_103a GPU, rtcc_create
+ *    returns RTCC_ERR_CUDA.
+ */
+#ifndef RTCC_H
+#define RTCC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RTCC_OK = 0,
+    RTCC_ERR_INVALID_ARG = 1,   /* bad size, null pointer, asymmetric input, unknown enum */
+    RTCC_ERR_OOM = 2,           /* device allocation failed */
+    RTCC_ERR_CUDA = 3,          /* CUDA runtime/driver error (no device, launch failure) */
+    RTCC_ERR_NOCONV = 4,        /* ground-state iterations did not converge */
+    RTCC_ERR_DIVERGED = 5,      /* NaN/Inf or norm blow-up in a propagated state */
+    RTCC_ERR_STEP_UNDERFLOW = 6,/* Cash-Karp step fell below h_min or too many rejects */
+    RTCC_ERR_TIMEOUT = 7,       /* a bounded device-side wait expired (kernel returned early) */
+    RTCC_ERR_UNSUPPORTED = 8    /* option not available in this build */
+} rtcc_status_t;
+
+/* Arithmetic of the residual contractions.  The propagated state, the RK
+ * combinations, the error estimate, the controller and the dipole reduction are
+ * float64 in every mode (Sec. 4.1 studies single vs double precision). */
+typedef enum {
+    RTCC_P64 = 0,         /* float64 contractions (SIMT DFMA) */
+    RTCC_P32_TF32 = 1,    /* one TF32 tcgen05 pass, float32 accumulate */
+    RTCC_P32_3XTF32 = 2,  /* split hi/lo TF32 (3 passes), float32 accumulate */
+    RTCC_P32_BF16X3 = 3   /* split hi/lo BF16 (3 passes), float32 accumulate */
+} rtcc_precision_t;
+
+typedef enum { RTCC_CARRIER_SIN = 0, RTCC_CARRIER_COS = 1 } rtcc_carrier_t;
+
+/* Gaussian-envelope pulse (Sec. 3, Eq. field):
+ *   E(t) = sign * E0 * exp(-(t-t0)^2/(2 sigma^2)) * carrier(omega (t-t0)) * pol
+ * The paper's form is carrier = cos, sign = -1; pol = (1,1,1)/sqrt(3) is Eq. iso-field. */
+typedef struct {
+    double E0, omega, sigma, t0;
+    double pol[3];
+    int carrier;    /* rtcc_carrier_t */
+    double sign;    /* +1 or -1 */
+} rtcc_field_t;
+
+typedef enum { RTCC_RK4 = 0, RTCC_CK = 1, RTCC_MIXED_RK4 = 2 } rtcc_method_t;
+
+/* Integrator settings (Sec. 2.1, Sec. 4.2).
+ *   RK4:        fixed step h.
+ *   CK:         Cash-Karp with the 37/378 (fifth-order) solution propagated, error
+ *               Delta = max |y5 - y4| over all complex components, accept if Delta <= tol,
+ *               h_new = safety*h*(tol/Delta)^(1/5) (accept) or ^(1/4) (reject, repeat),
+ *               clamped to [0.2h, 5h] and [h_min, h_max]; h is the first trial step.
+ *   MIXED_RK4:  RK4 with h1 while t < t_switch (the crossing step is cut to land on
+ *               t_switch), h2 afterwards.
+ * Stop after nsteps accepted steps if nsteps > 0, else at t_end (last step cut to land). */
+typedef struct {
+    int method;        /* rtcc_method_t */
+    double h, h1, h2, t_switch;
+    double tol, safety, h_min, h_max;
+    int max_rejects;
+    int nsteps;
+    double t_end;
+} rtcc_integrator_t;
+
+typedef struct rtcc_ctx* rtcc_handle_t;
+
+/* Create a handle (Sec. 3; Sec. 4.3 integral residency).
+ *  f   : host, nmo*nmo float64, symmetric field-free Fock matrix.
+ *  B   : host, naux*nmo*nmo float64, density-fitting factors symmetric in the last two
+ *        indices; the library forms (pq|rs) = sum_P B[P][p][q] B[P][r][s] on the device
+ *        for every block the residual needs and keeps them resident.
+ *  mu  : host, 3*nmo*nmo float64, symmetric dipole matrices (x, y, z).
+ *  o,v : occupied / virtual counts (o >= 1, v >= 1).   ntraj: trajectories (>= 1).
+ *  prec: rtcc_precision_t of the contractions.
+ *  out : receives the handle.  All trajectories start at y = 0 (no ground state) and time 0.
+ * Errors: INVALID_ARG (sizes, null, asymmetric f/B/mu), OOM, CUDA. */
+rtcc_status_t rtcc_create(const double* f, const double* B, int naux, const double* mu,
+                          int o, int v, int ntraj, int prec, rtcc_handle_t* out);
+
+/* Free every device resource of the handle.  Null is accepted. */
+rtcc_status_t rtcc_destroy(rtcc_handle_t h);
+
+/* Number of complex elements of one trajectory's state y (2*o*v + 2*o*o*v*v). */
+rtcc_status_t rtcc_state_size(rtcc_handle_t h, size_t* n);
+
+/* Field-free ground state (Sec. 2.1: y0 is the ground-state T and Lambda solution),
+ * float64 on the device whatever the handle's precision: Jacobi updates with
+ * orbital-energy denominators plus DIIS until max|Omega| and max|R| < tol.
+ * Every trajectory is set to the result at time 0.  e_corr (host, may be null)
+ * receives the correlation energy, mu0 (host, 3 doubles, may be null) the real dipole.
+ * Errors: NOCONV after maxiter iterations, CUDA. */
+rtcc_status_t rtcc_ground_state(rtcc_handle_t h, double tol, int maxiter,
+                                double* e_corr, double* mu0);
+
+/* Copy one trajectory's state, time and current step size out of / into the handle.
+ * y: host or device, rtcc_state_size() complex numbers.  time/hstep may be null (get)
+ * or are applied (set).  traj in [0, ntraj).  Used for checkpoint/resume and tests. */
+rtcc_status_t rtcc_get_state(rtcc_handle_t h, int traj, double* y, double* time, double* hstep);
+rtcc_status_t rtcc_set_state(rtcc_handle_t h, int traj, const double* y, double time, double hstep);
+
+/* One evaluation of the right-hand side of Eq. IVP for every trajectory:
+ *   dt/dt = -i Omega(t; f(t)),  dl/dt = +i R(t, l; f(t))   with f(t) = f - E(t_z).mu
+ * y    : host or device, ntraj * state_size complex (trajectory-major).
+ * fields, times: host, ntraj entries (field of trajectory z evaluated at times[z]).
+ * dydt : host or device, ntraj * state_size complex (output).
+ * This is exactly the function every Runge-Kutta stage calls (Eqs. derivT/derivL). */
+rtcc_status_t rtcc_rhs(rtcc_handle_t h, const double* y, const rtcc_field_t* fields,
+                       const double* times, double* dydt);
+
+/* Dipole of every trajectory's current state (Eq. dipole): mu_out host or device,
+ * ntraj*3 complex. */
+rtcc_status_t rtcc_dipole(rtcc_handle_t h, double* mu_out);
+
+/* Propagate every trajectory from its current state and time (Sec. 2.1, Sec. 4.2).
+ * fields : host, ntraj pulses.   integ: host, shared integrator settings.
+ * max_out: samples per trajectory the output arrays hold (>= 1).
+ * t_out  : host or device, ntraj*max_out float64 times (sample 0 = start time).
+ * mu_out : host or device, ntraj*max_out*3 complex dipoles (re, im).
+ * n_out  : host, ntraj ints: samples written per trajectory.
+ * Each trajectory carries its own step size (Cash-Karp) and time; all trajectories
+ * share every GEMM.  Sampling stops silently when max_out is reached; propagation
+ * continues to the end.  Errors: DIVERGED, STEP_UNDERFLOW, TIMEOUT, CUDA. */
+rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields,
+                             const rtcc_integrator_t* integ, int max_out,
+                             double* t_out, double* mu_out, int* n_out);
+
+/* Counters of the last rtcc_propagate: accepted steps, rejected attempts and
+ * right-hand-side evaluations summed over trajectories (host, may be null). */
+rtcc_status_t rtcc_last_stats(rtcc_handle_t h, long long* accepted, long long* rejected,
+                              long long* rhs_evals);
+
+/* Absorption spectrum (Sec. 2.2: I(w) = Im Tr alpha(w); Sec. 4.2: non-uniform samples
+ * are interpolated onto a uniform grid).  Runs on the current CUDA device.
+ *  t      : host, n sample times (increasing; need not be uniform).
+ *  mu     : host, n*3 float64 real parts of the dipole.
+ *  field  : host; the scalar pulse amplitude E(t) of this field is transformed and
+ *           divided out, unless kappa > 0 (delta pulse: alpha = mu(w)/kappa).
+ *  gamma  : exponential damping exp(-gamma (t - t_0)) applied to mu(t) - mu(t_0).
+ *  dt     : uniform grid spacing for the interpolation (<= 0: smallest sample spacing).
+ *  omega  : host, n_omega frequencies;  I : host, n_omega outputs
+ *           I(w) = Im[ (pol . D(w)) / E(w) ],  D(w) = dt sum_k d(t_k) exp(i w t_k).
+ * Errors: INVALID_ARG, CUDA. */
+rtcc_status_t rtcc_spectrum(const double* t, const double* mu, int n, const rtcc_field_t* field,
+                            double kappa, double gamma, double dt, const double* omega,
+                            int n_omega, double* I);
+
+/* Thread-local description of the most recent error (never null). */
+const char* rtcc_last_error(void);
+
+/* Library self-test of the contraction core (not part of the method): computes
+ * C[b][m][n] = sum_k A[b][m][k] * Bm[b][n][k] for float64 host or device inputs with
+ * the handle-independent GEMM path of precision `prec` (TF32/3xTF32/BF16x3 run on
+ * the tcgen05 tensor cores, P64 on the float64 path).  C is float64 host or device.
+ * Errors: INVALID_ARG, CUDA, TIMEOUT. */
+rtcc_status_t rtcc_selftest_gemm(int prec, int batch, int M, int N, int K, const double* A,
+                                 const double* Bm, double* C);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTCC_H */

@@ -1,0 +1,525 @@
+// Contraction engine: planning and execution of einsum programs (see engine.cuh).
+#include "engine.cuh"
+#include <algorithm>
+#include <set>
+
+namespace rtcc {
+
+void launch_reduce(const DirectDesc& d, long long splits, cudaStream_t s);
+
+namespace {
+
+enum CompKind : int { CK_ADD = 0, CK_DIRECT = 1, CK_REDUCE = 2, CK_GEMM = 3 };
+
+constexpr long long kDirectMaxWork = 1ll << 21;   // real multiply-adds below which a term runs direct
+constexpr long long kReduceMaxOut = 2048;         // outputs up to which a long-K term is split-K reduced
+
+IndexMap map_for(const Tensor& t, const std::string& tl, const std::string& labs) {
+  IndexMap m{};
+  RTCC_REQUIRE((int)labs.size() <= kMaxLab, "too many labels in one index group of " + t.name);
+  m.n = (int)labs.size();
+  for (int i = 0; i < m.n; ++i) {
+    const size_t p = tl.find(labs[i]);
+    RTCC_REQUIRE(p != std::string::npos, "label missing in " + t.name);
+    m.dims[i] = t.dims[p];
+    m.strides[i] = t.strides[p];
+  }
+  return m;
+}
+
+long long prod_dims(const IndexMap& m) {
+  long long s = 1;
+  for (int i = 0; i < m.n; ++i) s *= m.dims[i];
+  return s;
+}
+
+long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+struct Compiled {
+  int kind = CK_ADD;
+  AddDesc add{};
+  DirectDesc dir{};
+  long long splits = 1;
+  // GEMM path
+  PackDesc pa{}, pb{};
+  bool a_const = false, b_const = false;
+  void* a_pre = nullptr;
+  void* b_pre = nullptr;
+  size_t a_bytes = 0, b_bytes = 0, c_bytes = 0;
+  UnpackDesc up{};
+  long long GM = 0, GN = 0, Kpad = 0, NB = 0;
+  int tc_kind = -1;   // -1: float64 SIMT GEMM, 0: tf32, 1: bf16
+  TcGemmPlan tcp{};
+  long long alg_flops = 0;    // useful real flops (one pass)
+  long long exec_flops = 0;   // flops issued by the GEMM kernel (passes and padding included)
+};
+
+void* dev_alloc(size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error(2, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  return p;
+}
+
+Engine::Engine(Prec p, cudaStream_t s) : prec_(p), stream_(s) {
+  dev_err_ = static_cast<int*>(dev_alloc(sizeof(int) * 4));
+  allocs_.push_back(dev_err_);
+  RTCC_CUDA(cudaMemsetAsync(dev_err_, 0, sizeof(int) * 4, stream_));
+}
+
+Engine::~Engine() {
+  for (void* p : allocs_) cudaFree(p);
+}
+
+static std::vector<long long> contiguous_strides(const std::vector<int>& dims) {
+  std::vector<long long> s(dims.size());
+  long long acc = 1;
+  for (int i = (int)dims.size() - 1; i >= 0; --i) {
+    s[i] = acc;
+    acc *= dims[i];
+  }
+  return s;
+}
+
+int Engine::external(const std::string& name, const std::vector<int>& dims, bool cplx, double* ptr,
+                     std::vector<long long> strides, bool constant) {
+  Tensor t;
+  t.name = name;
+  t.dims = dims;
+  t.strides = strides.empty() ? contiguous_strides(dims) : strides;
+  RTCC_REQUIRE(t.strides.size() == dims.size(), "stride rank mismatch for " + name);
+  t.cplx = cplx;
+  t.constant = constant;
+  t.storage = ST_EXTERNAL;
+  t.ptr = ptr;
+  tensors_.push_back(t);
+  return (int)tensors_.size() - 1;
+}
+
+int Engine::owned(const std::string& name, const std::vector<int>& dims, bool cplx, bool constant) {
+  Tensor t;
+  t.name = name;
+  t.dims = dims;
+  t.strides = contiguous_strides(dims);
+  t.cplx = cplx;
+  t.constant = constant;
+  t.storage = ST_OWNED;
+  const size_t bytes = (size_t)t.numel() * (cplx ? 16 : 8);
+  t.ptr = static_cast<double*>(dev_alloc(bytes));
+  allocs_.push_back(t.ptr);
+  bytes_ += bytes;
+  RTCC_CUDA(cudaMemsetAsync(t.ptr, 0, bytes, stream_));
+  tensors_.push_back(t);
+  return (int)tensors_.size() - 1;
+}
+
+int Engine::new_arena() {
+  arena_size_.push_back(0);
+  arena_hwm_.push_back(0);
+  arena_ptr_.push_back(nullptr);
+  return (int)arena_size_.size() - 1;
+}
+
+int Engine::temp(int arena, const std::string& name, const std::vector<int>& dims, bool cplx) {
+  RTCC_REQUIRE(!finalized_, "engine already finalized");
+  Tensor t;
+  t.name = name;
+  t.dims = dims;
+  t.strides = contiguous_strides(dims);
+  t.cplx = cplx;
+  t.storage = ST_ARENA;
+  t.arena = arena;
+  t.arena_off = arena_size_[arena];
+  const long long nd = t.numel() * (cplx ? 2 : 1);
+  arena_size_[arena] += round_up(nd, 32);   // 256-byte alignment of every temporary
+  tensors_.push_back(t);
+  return (int)tensors_.size() - 1;
+}
+
+void Engine::ein(Program& P, int c, const std::string& lc, int a, const std::string& la, int b,
+                 const std::string& lb, cplx alpha) {
+  P.ops.push_back(Op{OP_EIN, c, a, b, lc, la, lb, alpha});
+}
+
+void Engine::add(Program& P, int c, const std::string& lc, int a, const std::string& la, cplx alpha) {
+  P.ops.push_back(Op{OP_ADD, c, a, -1, lc, la, "", alpha});
+}
+
+Program Engine::reverse(const Program& fwd, const std::vector<int>& active_inputs, int arena,
+                        std::map<int, int>& adj) {
+  std::set<int> active(active_inputs.begin(), active_inputs.end());
+  for (const Op& op : fwd.ops) {
+    const bool act = (op.kind == OP_EIN) ? (active.count(op.a) || active.count(op.b)) : active.count(op.a) > 0;
+    if (act) active.insert(op.c);
+  }
+  auto adj_of = [&](int id) {
+    auto it = adj.find(id);
+    if (it != adj.end()) return it->second;
+    const Tensor& t = tensors_[id];
+    const int d = temp(arena, "d_" + t.name, t.dims, true);
+    adj[id] = d;
+    return d;
+  };
+  for (int id : active) adj_of(id);
+  Program R;
+  R.name = fwd.name + "_vjp";
+  R.zero_arenas = {arena};
+  for (auto it = fwd.ops.rbegin(); it != fwd.ops.rend(); ++it) {
+    const Op& op = *it;
+    if (!active.count(op.c)) continue;
+    const int dc = adj.at(op.c);
+    if (op.kind == OP_EIN) {
+      if (active.count(op.a)) ein(R, adj.at(op.a), op.la, dc, op.lc, op.b, op.lb, op.alpha);
+      if (active.count(op.b)) ein(R, adj.at(op.b), op.lb, op.a, op.la, dc, op.lc, op.alpha);
+    } else if (active.count(op.a)) {
+      RTCC_REQUIRE(op.la.size() == op.lc.size(), "reverse of a broadcasting add of an active tensor");
+      add(R, adj.at(op.a), op.la, dc, op.lc, op.alpha);
+    }
+  }
+  return R;
+}
+
+void Engine::plan(Program& P) {
+  P.comp.clear();
+  for (const Op& op : P.ops) {
+    auto cp = std::make_shared<Compiled>();
+    Compiled& k = *cp;
+    const Tensor& C = tensors_[op.c];
+    const Tensor& A = tensors_[op.a];
+    RTCC_REQUIRE(op.lc.size() == C.dims.size(), "label/rank mismatch for output " + C.name + " in " + P.name);
+    RTCC_REQUIRE(op.la.size() == A.dims.size(), "label/rank mismatch for " + A.name + " in " + P.name);
+    RTCC_REQUIRE(C.cplx || (!A.cplx && (op.kind == OP_ADD || !tensors_[op.b].cplx)),
+                 "complex result into real tensor " + C.name);
+    RTCC_REQUIRE(!C.constant || P.name == "setup", "write to constant tensor " + C.name);
+    if (op.kind == OP_ADD) {
+      k.kind = CK_ADD;
+      AddDesc& d = k.add;
+      d.A = A.ptr;
+      d.C = C.ptr;
+      d.a_cplx = A.cplx;
+      d.c_cplx = C.cplx;
+      d.c_all = map_for(C, op.lc, op.lc);
+      d.a_all = d.c_all;
+      for (int i = 0; i < d.c_all.n; ++i) {
+        const size_t p = op.la.find(op.lc[i]);
+        if (p == std::string::npos) d.a_all.strides[i] = 0;
+        else {
+          RTCC_REQUIRE(A.dims[p] == C.dims[i], "extent mismatch in add " + A.name + " -> " + C.name);
+          d.a_all.strides[i] = A.strides[p];
+        }
+      }
+      for (char l : op.la) RTCC_REQUIRE(op.lc.find(l) != std::string::npos, "add reduces a label: " + A.name);
+      d.n = prod_dims(d.c_all);
+      d.ar = op.alpha.real();
+      d.ai = op.alpha.imag();
+      P.comp.push_back(cp);
+      continue;
+    }
+    const Tensor& B = tensors_[op.b];
+    RTCC_REQUIRE(op.lb.size() == B.dims.size(), "label/rank mismatch for " + B.name + " in " + P.name);
+    std::string Lb, Lm, Ln, Lk;
+    for (char l : op.lc) {
+      const bool ina = op.la.find(l) != std::string::npos, inb = op.lb.find(l) != std::string::npos;
+      RTCC_REQUIRE(ina || inb, std::string("output label only in output: ") + l + " in " + P.name);
+      if (ina && inb) Lb += l;
+      else if (ina) Lm += l;
+      else Ln += l;
+    }
+    for (char l : op.la)
+      if (op.lc.find(l) == std::string::npos) {
+        RTCC_REQUIRE(op.lb.find(l) != std::string::npos, std::string("dangling label ") + l + " in " + P.name);
+        Lk += l;
+      }
+    for (char l : op.lb)
+      if (op.lc.find(l) == std::string::npos)
+        RTCC_REQUIRE(op.la.find(l) != std::string::npos, std::string("dangling label ") + l + " in " + P.name);
+    // extent consistency
+    auto ext = [&](const Tensor& t, const std::string& tl, char l) { return t.dims[tl.find(l)]; };
+    for (char l : op.lc) {
+      if (op.la.find(l) != std::string::npos)
+        RTCC_REQUIRE(ext(A, op.la, l) == ext(C, op.lc, l), "extent mismatch " + A.name + "/" + C.name);
+      if (op.lb.find(l) != std::string::npos)
+        RTCC_REQUIRE(ext(B, op.lb, l) == ext(C, op.lc, l), "extent mismatch " + B.name + "/" + C.name);
+    }
+    for (char l : Lk) RTCC_REQUIRE(ext(A, op.la, l) == ext(B, op.lb, l), "K extent mismatch " + A.name + "/" + B.name);
+
+    const long long NB = prod_dims(map_for(C, op.lc, Lb));
+    const long long M = prod_dims(map_for(C, op.lc, Lm));
+    const long long N = prod_dims(map_for(C, op.lc, Ln));
+    const long long K = prod_dims(map_for(A, op.la, Lk));
+    const int cfac = (A.cplx && B.cplx) ? 4 : ((A.cplx || B.cplx) ? 2 : 1);
+    const long long work = NB * M * N * K * cfac;
+    k.alg_flops = 2 * work;
+
+    DirectDesc& d = k.dir;
+    d.A = A.ptr;
+    d.B = B.ptr;
+    d.C = C.ptr;
+    d.a_cplx = A.cplx;
+    d.b_cplx = B.cplx;
+    d.c_cplx = C.cplx;
+    d.am = map_for(A, op.la, Lm);
+    d.ak = map_for(A, op.la, Lk);
+    d.ab = map_for(A, op.la, Lb);
+    d.bn = map_for(B, op.lb, Ln);
+    d.bk = map_for(B, op.lb, Lk);
+    d.bb = map_for(B, op.lb, Lb);
+    d.cm = map_for(C, op.lc, Lm);
+    d.cn = map_for(C, op.lc, Ln);
+    d.cb = map_for(C, op.lc, Lb);
+    d.M = M;
+    d.N = N;
+    d.K = K;
+    d.NB = NB;
+    d.ar = op.alpha.real();
+    d.ai = op.alpha.imag();
+
+    const long long nout = NB * M * N;
+    if (Lk.empty()) {
+      k.kind = CK_DIRECT;
+    } else if (force_gemm_) {
+      k.kind = CK_GEMM;
+    } else if (nout <= kReduceMaxOut && K >= 256) {
+      k.kind = CK_REDUCE;
+      long long want = std::max(1ll, (152ll * 8) / std::max(1ll, nout));
+      k.splits = std::max(1ll, std::min(want, (K + 1023) / 1024));
+    } else if (work < kDirectMaxWork) {
+      k.kind = CK_DIRECT;
+    } else {
+      k.kind = CK_GEMM;
+    }
+    if (k.kind == CK_GEMM) {
+      const int nss = (prec_ == Prec::TF32X3 || prec_ == Prec::BF16X3) ? 3 : 1;
+      const int elem = (prec_ == Prec::P64) ? PE_F64 : (prec_ == Prec::BF16X3 ? PE_BF16 : PE_F32);
+      const int esz = (elem == PE_F64) ? 8 : (elem == PE_F32 ? 4 : 2);
+      k.tc_kind = (prec_ == Prec::P64) ? -1 : (prec_ == Prec::BF16X3 ? 1 : 0);
+      const long long kblk = (k.tc_kind < 0) ? 16 : tc_kblock_elems(k.tc_kind);
+      PackDesc& pa = k.pa;
+      PackDesc& pb = k.pb;
+      pa = PackDesc{};
+      pb = PackDesc{};
+      pa.src = A.ptr;
+      pa.src_cplx = A.cplx;
+      pa.rows = d.am;
+      pa.cols = d.ak;
+      pa.bat = d.ab;
+      pa.R = M;
+      pa.K = K;
+      pa.NB = NB;
+      pb.src = B.ptr;
+      pb.src_cplx = B.cplx;
+      pb.rows = d.bn;
+      pb.cols = d.bk;
+      pb.bat = d.bb;
+      pb.R = N;
+      pb.K = K;
+      pb.NB = NB;
+      int mode = OM_REAL;
+      auto set1 = [](PackDesc& p, int nrb, int ncs) {
+        p.nrb = nrb;
+        p.ncs = ncs;
+        for (int r = 0; r < 2; ++r)
+          for (int c = 0; c < 2; ++c) {
+            p.comp[r][c] = 0;
+            p.sign[r][c] = 1;
+          }
+      };
+      if (!A.cplx && !B.cplx) {
+        set1(pa, 1, 1);
+        set1(pb, 1, 1);
+      } else if (A.cplx && !B.cplx) {
+        set1(pa, 2, 1);
+        pa.comp[1][0] = 1;
+        set1(pb, 1, 1);
+        mode = OM_STACK_M;
+      } else if (!A.cplx && B.cplx) {
+        set1(pa, 1, 1);
+        set1(pb, 2, 1);
+        pb.comp[1][0] = 1;
+        mode = OM_STACK_N;
+      } else {
+        PackDesc& ex = (M <= N) ? pa : pb;   // 2x2 real embedding on the side with fewer rows
+        PackDesc& pl = (M <= N) ? pb : pa;
+        set1(ex, 2, 2);
+        ex.comp[0][0] = 0; ex.sign[0][0] = 1;
+        ex.comp[0][1] = 1; ex.sign[0][1] = -1;
+        ex.comp[1][0] = 1; ex.sign[1][0] = 1;
+        ex.comp[1][1] = 0; ex.sign[1][1] = 1;
+        set1(pl, 1, 2);
+        pl.comp[0][1] = 1;
+        mode = (M <= N) ? OM_STACK_M : OM_STACK_N;
+      }
+      pa.nss = pb.nss = nss;
+      if (nss == 1) {
+        pa.part[0] = pb.part[0] = SP_FULL;
+      } else {
+        pa.part[0] = SP_HI; pa.part[1] = SP_HI; pa.part[2] = SP_LO;
+        pb.part[0] = SP_HI; pb.part[1] = SP_LO; pb.part[2] = SP_HI;
+      }
+      const long long Kp = round_up((long long)nss * pa.ncs * K, kblk);
+      pa.Kpad = pb.Kpad = Kp;
+      pa.elem = pb.elem = elem;
+      pa.round_tf32 = pb.round_tf32 = 1;
+      k.GM = (long long)pa.nrb * M;
+      k.GN = (long long)pb.nrb * N;
+      k.Kpad = Kp;
+      k.NB = NB;
+      k.a_const = A.constant;
+      k.b_const = B.constant;
+      k.a_bytes = (size_t)(NB * k.GM * Kp * esz);
+      k.b_bytes = (size_t)(NB * k.GN * Kp * esz);
+      k.c_bytes = (size_t)(NB * k.GM * k.GN * (k.tc_kind < 0 ? 8 : 4));
+      k.exec_flops = 2 * NB * k.GM * k.GN * Kp;
+      UnpackDesc& u = k.up;
+      u.gout_f64 = (k.tc_kind < 0);
+      u.ldg = k.GN;
+      u.rows_g = k.GM;
+      u.mode = mode;
+      u.M = M;
+      u.N = N;
+      u.NB = NB;
+      u.cm = d.cm;
+      u.cn = d.cn;
+      u.cb = d.cb;
+      u.C = C.ptr;
+      u.c_cplx = C.cplx;
+      u.ar = d.ar;
+      u.ai = d.ai;
+      if (!k.a_const) wsA_bytes_ = std::max(wsA_bytes_, k.a_bytes);
+      if (!k.b_const) wsB_bytes_ = std::max(wsB_bytes_, k.b_bytes);
+      wsC_bytes_ = std::max(wsC_bytes_, k.c_bytes);
+    }
+    P.comp.push_back(cp);
+  }
+}
+
+void Engine::bind(Program& P) {
+  for (size_t i = 0; i < P.ops.size(); ++i) {
+    const Op& op = P.ops[i];
+    Compiled& k = *P.comp[i];
+    // pointers of arena tensors are known only now
+    const Tensor& C = tensors_[op.c];
+    const Tensor& A = tensors_[op.a];
+    if (k.kind == CK_ADD) {
+      k.add.A = A.ptr;
+      k.add.C = C.ptr;
+      continue;
+    }
+    const Tensor& B = tensors_[op.b];
+    k.dir.A = A.ptr;
+    k.dir.B = B.ptr;
+    k.dir.C = C.ptr;
+    if (k.kind != CK_GEMM) continue;
+    k.pa.src = A.ptr;
+    k.pb.src = B.ptr;
+    k.up.C = C.ptr;
+    if (k.a_const) {
+      k.a_pre = dev_alloc(k.a_bytes);
+      allocs_.push_back(k.a_pre);
+      bytes_ += k.a_bytes;
+      k.pa.dst = k.a_pre;
+      launch_pack(k.pa, stream_);
+    } else {
+      k.pa.dst = wsA_;
+    }
+    if (k.b_const) {
+      k.b_pre = dev_alloc(k.b_bytes);
+      allocs_.push_back(k.b_pre);
+      bytes_ += k.b_bytes;
+      k.pb.dst = k.b_pre;
+      launch_pack(k.pb, stream_);
+    } else {
+      k.pb.dst = wsB_;
+    }
+    k.up.gout = wsC_;
+    if (k.tc_kind >= 0)
+      tc_gemm_plan(k.tcp, k.tc_kind, k.pa.dst, k.pb.dst, static_cast<float*>(wsC_), k.GM, k.GN, k.Kpad, k.NB,
+                   dev_err_);
+  }
+}
+
+void Engine::finalize(std::vector<Program*> progs) {
+  RTCC_REQUIRE(!finalized_, "engine finalized twice");
+  for (size_t a = 0; a < arena_size_.size(); ++a) {
+    arena_size_[a] = std::max(arena_size_[a], arena_hwm_[a]);
+    const size_t bytes = (size_t)std::max(1ll, arena_size_[a]) * 8;
+    arena_ptr_[a] = static_cast<double*>(dev_alloc(bytes));
+    allocs_.push_back(arena_ptr_[a]);
+    bytes_ += bytes;
+    RTCC_CUDA(cudaMemsetAsync(arena_ptr_[a], 0, bytes, stream_));
+  }
+  for (Tensor& t : tensors_)
+    if (t.storage == ST_ARENA) t.ptr = arena_ptr_[t.arena] + t.arena_off;
+  for (Program* P : progs) plan(*P);
+  auto alloc_ws = [&](void*& p, size_t bytes) {
+    if (bytes == 0) return;
+    p = dev_alloc(bytes);
+    allocs_.push_back(p);
+    bytes_ += bytes;
+  };
+  alloc_ws(wsA_, wsA_bytes_);
+  alloc_ws(wsB_, wsB_bytes_);
+  alloc_ws(wsC_, wsC_bytes_);
+  for (Program* P : progs) bind(*P);
+  RTCC_CUDA(cudaStreamSynchronize(stream_));
+  finalized_ = true;
+}
+
+void Engine::run(const Program& P) {
+  for (int a : P.zero_arenas)
+    RTCC_CUDA(cudaMemsetAsync(arena_ptr_[a], 0, (size_t)std::max(1ll, arena_size_[a]) * 8, stream_));
+  for (int t : P.zero_tensors) {
+    const Tensor& x = tensors_[t];
+    RTCC_CUDA(cudaMemsetAsync(x.ptr, 0, (size_t)x.numel() * (x.cplx ? 16 : 8), stream_));
+  }
+  for (const auto& z : P.zero2d) RTCC_CUDA(cudaMemset2DAsync(z.ptr, z.pitch, 0, z.width, z.height, stream_));
+  for (const auto& cp : P.comp) {
+    const Compiled& k = *cp;
+    switch (k.kind) {
+      case CK_ADD: launch_add(k.add, stream_); break;
+      case CK_DIRECT: launch_direct(k.dir, stream_); break;
+      case CK_REDUCE: launch_reduce(k.dir, k.splits, stream_); break;
+      default:
+        if (!k.a_const) launch_pack(k.pa, stream_);
+        if (!k.b_const) launch_pack(k.pb, stream_);
+        if (k.tc_kind >= 0) launch_tc_gemm(k.tcp, stream_);
+        else
+          launch_gemm_f64(static_cast<const double*>(k.pa.dst), static_cast<const double*>(k.pb.dst),
+                          static_cast<double*>(wsC_), k.GM, k.GN, k.Kpad, k.NB, stream_);
+        launch_unpack(k.up, stream_);
+    }
+  }
+}
+
+EngineStats Engine::stats_of(const Program& P) const {
+  EngineStats s;
+  for (const auto& cp : P.comp) {
+    if (cp->kind == CK_GEMM) {
+      s.gemm_flops += cp->alg_flops;
+      s.launches += 2 + (cp->a_const ? 0 : 1) + (cp->b_const ? 0 : 1);
+    } else {
+      s.direct_flops += cp->alg_flops;
+      s.launches += 1;
+    }
+  }
+  s.launches += (int)(P.zero_arenas.size() + P.zero_tensors.size() + P.zero2d.size());
+  return s;
+}
+
+void Engine::check_error() {
+  int h = 0;
+  RTCC_CUDA(cudaMemcpyAsync(&h, dev_err_, sizeof(int), cudaMemcpyDeviceToHost, stream_));
+  RTCC_CUDA(cudaStreamSynchronize(stream_));
+  if (h != DEV_OK) {
+    RTCC_CUDA(cudaMemsetAsync(dev_err_, 0, sizeof(int), stream_));
+    throw Error(7, "a tensor-core GEMM wait expired on the device (code " + std::to_string(h) + ")");
+  }
+}
+
+}  // namespace rtcc

@@ -1,0 +1,134 @@
+// Contraction engine: einsum-style programs over device tensors, compiled once into a
+// fixed launch sequence (pack -> GEMM -> unpack, or a direct kernel for small terms),
+// plus a reverse-mode generator that turns a program into its vector-Jacobian program.
+#pragma once
+#include "common.cuh"
+#include <complex>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+#include <algorithm>
+
+namespace rtcc {
+
+using cplx = std::complex<double>;
+
+enum class Prec : int { P64 = 0, TF32 = 1, TF32X3 = 2, BF16X3 = 3 };
+
+enum Storage : int { ST_EXTERNAL = 0, ST_ARENA = 1, ST_OWNED = 2 };
+
+struct Tensor {
+  std::string name;
+  std::vector<int> dims;
+  std::vector<long long> strides;   // element strides (complex elements for complex tensors)
+  bool cplx = true;
+  bool constant = false;            // never differentiated; packed once when used in a GEMM
+  int storage = ST_EXTERNAL;
+  int arena = -1;                   // arena index for ST_ARENA
+  long long arena_off = 0;          // offset in doubles
+  double* ptr = nullptr;
+  long long numel() const {
+    long long n = 1;
+    for (int d : dims) n *= d;
+    return n;
+  }
+};
+
+enum OpKind : int { OP_EIN = 0, OP_ADD = 1 };
+struct Op {
+  int kind;
+  int c, a, b;
+  std::string lc, la, lb;
+  cplx alpha;
+};
+
+struct Compiled;   // defined in engine.cu
+
+struct Program {
+  std::string name;
+  std::vector<Op> ops;
+  std::vector<int> zero_arenas;     // arenas cleared before the first op
+  std::vector<int> zero_tensors;    // contiguous tensors cleared before the first op
+  struct Zero2D { void* ptr; size_t pitch, width, height; };
+  std::vector<Zero2D> zero2d;       // strided regions cleared before the first op
+  std::vector<std::shared_ptr<Compiled>> comp;
+};
+
+struct EngineStats {
+  long long gemm_flops = 0;   // real multiply-adds x2 issued on the GEMM path per run (all programs)
+  long long direct_flops = 0;
+  int launches = 0;
+};
+
+class Engine {
+ public:
+  Engine(Prec p, cudaStream_t s);
+  ~Engine();
+  Engine(const Engine&) = delete;
+  Engine& operator=(const Engine&) = delete;
+
+  Prec prec() const { return prec_; }
+  // Route every contraction with a summed index through the packed GEMM path (self-test).
+  void set_force_gemm(bool f) { force_gemm_ = f; }
+  cudaStream_t stream() const { return stream_; }
+  int* dev_err() const { return dev_err_; }
+
+  // --- tensors ------------------------------------------------------------------------
+  int external(const std::string& name, const std::vector<int>& dims, bool cplx, double* ptr,
+               std::vector<long long> strides = {}, bool constant = false);
+  int owned(const std::string& name, const std::vector<int>& dims, bool cplx, bool constant);
+  int new_arena();
+  int temp(int arena, const std::string& name, const std::vector<int>& dims, bool cplx = true);
+  // Temporaries created after arena_reset(a, mark) reuse the space from `mark` on; only
+  // for programs that never run interleaved with one another.
+  long long arena_mark(int arena) const { return arena_size_[arena]; }
+  void arena_reset(int arena, long long mark) { arena_hwm_[arena] = std::max(arena_hwm_[arena], arena_size_[arena]); arena_size_[arena] = mark; }
+  Tensor& T(int id) { return tensors_[id]; }
+  const Tensor& T(int id) const { return tensors_[id]; }
+
+  // --- program building ------------------------------------------------------------------
+  static void ein(Program& P, int c, const std::string& lc, int a, const std::string& la, int b,
+                  const std::string& lb, cplx alpha = 1.0);
+  static void add(Program& P, int c, const std::string& lc, int a, const std::string& la, cplx alpha = 1.0);
+
+  // Reverse mode: given the forward program and the ids of its active inputs, return the
+  // program that accumulates adjoints; adj maps tensor id -> adjoint tensor id (created in
+  // `arena`; adjoints of inputs included).
+  Program reverse(const Program& fwd, const std::vector<int>& active_inputs, int arena,
+                  std::map<int, int>& adj);
+
+  // Allocate arenas and owned tensors, plan every op of the given programs, allocate the
+  // shared workspaces, bind pointers (tensor maps, constant packing).  Call once.
+  void finalize(std::vector<Program*> progs);
+
+  void run(const Program& P);
+  EngineStats stats_of(const Program& P) const;
+  void check_error();   // throws on a device-side timeout recorded by a kernel
+  size_t device_bytes() const { return bytes_; }
+
+ private:
+  void plan(Program& P);
+  void bind(Program& P);
+
+  Prec prec_;
+  cudaStream_t stream_;
+  std::vector<Tensor> tensors_;
+  std::vector<long long> arena_size_;
+  std::vector<long long> arena_hwm_;
+  std::vector<double*> arena_ptr_;
+  std::vector<void*> allocs_;
+  int* dev_err_ = nullptr;
+  void* wsA_ = nullptr;
+  void* wsB_ = nullptr;
+  void* wsC_ = nullptr;
+  size_t wsA_bytes_ = 0, wsB_bytes_ = 0, wsC_bytes_ = 0;
+  size_t bytes_ = 0;
+  bool finalized_ = false;
+  bool force_gemm_ = false;
+};
+
+// Allocation helper that records ownership (freed with the engine).
+void* dev_alloc(size_t bytes);
+
+}  // namespace rtcc

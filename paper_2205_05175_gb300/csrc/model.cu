@@ -1,0 +1,352 @@
+// RT-CCSD model programs: integral blocks, closed-shell ket residual (Eq. derivT),
+// its reverse-mode vector-Jacobian program (Eq. derivL), the dipole (Eq. dipole) and
+// the correlation energy.
+//
+// Closed-shell conventions: t1[i][a] is the (i alpha -> a alpha) amplitude and
+// t2[i][j][a][b] the (i alpha j beta -> a alpha b beta) amplitude; the residual
+// components are the same spin blocks of <mu|e^{-T} H e^{T}|0>, written with
+// Stanton-Gauss intermediates spin-integrated for a general (field-dressed,
+// non-diagonal) Fock matrix.  Integrals: v[p][q][r][s] = <pq|rs> = (pr|qs).
+// Index letters: z trajectory, x dipole component, P auxiliary, i j m n occupied,
+// a b e f virtual.
+#include "model.cuh"
+
+namespace rtcc {
+
+IntegralStore::~IntegralStore() {
+  for (void* p : owned) cudaFree(p);
+}
+
+void build_integrals(IntegralStore& S, const double* dB, int naux, int o, int v, cudaStream_t stream) {
+  S.o = o;
+  S.v = v;
+  S.naux = naux;
+  const int n = o + v;
+  Engine E(Prec::P64, stream);
+  auto alloc = [&](int b, std::vector<int> dims) {
+    long long ne = 1;
+    for (int d : dims) ne *= d;
+    const size_t bytes = (size_t)ne * 8;
+    S.blk[b] = static_cast<double*>(dev_alloc(bytes));
+    S.owned.push_back(S.blk[b]);
+    S.bytes += bytes;
+    RTCC_CUDA(cudaMemsetAsync(S.blk[b], 0, bytes, stream));
+    return E.external("int" + std::to_string(b), dims, false, S.blk[b]);
+  };
+  using B = IntegralStore;
+  double* Bp = const_cast<double*>(dB);
+  const long long sP = (long long)n * n;
+  const int Boo = E.external("Boo", {naux, o, o}, false, Bp, {sP, n, 1}, true);
+  const int Bov = E.external("Bov", {naux, o, v}, false, Bp + o, {sP, n, 1}, true);
+  const int Bvo = E.external("Bvo", {naux, v, o}, false, Bp + (size_t)o * n, {sP, n, 1}, true);
+  const int Bvv = E.external("Bvv", {naux, v, v}, false, Bp + (size_t)o * n + o, {sP, n, 1}, true);
+  const int oooo = alloc(B::OOOO, {o, o, o, o});
+  const int ooov = alloc(B::OOOV, {o, o, o, v});
+  const int oovo = alloc(B::OOVO, {o, o, v, o});
+  const int oovv = alloc(B::OOVV, {o, o, v, v});
+  const int ovov = alloc(B::OVOV, {o, v, o, v});
+  const int ovvo = alloc(B::OVVO, {o, v, v, o});
+  const int ovoo = alloc(B::OVOO, {o, v, o, o});
+  const int ovvv = alloc(B::OVVV, {o, v, v, v});
+  const int vvvo = alloc(B::VVVO, {v, v, v, o});
+  const int vvvv = alloc(B::VVVV, {v, v, v, v});
+  const int Lovvv = alloc(B::LOVVV, {o, v, v, v});
+  const int Loovv = alloc(B::LOOVV, {o, o, v, v});
+  const int Looov = alloc(B::LOOOV, {o, o, o, v});
+  const int Lovvo = alloc(B::LOVVO, {o, v, v, o});
+  const int Loovo = alloc(B::LOOVO, {o, o, v, o});
+  Program P;
+  P.name = "setup";
+  // <pq|rs> = sum_P B[P][p][r] B[P][q][s]
+  Engine::ein(P, oooo, "mnij", Boo, "Pmi", Boo, "Pnj");
+  Engine::ein(P, ooov, "mnie", Boo, "Pmi", Bov, "Pne");
+  Engine::ein(P, oovo, "mnei", Bov, "Pme", Boo, "Pni");
+  Engine::ein(P, oovv, "mnef", Bov, "Pme", Bov, "Pnf");
+  Engine::ein(P, ovov, "mbie", Boo, "Pmi", Bvv, "Pbe");
+  Engine::ein(P, ovvo, "mbej", Bov, "Pme", Bvo, "Pbj");
+  Engine::ein(P, ovoo, "mbij", Boo, "Pmi", Bvo, "Pbj");
+  Engine::ein(P, ovvv, "mbef", Bov, "Pme", Bvv, "Pbf");
+  Engine::ein(P, vvvo, "abej", Bvv, "Pae", Bvo, "Pbj");
+  Engine::ein(P, vvvv, "abef", Bvv, "Pae", Bvv, "Pbf");
+  // exchange combinations
+  Engine::add(P, Lovvv, "mafe", ovvv, "mafe", 2.0);
+  Engine::add(P, Lovvv, "mafe", ovvv, "maef", -1.0);
+  Engine::add(P, Loovv, "mnef", oovv, "mnef", 2.0);
+  Engine::add(P, Loovv, "mnef", oovv, "mnfe", -1.0);
+  Engine::add(P, Looov, "mnie", ooov, "mnie", 2.0);
+  Engine::add(P, Looov, "mnie", oovo, "mnei", -1.0);
+  Engine::add(P, Lovvo, "nafi", ovvo, "nafi", 2.0);
+  Engine::add(P, Lovvo, "nafi", ovov, "naif", -1.0);
+  Engine::add(P, Loovo, "nmei", oovo, "nmei", 2.0);
+  Engine::add(P, Loovo, "nmei", ooov, "nmie", -1.0);
+  E.finalize({&P});
+  E.run(P);
+  RTCC_CUDA(cudaStreamSynchronize(stream));
+}
+
+IntIds register_integrals(Engine& E, const IntegralStore& S) {
+  using B = IntegralStore;
+  const int o = S.o, v = S.v;
+  IntIds I;
+  auto reg = [&](int b, std::vector<int> dims) { I.b[b] = E.external("v" + std::to_string(b), dims, false, S.blk[b], {}, true); };
+  reg(B::OOOO, {o, o, o, o});
+  reg(B::OOOV, {o, o, o, v});
+  reg(B::OOVO, {o, o, v, o});
+  reg(B::OOVV, {o, o, v, v});
+  reg(B::OVOV, {o, v, o, v});
+  reg(B::OVVO, {o, v, v, o});
+  reg(B::OVOO, {o, v, o, o});
+  reg(B::OVVV, {o, v, v, v});
+  reg(B::VVVO, {v, v, v, o});
+  reg(B::VVVV, {v, v, v, v});
+  reg(B::LOVVV, {o, v, v, v});
+  reg(B::LOOVV, {o, o, v, v});
+  reg(B::LOOOV, {o, o, o, v});
+  reg(B::LOVVO, {o, v, v, o});
+  reg(B::LOOVO, {o, o, v, o});
+  return I;
+}
+
+namespace {
+
+// Views of one state-layout buffer [nz][ns] complex: x1 = [o][v] at 0, x2 = [o][o][v][v] at o*v,
+// y1 at o*v + o*o*v*v, y2 after it.
+struct StateViews {
+  int x1, x2, y1, y2;
+};
+StateViews state_views(Engine& E, const std::string& nm, double* buf, int nz, int o, int v) {
+  const long long ns = 2ll * o * v + 2ll * o * o * v * v;
+  const long long n1 = (long long)o * v, n2 = (long long)o * o * v * v;
+  StateViews s;
+  s.x1 = E.external(nm + ".x1", {nz, o, v}, true, buf, {ns, v, 1});
+  s.x2 = E.external(nm + ".x2", {nz, o, o, v, v}, true, buf + 2 * n1, {ns, (long long)o * v * v, (long long)v * v, v, 1});
+  s.y1 = E.external(nm + ".y1", {nz, o, v}, true, buf + 2 * (n1 + n2), {ns, v, 1});
+  s.y2 = E.external(nm + ".y2", {nz, o, o, v, v}, true, buf + 2 * (2 * n1 + n2),
+                    {ns, (long long)o * v * v, (long long)v * v, v, 1});
+  return s;
+}
+
+// Fock-like one-body operator views: f[.. p q] with an optional leading label.
+struct OneBody {
+  int oo, ov, vv;
+  std::string pre;   // "z" when the operator carries the trajectory label, "" otherwise
+};
+
+struct Builder {
+  Engine& E;
+  Program& P;
+  int arena;
+  int nz, o, v;
+  int tmp(const std::string& nm, std::vector<int> dims) {
+    dims.insert(dims.begin(), nz);
+    return E.temp(arena, nm, dims, true);
+  }
+  void ein(int c, const std::string& lc, int a, const std::string& la, int b, const std::string& lb,
+           cplx alpha = 1.0) {
+    Engine::ein(P, c, lc, a, la, b, lb, alpha);
+  }
+  void add(int c, const std::string& lc, int a, const std::string& la, cplx alpha = 1.0) {
+    Engine::add(P, c, lc, a, la, alpha);
+  }
+};
+
+// Closed-shell CCSD ket residual into views (r1 "zia", r2 "zijab").
+// Returns the id of tau (t2 + t1 t1) for the energy.
+int residual_ops(Builder& b, const IntIds* I, int t1, int t2, const OneBody& f, int r1, int r2) {
+  const int o = b.o, v = b.v;
+  const std::string F = f.pre;
+  using B = IntegralStore;
+  auto V = [&](int k) { return I->b[k]; };
+  const bool two = (I != nullptr);
+
+  const int tt = b.tmp("tt", {o, o, v, v});
+  b.ein(tt, "zijab", t1, "zia", t1, "zjb");
+  const int tau = b.tmp("tau", {o, o, v, v});
+  b.add(tau, "zijab", t2, "zijab");
+  b.add(tau, "zijab", tt, "zijab");
+  const int taut = b.tmp("taut", {o, o, v, v});
+  b.add(taut, "zijab", t2, "zijab");
+  b.add(taut, "zijab", tt, "zijab", 0.5);
+
+  // one-body intermediates
+  const int Fae = b.tmp("Fae", {v, v});
+  b.add(Fae, "zae", f.vv, F + "ae");
+  b.ein(Fae, "zae", f.ov, F + "me", t1, "zma", -0.5);
+  const int Fmi = b.tmp("Fmi", {o, o});
+  b.add(Fmi, "zmi", f.oo, F + "mi");
+  b.ein(Fmi, "zmi", t1, "zie", f.ov, F + "me", 0.5);
+  const int Fme = b.tmp("Fme", {o, v});
+  b.add(Fme, "zme", f.ov, F + "me");
+  if (two) {
+    b.ein(Fae, "zae", t1, "zmf", V(B::LOVVV), "mafe");
+    b.ein(Fae, "zae", taut, "zmnaf", V(B::LOOVV), "mnef", -1.0);
+    b.ein(Fmi, "zmi", t1, "zne", V(B::LOOOV), "mnie");
+    b.ein(Fmi, "zmi", taut, "zinef", V(B::LOOVV), "mnef");
+    b.ein(Fme, "zme", t1, "znf", V(B::LOOVV), "mnef");
+  }
+
+  // singles
+  const int t2t = b.tmp("t2t", {o, o, v, v});   // 2 t_imae - t_imea
+  b.add(t2t, "zimae", t2, "zimae", 2.0);
+  b.add(t2t, "zimae", t2, "zimea", -1.0);
+  b.add(r1, "zia", f.ov, F + "ia");
+  b.ein(r1, "zia", t1, "zie", Fae, "zae");
+  b.ein(r1, "zia", t1, "zma", Fmi, "zmi", -1.0);
+  b.ein(r1, "zia", t2t, "zimae", Fme, "zme");
+  if (two) {
+    b.ein(r1, "zia", t1, "znf", V(B::LOVVO), "nafi");
+    b.ein(r1, "zia", t2, "zimef", V(B::LOVVV), "mafe");
+    b.ein(r1, "zia", t2, "zmnae", V(B::LOOVO), "nmei", -1.0);
+  }
+
+  // doubles: Omega2 = S + S^(i<->j, a<->b)
+  const int Xbe = b.tmp("Xbe", {v, v});
+  b.add(Xbe, "zbe", Fae, "zbe");
+  b.ein(Xbe, "zbe", t1, "zmb", Fme, "zme", -0.5);
+  const int Zmj = b.tmp("Zmj", {o, o});
+  b.add(Zmj, "zmj", Fmi, "zmj");
+  b.ein(Zmj, "zmj", t1, "zje", Fme, "zme", 0.5);
+  const int S = b.tmp("S", {o, o, v, v});
+  b.ein(S, "zijab", t2, "zijae", Xbe, "zbe");
+  b.ein(S, "zijab", t2, "zimab", Zmj, "zmj", -1.0);
+  if (two) {
+    b.add(S, "zijab", V(B::OOVV), "ijab", 0.5);
+    // particle-particle ladder (half: the symmetrisation doubles it)
+    b.ein(S, "zijab", tau, "zijef", V(B::VVVV), "abef", 0.5);
+    // hole-hole ladder with W_mnij = <mn|ij> + P t1 terms + tau <mn|ef>
+    const int Wmnij = b.tmp("Wmnij", {o, o, o, o});
+    b.add(Wmnij, "zmnij", V(B::OOOO), "mnij");
+    b.ein(Wmnij, "zmnij", t1, "zje", V(B::OOOV), "mnie");
+    b.ein(Wmnij, "zmnij", t1, "zie", V(B::OOVO), "mnej");
+    b.ein(Wmnij, "zmnij", tau, "zijef", V(B::OOVV), "mnef");
+    b.ein(S, "zijab", tau, "zmnab", Wmnij, "zmnij", 0.5);
+    // t1 pieces of the particle-particle ladder
+    const int Zijmb = b.tmp("Zijmb", {o, o, o, v});
+    b.ein(Zijmb, "zijmb", tau, "zijef", V(B::OVVV), "mbef");
+    b.ein(S, "zijab", t1, "zma", Zijmb, "zijmb", -1.0);
+    // ring intermediates: (m a, b b, e a, j b) and (m a, b b, e b, j a) spin blocks of W_mbej
+    const int t1t1 = b.tmp("t1t1", {o, o, v, v});
+    b.ein(t1t1, "zjnfb", t1, "zjf", t1, "znb");
+    const int Wa = b.tmp("Wa", {o, v, v, o});
+    b.add(Wa, "zmbej", V(B::OVVO), "mbej");
+    b.ein(Wa, "zmbej", t1, "zjf", V(B::OVVV), "mbef");
+    b.ein(Wa, "zmbej", t1, "znb", V(B::OOVO), "mnej", -1.0);
+    b.ein(Wa, "zmbej", t1t1, "zjnfb", V(B::OOVV), "mnef", -1.0);
+    b.ein(Wa, "zmbej", t2, "zjnbf", V(B::LOOVV), "mnef", 0.5);
+    b.ein(Wa, "zmbej", t2, "zjnfb", V(B::OOVV), "mnef", -0.5);
+    const int Uh = b.tmp("Uh", {o, o, v, v});
+    b.add(Uh, "zjnfb", t2, "zjnfb", 0.5);
+    b.add(Uh, "zjnfb", t1t1, "zjnfb");
+    const int U = b.tmp("U", {o, v, v, o});
+    b.add(U, "zmbej", V(B::OVOV), "mbje", -1.0);
+    b.ein(U, "zmbej", t1, "zjf", V(B::OVVV), "mbfe", -1.0);
+    b.ein(U, "zmbej", t1, "znb", V(B::OOOV), "mnje");
+    b.ein(U, "zmbej", Uh, "zjnfb", V(B::OOVV), "mnfe");
+    b.ein(S, "zijab", t2t, "zimae", Wa, "zmbej");
+    b.ein(S, "zijab", t2, "zimae", U, "zmbej");
+    b.ein(S, "zijab", t2, "zmjae", U, "zmbei");
+    // t1 t1 <mb|ej> and t1 t1 <mb|ie> rings, t1 <ab|ej>, t1 <mb|ij>
+    const int Q1 = b.tmp("Q1", {o, v, o, o});
+    b.ein(Q1, "zmbij", t1, "zie", V(B::OVVO), "mbej");
+    b.ein(S, "zijab", t1, "zma", Q1, "zmbij", -1.0);
+    const int Q2 = b.tmp("Q2", {o, v, o, o});
+    b.ein(Q2, "zmbji", t1, "zje", V(B::OVOV), "mbie");
+    b.ein(S, "zijab", t1, "zma", Q2, "zmbji", -1.0);
+    b.ein(S, "zijab", t1, "zie", V(B::VVVO), "abej");
+    b.ein(S, "zijab", t1, "zma", V(B::OVOO), "mbij", -1.0);
+  }
+  b.add(r2, "zijab", S, "zijab");
+  b.add(r2, "zijab", S, "zjiba");
+  return tau;
+}
+
+}  // namespace
+
+RhsPrograms build_rhs(Engine& E, const IntIds& I, int nz, int o, int v, double* state, double* fock,
+                      double* out, bool with_lambda) {
+  RhsPrograms R;
+  const int n = o + v;
+  const StateViews in = state_views(E, "y", state, nz, o, v);
+  const StateViews ou = state_views(E, "r", out, nz, o, v);
+  const long long sf = (long long)n * n;
+  OneBody f;
+  f.pre = "z";
+  f.oo = E.external("f.oo", {nz, o, o}, false, fock, {sf, n, 1});
+  f.ov = E.external("f.ov", {nz, o, v}, false, fock + o, {sf, n, 1});
+  f.vv = E.external("f.vv", {nz, v, v}, false, fock + (size_t)o * n + o, {sf, n, 1});
+  const int fa = E.new_arena();
+  R.fwd.name = "rhs_fwd";
+  R.fwd.zero_arenas = {fa};
+  const long long ns = 2ll * o * v + 2ll * o * o * v * v, nT = (long long)o * v + (long long)o * o * v * v;
+  R.fwd.zero2d = {{out, (size_t)ns * 16, (size_t)nT * 16, (size_t)nz}};
+  Builder b{E, R.fwd, fa, nz, o, v};
+  R.t1 = in.x1;
+  R.t2 = in.x2;
+  R.l1 = in.y1;
+  R.l2 = in.y2;
+  R.tau = residual_ops(b, &I, in.x1, in.x2, f, ou.x1, ou.x2);
+  if (!with_lambda) return R;
+  std::map<int, int> adj;
+  const int ra = E.new_arena();
+  R.rev = E.reverse(R.fwd, {in.x1, in.x2}, ra, adj);
+  R.rev.zero2d = {{out + 2 * nT, (size_t)ns * 16, (size_t)nT * 16, (size_t)nz}};
+  // seeds: dL/dOmega = l, dE/dt1 = 2 f_ov, dE/dtau = L_ijab
+  std::vector<Op> seeds;
+  seeds.push_back(Op{OP_ADD, adj.at(ou.x1), in.y1, -1, "zia", "zia", "", 1.0});
+  seeds.push_back(Op{OP_ADD, adj.at(ou.x2), in.y2, -1, "zijab", "zijab", "", 1.0});
+  seeds.push_back(Op{OP_ADD, adj.at(in.x1), f.ov, -1, "zia", "zia", "", 2.0});
+  seeds.push_back(Op{OP_ADD, adj.at(R.tau), I.b[IntegralStore::LOOVV], -1, "zijab", "ijab", "", 1.0});
+  R.rev.ops.insert(R.rev.ops.begin(), seeds.begin(), seeds.end());
+  // outputs: R1 = dL/dt1, R2 = symmetrised dL/dt2
+  Engine::add(R.rev, ou.y1, "zia", adj.at(in.x1), "zia");
+  Engine::add(R.rev, ou.y2, "zijab", adj.at(in.x2), "zijab", 0.5);
+  Engine::add(R.rev, ou.y2, "zijab", adj.at(in.x2), "zjiba", 0.5);
+  return R;
+}
+
+DipolePrograms build_dipole(Engine& E, int nz, int o, int v, double* state, const double* mu_dev,
+                            double* dip_out) {
+  DipolePrograms D;
+  const int n = o + v;
+  const StateViews in = state_views(E, "yd", state, nz, o, v);
+  const int arena = E.new_arena();
+  // per-component one-body residual buffers (shared by the three programs, run in turn)
+  const int om1 = E.temp(arena, "om1mu", {nz, o, v}, true);
+  const int om2 = E.temp(arena, "om2mu", {nz, o, o, v, v}, true);
+  const long long mark = E.arena_mark(arena);
+  for (int x = 0; x < 3; ++x) {
+    E.arena_reset(arena, mark);
+    Program& P = D.prog[x];
+    P.name = "dipole" + std::to_string(x);
+    P.zero_arenas = {arena};
+    const double* mx = mu_dev + (size_t)x * n * n;
+    OneBody f;
+    f.pre = "";
+    f.oo = E.external("mu.oo", {o, o}, false, const_cast<double*>(mx), {n, 1}, true);
+    f.ov = E.external("mu.ov", {o, v}, false, const_cast<double*>(mx) + o, {n, 1}, true);
+    f.vv = E.external("mu.vv", {v, v}, false, const_cast<double*>(mx) + (size_t)o * n + o, {n, 1}, true);
+    Builder b{E, P, arena, nz, o, v};
+    residual_ops(b, nullptr, in.x1, in.x2, f, om1, om2);
+    const int dx = E.external("dip" + std::to_string(x), {nz}, true, dip_out + 2 * (size_t)x * nz);
+    P.zero_tensors = {dx};
+    Engine::ein(P, dx, "z", f.ov, "ia", in.x1, "zia", 2.0);
+    Engine::ein(P, dx, "z", in.y1, "zia", om1, "zia");
+    Engine::ein(P, dx, "z", in.y2, "zijab", om2, "zijab");
+  }
+  return D;
+}
+
+Program build_energy(Engine& E, const IntIds& I, const RhsPrograms& R, int nz, int o, int v, double* fock,
+                     double* e_out) {
+  Program P;
+  P.name = "energy";
+  const int n = o + v;
+  const int fov = E.external("fe.ov", {nz, o, v}, false, fock + o, {(long long)n * n, n, 1});
+  const int e = E.external("ecorr", {nz}, true, e_out);
+  P.zero_tensors = {e};
+  Engine::ein(P, e, "z", fov, "zia", R.t1, "zia", 2.0);
+  Engine::ein(P, e, "z", R.tau, "zijab", I.b[IntegralStore::LOOVV], "ijab");
+  return P;
+}
+
+}  // namespace rtcc

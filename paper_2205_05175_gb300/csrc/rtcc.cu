@@ -1,0 +1,1058 @@
+// C-ABI of the RT-CCSD library (include/rtcc.h): handle, ground state, Runge-Kutta
+// propagation with a device-side step controller, dipole recording, spectrum.
+#include "model.cuh"
+#include "../../include/rtcc.h"
+#include <cmath>
+#include <cstring>
+#include <memory>
+
+namespace rtcc {
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+constexpr int kMaxStages = 6;
+enum TrajStatus : int { TS_RUN = 0, TS_DONE = 1, TS_DIVERGED = 2, TS_UNDERFLOW = 3 };
+
+// Butcher tableaus (Sec. 2.1 Eqs. rk_y/rk_k; Sec. 4.2 Eq. rk4truncation, Eqs. ck-k/ck-y with
+// the row sums sum_j a_ij = c_i restored: a42 = -9/10, a63 = +575/13824, c4 = 3/5, c5 = 1).
+struct Tableau {
+  int s;
+  double c[kMaxStages];
+  double a[kMaxStages][kMaxStages];
+  double b[kMaxStages];    // propagated solution
+  double e[kMaxStages];    // b - b_embedded (error weights), zero for RK4
+  bool adaptive;
+};
+
+Tableau rk4_tableau() {
+  Tableau t{};
+  t.s = 4;
+  t.c[0] = 0; t.c[1] = 0.5; t.c[2] = 0.5; t.c[3] = 1.0;
+  t.a[1][0] = 0.5;
+  t.a[2][1] = 0.5;
+  t.a[3][2] = 1.0;
+  t.b[0] = 1.0 / 6; t.b[1] = 1.0 / 3; t.b[2] = 1.0 / 3; t.b[3] = 1.0 / 6;
+  t.adaptive = false;
+  return t;
+}
+
+Tableau ck_tableau() {
+  Tableau t{};
+  t.s = 6;
+  const double c[6] = {0, 1.0 / 5, 3.0 / 10, 3.0 / 5, 1.0, 7.0 / 8};
+  for (int i = 0; i < 6; ++i) t.c[i] = c[i];
+  t.a[1][0] = 1.0 / 5;
+  t.a[2][0] = 3.0 / 40; t.a[2][1] = 9.0 / 40;
+  t.a[3][0] = 3.0 / 10; t.a[3][1] = -9.0 / 10; t.a[3][2] = 6.0 / 5;
+  t.a[4][0] = -11.0 / 54; t.a[4][1] = 5.0 / 2; t.a[4][2] = -70.0 / 27; t.a[4][3] = 35.0 / 27;
+  t.a[5][0] = 1631.0 / 55296; t.a[5][1] = 175.0 / 512; t.a[5][2] = 575.0 / 13824;
+  t.a[5][3] = 44275.0 / 110592; t.a[5][4] = 253.0 / 4096;
+  const double b5[6] = {37.0 / 378, 0, 250.0 / 621, 125.0 / 594, 0, 512.0 / 1771};
+  const double b4[6] = {2825.0 / 27648, 0, 18575.0 / 48384, 13525.0 / 55296, 277.0 / 14336, 1.0 / 4};
+  for (int i = 0; i < 6; ++i) {
+    t.b[i] = b5[i];
+    t.e[i] = b5[i] - b4[i];
+  }
+  t.adaptive = true;
+  return t;
+}
+
+// ---------------------------------------------------------------------------------------
+// Device kernels of the integrator (all float64)
+
+__device__ __forceinline__ double field_amp(const rtcc_field_t& f, double t) {
+  const double x = t - f.t0;
+  const double env = exp(-0.5 * x * x / (f.sigma * f.sigma));
+  const double car = (f.carrier == RTCC_CARRIER_COS) ? cos(f.omega * x) : sin(f.omega * x);
+  return f.sign * f.E0 * env * car;
+}
+
+// F[z] = f0 - E_z(t_z + c h_z) . mu   (Sec. 2.2, V = -mu.E; Eq. field)
+__global__ void k_fock(double* F, const double* f0, const double* mu, const rtcc_field_t* fields,
+                       const double* tz, const double* hz, double c, int nz, int n2) {
+  const int z = blockIdx.y;
+  const double tt = tz[z] + c * hz[z];
+  const rtcc_field_t fl = fields[z];
+  const double amp = field_amp(fl, tt);
+  const double ex = amp * fl.pol[0], ey = amp * fl.pol[1], ez = amp * fl.pol[2];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n2; k += gridDim.x * blockDim.x)
+    F[(size_t)z * n2 + k] = f0[k] - ex * mu[k] - ey * mu[n2 + k] - ez * mu[2 * n2 + k];
+}
+
+struct StageArgs {
+  const double* R[kMaxStages];   // raw right-hand sides (Omega | R) of the stages used
+  double coef[kMaxStages];
+  int nterms;
+  const double* copy_src;        // the most recent right-hand side, saved to copy_dst
+  double* copy_dst;
+};
+
+// y_out = y + h_z * sum_j coef_j * D R_j, with D = -i on the T part and +i on the Lambda part
+// (dt/dt = -i Omega, dl/dt = +i R).  Optionally saves the newest right-hand side.
+__global__ void k_stage(double* __restrict__ yout, const double* __restrict__ y, StageArgs A, const double* hz,
+                        long long ns, long long nT) {
+  const int z = blockIdx.y;
+  const double h = hz[z];
+  const size_t base = (size_t)z * ns;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ns; k += (long long)gridDim.x * blockDim.x) {
+    const size_t q = 2 * (base + k);
+    double sr = 0.0, si = 0.0;
+    for (int j = 0; j < A.nterms; ++j) {
+      sr += A.coef[j] * A.R[j][q];
+      si += A.coef[j] * A.R[j][q + 1];
+    }
+    if (A.copy_dst) {
+      A.copy_dst[q] = A.copy_src[q];
+      A.copy_dst[q + 1] = A.copy_src[q + 1];
+    }
+    // D * s: -i (sr + i si) = si - i sr ; +i (sr + i si) = -si + i sr
+    const double dr = (k < nT) ? si : -si;
+    const double di = (k < nT) ? -sr : sr;
+    yout[q] = y[q] + h * dr;
+    yout[q + 1] = y[q + 1] + h * di;
+  }
+}
+
+// Final combination: ynew = y + h sum b_j D R_j; err_z = max |h sum e_j R_j|; non-finite -> +inf.
+__global__ void k_final(double* __restrict__ ynew, const double* __restrict__ y, StageArgs B, StageArgs Ew,
+                        const double* hz, long long ns, long long nT, unsigned long long* err_bits, int adaptive) {
+  const int z = blockIdx.y;
+  const double h = hz[z];
+  const size_t base = (size_t)z * ns;
+  double emax = 0.0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ns; k += (long long)gridDim.x * blockDim.x) {
+    const size_t q = 2 * (base + k);
+    double sr = 0.0, si = 0.0, er = 0.0, ei = 0.0;
+    for (int j = 0; j < B.nterms; ++j) {
+      const double rr = B.R[j][q], ri = B.R[j][q + 1];
+      sr += B.coef[j] * rr;
+      si += B.coef[j] * ri;
+      if (adaptive) {
+        er += Ew.coef[j] * rr;
+        ei += Ew.coef[j] * ri;
+      }
+    }
+    const double dr = (k < nT) ? si : -si;
+    const double di = (k < nT) ? -sr : sr;
+    const double yr = y[q] + h * dr, yi = y[q + 1] + h * di;
+    ynew[q] = yr;
+    ynew[q + 1] = yi;
+    double ek = adaptive ? h * sqrt(er * er + ei * ei) : 0.0;
+    if (!isfinite(yr) || !isfinite(yi) || !isfinite(ek)) ek = INFINITY;
+    emax = fmax(emax, ek);
+  }
+  for (int off = 16; off > 0; off >>= 1) emax = fmax(emax, __shfl_down_sync(0xffffffffu, emax, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(&err_bits[z], (unsigned long long)__double_as_longlong(emax));
+}
+
+struct Ctl {
+  double* t;          // current time per trajectory
+  double* h;          // next trial step (CK) per trajectory
+  double* htry;       // step of the current attempt
+  int* status;
+  int* accepted;      // 1 if the current attempt was accepted
+  int* steps;         // accepted steps
+  int* rejects;       // consecutive rejects
+  unsigned long long* err_bits;
+  long long* counters;   // [0] accepted, [1] rejected (summed over trajectories)
+  int* nout;
+};
+
+__global__ void k_prestep(Ctl c, rtcc_integrator_t in, int nz) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= nz) return;
+  c.err_bits[z] = 0ull;
+  c.accepted[z] = 0;
+  if (c.status[z] != TS_RUN) {
+    c.htry[z] = 0.0;
+    return;
+  }
+  const double t = c.t[z];
+  const double eps = 1e-12;
+  double hs;
+  if (in.method == RTCC_RK4) hs = in.h;
+  else if (in.method == RTCC_MIXED_RK4) hs = (t < in.t_switch - eps) ? fmin(in.h1, in.t_switch - t) : in.h2;
+  else hs = c.h[z];
+  if (in.nsteps <= 0) hs = fmin(hs, in.t_end - t);
+  c.htry[z] = hs;
+}
+
+__global__ void k_controller(Ctl c, rtcc_integrator_t in, int nz) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= nz || c.status[z] != TS_RUN) return;
+  const double delta = __longlong_as_double((long long)c.err_bits[z]);
+  const double hs = c.htry[z];
+  const double eps = 1e-12;
+  if (!isfinite(delta)) {
+    c.status[z] = TS_DIVERGED;
+    return;
+  }
+  bool acc = true;
+  if (in.method == RTCC_CK) {
+    // Eq. ck-h-final: safety * h * (tol/Delta)^(1/5) after an accepted attempt, ^(1/4) after a rejected one
+    acc = delta <= in.tol;
+    double fac = (delta == 0.0) ? 5.0 : in.safety * pow(in.tol / delta, acc ? 0.2 : 0.25);
+    fac = fmin(5.0, fmax(0.2, fac));
+    const double hn = fmin(in.h_max, fmax(in.h_min, hs * fac));
+    c.h[z] = hn;
+    if (!acc) {
+      c.rejects[z] += 1;
+      atomicAdd((unsigned long long*)&c.counters[1], 1ull);
+      if (c.rejects[z] > in.max_rejects || hn <= in.h_min) c.status[z] = TS_UNDERFLOW;
+      return;
+    }
+    c.rejects[z] = 0;
+  }
+  c.accepted[z] = 1;
+  c.t[z] += hs;
+  c.steps[z] += 1;
+  atomicAdd((unsigned long long*)&c.counters[0], 1ull);
+  const bool done = (in.nsteps > 0) ? (c.steps[z] >= in.nsteps) : (c.t[z] >= in.t_end - eps);
+  if (done) c.status[z] = TS_DONE;
+}
+
+__global__ void k_accept(double* __restrict__ y, const double* __restrict__ ynew, const int* accepted, long long ns) {
+  const int z = blockIdx.y;
+  if (!accepted[z]) return;
+  const size_t base = 2 * (size_t)z * ns;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < 2 * ns; k += (long long)gridDim.x * blockDim.x)
+    y[base + k] = ynew[base + k];
+}
+
+// Append (t, mu) for trajectories accepted in this attempt (or all when force).
+__global__ void k_record(Ctl c, const double* dip, double r0, double r1, double r2, double* tout, double* muout,
+                         int max_out, int nz, int force) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= nz) return;
+  if (!force && !c.accepted[z]) return;
+  const int n = c.nout[z];
+  if (n >= max_out) return;
+  tout[(size_t)z * max_out + n] = c.t[z];
+  const double ref[3] = {r0, r1, r2};
+  for (int x = 0; x < 3; ++x) {
+    const size_t q = 2 * ((size_t)x * nz + z);
+    muout[2 * (((size_t)z * max_out + n) * 3 + x)] = dip[q] + ref[x];
+    muout[2 * (((size_t)z * max_out + n) * 3 + x) + 1] = dip[q + 1];
+  }
+  c.nout[z] = n + 1;
+}
+
+// dydt = D * R (D = -i on the T part, +i on the Lambda part)
+__global__ void k_apply_D(double* out, const double* R, long long ns, long long nT, int nz) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < (long long)nz * ns;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long kk = k % ns;
+    const double rr = R[2 * k], ri = R[2 * k + 1];
+    out[2 * k] = (kk < nT) ? ri : -ri;
+    out[2 * k + 1] = (kk < nT) ? -rr : rr;
+  }
+}
+
+// Ground state: x += r / D over one amplitude block (singles then doubles) of one state.
+__global__ void k_jacobi(double* x, const double* r, const double* f0, int o, int v, int nmo, double* e_out) {
+  const long long n1 = (long long)o * v, n2 = n1 * o * v;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n1 + n2; k += (long long)gridDim.x * blockDim.x) {
+    double d;
+    if (k < n1) {
+      const int i = (int)(k / v), a = (int)(k % v);
+      d = f0[(size_t)i * nmo + i] - f0[(size_t)(o + a) * nmo + o + a];
+    } else {
+      long long q = k - n1;
+      const int b = (int)(q % v); q /= v;
+      const int a = (int)(q % v); q /= v;
+      const int j = (int)(q % o);
+      const int i = (int)(q / o);
+      d = f0[(size_t)i * nmo + i] + f0[(size_t)j * nmo + j] - f0[(size_t)(o + a) * nmo + o + a] -
+          f0[(size_t)(o + b) * nmo + o + b];
+    }
+    const double er = r[2 * k] / d, ei = r[2 * k + 1] / d;
+    x[2 * k] += er;
+    x[2 * k + 1] += ei;
+    if (e_out) {
+      e_out[2 * k] = er;
+      e_out[2 * k + 1] = ei;
+    }
+  }
+}
+
+__global__ void k_maxabs(const double* r, long long n, unsigned long long* out) {
+  double m = 0.0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const double a = sqrt(r[2 * k] * r[2 * k] + r[2 * k + 1] * r[2 * k + 1]);
+    m = isfinite(a) ? fmax(m, a) : INFINITY;
+  }
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// Re sum conj(a) b
+__global__ void k_dot(const double* a, const double* b, long long n, double* out) {
+  double s = 0.0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+    s += a[2 * k] * b[2 * k] + a[2 * k + 1] * b[2 * k + 1];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+struct Combo {
+  const double* x[12];
+  double c[12];
+  int m;
+};
+__global__ void k_combine(double* out, Combo C, long long n) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < 2 * n; k += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < C.m; ++j) s += C.c[j] * C.x[j][k];
+    out[k] = s;
+  }
+}
+
+// x2 <- (x2 + x2^(ij,ab swapped)) / 2 for the doubles block of one state (keeps DIIS iterates pair-symmetric)
+__global__ void k_sym_pair(double* x2, int o, int v) {
+  const long long n = (long long)o * o * v * v;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    long long q = k;
+    const int b = (int)(q % v); q /= v;
+    const int a = (int)(q % v); q /= v;
+    const int j = (int)(q % o);
+    const int i = (int)(q / o);
+    const long long kt = (((long long)j * o + i) * v + b) * v + a;
+    if (kt <= k) continue;
+    const double r = 0.5 * (x2[2 * k] + x2[2 * kt]), im = 0.5 * (x2[2 * k + 1] + x2[2 * kt + 1]);
+    x2[2 * k] = r; x2[2 * kt] = r;
+    x2[2 * k + 1] = im; x2[2 * kt + 1] = im;
+  }
+}
+
+// Spectrum (Sec. 2.2; Sec. 4.2 interpolation): natural cubic spline second derivatives per
+// component by the tridiagonal (Thomas) recursion, evaluation on a uniform grid, direct DFT.
+__global__ void k_spline_m(const double* t, const double* y, int n, double* M, double* cp, double* dp) {
+  const int x = threadIdx.x;   // component
+  if (x >= 3) return;
+  double* Mx = M + (size_t)x * n;
+  double* c = cp + (size_t)x * n;
+  double* d = dp + (size_t)x * n;
+  auto Y = [&](int k) { return y[(size_t)k * 3 + x]; };
+  // rows 1..n-2: h_{k-1} M_{k-1} + 2 (h_{k-1} + h_k) M_k + h_k M_{k+1} = r_k ; M_0 = M_{n-1} = 0
+  c[0] = 0.0;
+  d[0] = 0.0;
+  for (int k = 1; k < n - 1; ++k) {
+    const double hl = t[k] - t[k - 1], hr = t[k + 1] - t[k];
+    const double r = 6.0 * ((Y(k + 1) - Y(k)) / hr - (Y(k) - Y(k - 1)) / hl);
+    const double den = 2.0 * (hl + hr) - hl * c[k - 1];
+    c[k] = hr / den;
+    d[k] = (r - hl * d[k - 1]) / den;
+  }
+  Mx[n - 1] = 0.0;
+  for (int k = n - 2; k >= 1; --k) Mx[k] = d[k] - c[k] * Mx[k + 1];
+  Mx[0] = 0.0;
+}
+
+__global__ void k_spline_eval(const double* t, const double* y, const double* M, int n, double t0, double dt, int nu,
+                              double* yu) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nu; q += gridDim.x * blockDim.x) {
+    const double tq = t0 + dt * q;
+    int lo = 0, hi = n - 1;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) / 2;
+      if (t[mid] <= tq) lo = mid;
+      else hi = mid;
+    }
+    const double h = t[lo + 1] - t[lo], dx = tq - t[lo];
+    for (int x = 0; x < 3; ++x) {
+      const double* Mx = M + (size_t)x * n;
+      const double y0 = y[(size_t)lo * 3 + x], y1 = y[(size_t)(lo + 1) * 3 + x];
+      const double a = (Mx[lo + 1] - Mx[lo]) / (6.0 * h), b = Mx[lo] / 2.0;
+      const double c = (y1 - y0) / h - h * (2.0 * Mx[lo] + Mx[lo + 1]) / 6.0;
+      yu[(size_t)q * 3 + x] = y0 + c * dx + b * dx * dx + a * dx * dx * dx;
+    }
+  }
+}
+
+// I(w) = Im[ (pol . D(w)) / E(w) ], D(w) = dt sum_k d(t_k) e^{i w t_k}, d = (mu - mu_0) e^{-gamma (t - t_0)}
+__global__ void k_dft(const double* t, const double* y, int n, double dt, rtcc_field_t fld, double kappa, double gamma,
+                      const double* omega, int nw, double* I) {
+  const int w = blockIdx.x;
+  if (w >= nw) return;
+  const double om = omega[w];
+  double dr = 0, di = 0, er = 0, ei = 0;
+  const double t0 = t[0];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const double tk = t[k];
+    const double damp = exp(-gamma * (tk - t0));
+    const double d = ((y[(size_t)k * 3] - y[0]) * fld.pol[0] + (y[(size_t)k * 3 + 1] - y[1]) * fld.pol[1] +
+                      (y[(size_t)k * 3 + 2] - y[2]) * fld.pol[2]) * damp;
+    double s, c;
+    sincos(om * tk, &s, &c);
+    dr += d * c;
+    di += d * s;
+    if (kappa <= 0.0) {
+      const double e = field_amp(fld, tk);
+      er += e * c;
+      ei += e * s;
+    }
+  }
+  __shared__ double sh[4][32];
+  for (int off = 16; off > 0; off >>= 1) {
+    dr += __shfl_down_sync(0xffffffffu, dr, off);
+    di += __shfl_down_sync(0xffffffffu, di, off);
+    er += __shfl_down_sync(0xffffffffu, er, off);
+    ei += __shfl_down_sync(0xffffffffu, ei, off);
+  }
+  const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { sh[0][wi] = dr; sh[1][wi] = di; sh[2][wi] = er; sh[3][wi] = ei; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    dr = di = er = ei = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { dr += sh[0][q]; di += sh[1][q]; er += sh[2][q]; ei += sh[3][q]; }
+    dr *= dt; di *= dt;
+    if (kappa > 0.0) { er = kappa; ei = 0.0; }
+    else { er *= dt; ei *= dt; }
+    // Im[(dr + i di) / (er + i ei)] = (di er - dr ei) / |E|^2
+    I[w] = (di * er - dr * ei) / (er * er + ei * ei);
+  }
+}
+
+inline unsigned blocks_for(long long n, int threads = 256) {
+  long long b = (n + threads - 1) / threads;
+  return (unsigned)std::max(1ll, std::min(b, 152ll * 32));
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+}  // namespace rtcc
+
+using namespace rtcc;
+
+struct GroundEngine {
+  std::unique_ptr<Engine> E;
+  RhsPrograms rhs;
+  Program energy;
+  double *Y = nullptr, *R = nullptr, *F = nullptr, *Ec = nullptr;
+};
+
+struct rtcc_ctx {
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  int o = 0, v = 0, nmo = 0, naux = 0, nz = 0;
+  Prec prec = Prec::P64;
+  long long ns = 0, nT = 0;
+  double *f0 = nullptr, *Bd = nullptr, *mu = nullptr;
+  double mu_ref[3] = {0, 0, 0};
+  std::unique_ptr<IntegralStore> ints;
+  std::unique_ptr<Engine> E;
+  RhsPrograms rhs;
+  DipolePrograms dip;
+  double *Y = nullptr, *Ys = nullptr, *Ynew = nullptr, *Rout = nullptr, *Rk[kMaxStages] = {nullptr}, *F = nullptr,
+         *DIP = nullptr;
+  rtcc_field_t* d_fields = nullptr;
+  Ctl ctl{};
+  std::vector<void*> allocs;
+  std::unique_ptr<GroundEngine> gs;
+  long long last_stats[3] = {0, 0, 0};
+  ~rtcc_ctx() {
+    gs.reset();
+    E.reset();
+    ints.reset();
+    for (void* p : allocs) cudaFree(p);
+    if (stream) cudaStreamDestroy(stream);
+  }
+  template <class T>
+  T* alloc(size_t n) {
+    T* p = static_cast<T*>(dev_alloc(n * sizeof(T)));
+    allocs.push_back(p);
+    RTCC_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), stream));
+    return p;
+  }
+};
+
+namespace {
+
+rtcc_status_t fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return (rtcc_status_t)code;
+}
+
+template <class F>
+rtcc_status_t guarded(F&& f) {
+  try {
+    f();
+    return RTCC_OK;
+  } catch (const Error& e) {
+    return fail(e.status, e.what());
+  } catch (const std::exception& e) {
+    return fail(RTCC_ERR_CUDA, e.what());
+  }
+}
+
+void copy_in(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  RTCC_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+}
+void copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  RTCC_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+}
+
+void run_dipole(rtcc_ctx* h) {
+  for (int x = 0; x < 3; ++x) h->E->run(h->dip.prog[x]);
+}
+
+// One Runge-Kutta attempt over all trajectories (stages, combination, controller, accept, dipole, record).
+void run_attempt(rtcc_ctx* h, const Tableau& tb, const rtcc_integrator_t& in, double* tout, double* muout, int max_out) {
+  cudaStream_t s = h->stream;
+  const int nz = h->nz;
+  const long long ns = h->ns, nT = h->nT;
+  const dim3 gst(blocks_for(ns) / nz + 1 > 4096 ? 4096 : blocks_for(ns) / nz + 1, nz);
+  k_prestep<<<(nz + 127) / 128, 128, 0, s>>>(h->ctl, in, nz);
+  for (int st = 0; st < tb.s; ++st) {
+    StageArgs A{};
+    A.nterms = 0;
+    for (int j = 0; j < st; ++j) {
+      if (tb.a[st][j] == 0.0 && j != st - 1) continue;
+      A.R[A.nterms] = (j == st - 1) ? h->Rout : h->Rk[j];
+      A.coef[A.nterms] = tb.a[st][j];
+      ++A.nterms;
+    }
+    if (st > 0) {
+      A.copy_src = h->Rout;
+      A.copy_dst = h->Rk[st - 1];
+    }
+    k_stage<<<gst, 256, 0, s>>>(h->Ys, h->Y, A, h->ctl.htry, ns, nT);
+    k_fock<<<dim3(blocks_for((long long)h->nmo * h->nmo), nz), 256, 0, s>>>(h->F, h->f0, h->mu, h->d_fields, h->ctl.t,
+                                                                           h->ctl.htry, tb.c[st], nz, h->nmo * h->nmo);
+    h->E->run(h->rhs.fwd);
+    h->E->run(h->rhs.rev);
+  }
+  StageArgs B{}, Ew{};
+  for (int j = 0; j < tb.s; ++j) {
+    B.R[j] = (j == tb.s - 1) ? h->Rout : h->Rk[j];
+    B.coef[j] = tb.b[j];
+    Ew.coef[j] = tb.e[j];
+  }
+  B.nterms = tb.s;
+  k_final<<<gst, 256, 0, s>>>(h->Ynew, h->Y, B, Ew, h->ctl.htry, ns, nT, h->ctl.err_bits, tb.adaptive ? 1 : 0);
+  k_controller<<<(nz + 127) / 128, 128, 0, s>>>(h->ctl, in, nz);
+  k_accept<<<gst, 256, 0, s>>>(h->Y, h->Ynew, h->ctl.accepted, ns);
+  run_dipole(h);
+  k_record<<<(nz + 127) / 128, 128, 0, s>>>(h->ctl, h->DIP, h->mu_ref[0], h->mu_ref[1], h->mu_ref[2], tout, muout, max_out,
+                                            nz, 0);
+  RTCC_CUDA(cudaGetLastError());
+}
+
+GroundEngine* ground_engine(rtcc_ctx* h) {
+  if (h->gs) return h->gs.get();
+  auto g = std::make_unique<GroundEngine>();
+  g->E = std::make_unique<Engine>(Prec::P64, h->stream);
+  Engine& E = *g->E;
+  const IntIds I = register_integrals(E, *h->ints);
+  g->Y = h->alloc<double>(2 * h->ns);
+  g->R = h->alloc<double>(2 * h->ns);
+  g->F = h->alloc<double>((size_t)h->nmo * h->nmo);
+  g->Ec = h->alloc<double>(2);
+  RTCC_CUDA(cudaMemcpyAsync(g->F, h->f0, sizeof(double) * h->nmo * h->nmo, cudaMemcpyDeviceToDevice, h->stream));
+  g->rhs = build_rhs(E, I, 1, h->o, h->v, g->Y, g->F, g->R, true);
+  g->energy = build_energy(E, I, g->rhs, 1, h->o, h->v, g->F, g->Ec);
+  E.finalize({&g->rhs.fwd, &g->rhs.rev, &g->energy});
+  h->gs = std::move(g);
+  return h->gs.get();
+}
+
+double read_max(rtcc_ctx* h, const double* r, long long n, unsigned long long* scratch) {
+  RTCC_CUDA(cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), h->stream));
+  k_maxabs<<<blocks_for(n), 256, 0, h->stream>>>(r, n, scratch);
+  unsigned long long bits = 0;
+  RTCC_CUDA(cudaMemcpyAsync(&bits, scratch, sizeof(bits), cudaMemcpyDeviceToHost, h->stream));
+  RTCC_CUDA(cudaStreamSynchronize(h->stream));
+  double m;
+  std::memcpy(&m, &bits, sizeof(m));
+  return m;
+}
+
+// Jacobi + DIIS on one amplitude block (T or Lambda) of the ground-state engine.
+void solve_block(rtcc_ctx* h, GroundEngine* g, bool lambda, double tol, int maxiter) {
+  const long long nT = h->nT;
+  double* x = g->Y + (lambda ? 2 * nT : 0);
+  double* r = g->R + (lambda ? 2 * nT : 0);
+  const int ndiis = 8;
+  double* hx = h->alloc<double>((size_t)2 * nT * ndiis);
+  double* he = h->alloc<double>((size_t)2 * nT * ndiis);
+  double* dots = h->alloc<double>(ndiis * ndiis);
+  unsigned long long* scratch = h->alloc<unsigned long long>(1);
+  std::vector<int> slot_age;
+  int count = 0;
+  double Bm[ndiis][ndiis] = {};
+  if (lambda) g->E->run(g->rhs.fwd);   // intermediates of the converged t stay valid
+  for (int it = 0; it < maxiter; ++it) {
+    if (lambda) g->E->run(g->rhs.rev);
+    else g->E->run(g->rhs.fwd);
+    const double err = read_max(h, r, nT, scratch);
+    if (!std::isfinite(err)) throw Error(RTCC_ERR_DIVERGED, "ground-state residual is not finite");
+    if (err < tol) return;
+    const int slot = count % ndiis;
+    double* xs = hx + (size_t)2 * nT * slot;
+    double* es = he + (size_t)2 * nT * slot;
+    k_jacobi<<<blocks_for(nT), 256, 0, h->stream>>>(x, r, h->f0, h->o, h->v, h->nmo, es);
+    RTCC_CUDA(cudaMemcpyAsync(xs, x, sizeof(double) * 2 * nT, cudaMemcpyDeviceToDevice, h->stream));
+    ++count;
+    const int m = std::min(count, ndiis);
+    // refresh the row/column of the new slot
+    RTCC_CUDA(cudaMemsetAsync(dots, 0, sizeof(double) * ndiis, h->stream));
+    for (int j = 0; j < m; ++j)
+      k_dot<<<blocks_for(nT), 256, 0, h->stream>>>(es, he + (size_t)2 * nT * j, nT, dots + j);
+    double row[ndiis];
+    RTCC_CUDA(cudaMemcpyAsync(row, dots, sizeof(double) * ndiis, cudaMemcpyDeviceToHost, h->stream));
+    RTCC_CUDA(cudaStreamSynchronize(h->stream));
+    for (int j = 0; j < m; ++j) Bm[slot][j] = Bm[j][slot] = row[j];
+    if (m >= 3) {
+      // solve [B 1; 1 0][c; l] = [0; 1] (Gaussian elimination with partial pivoting, m+1 <= 9)
+      const int N = m + 1;
+      double A[ndiis + 1][ndiis + 2] = {};
+      for (int i = 0; i < m; ++i) {
+        for (int j = 0; j < m; ++j) A[i][j] = Bm[i][j];
+        A[i][m] = -1.0;
+        A[m][i] = -1.0;
+      }
+      A[m][N] = -1.0;
+      bool ok = true;
+      for (int c = 0; c < N && ok; ++c) {
+        int p = c;
+        for (int i = c + 1; i < N; ++i)
+          if (std::fabs(A[i][c]) > std::fabs(A[p][c])) p = i;
+        if (std::fabs(A[p][c]) < 1e-300) { ok = false; break; }
+        for (int j = 0; j <= N; ++j) std::swap(A[c][j], A[p][j]);
+        for (int i = 0; i < N; ++i) {
+          if (i == c) continue;
+          const double f = A[i][c] / A[c][c];
+          for (int j = c; j <= N; ++j) A[i][j] -= f * A[c][j];
+        }
+      }
+      if (ok) {
+        Combo C{};
+        C.m = m;
+        for (int j = 0; j < m; ++j) {
+          C.x[j] = hx + (size_t)2 * nT * j;
+          C.c[j] = A[j][N] / A[j][j];
+        }
+        k_combine<<<blocks_for(2 * nT), 256, 0, h->stream>>>(x, C, nT);
+      }
+    }
+    k_sym_pair<<<blocks_for(nT), 256, 0, h->stream>>>(x + 2ll * h->o * h->v, h->o, h->v);
+  }
+  throw Error(RTCC_ERR_NOCONV, std::string("ground-state ") + (lambda ? "Lambda" : "T") + " equations did not converge");
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rtcc_last_error(void) { return g_last_error.c_str(); }
+
+rtcc_status_t rtcc_create(const double* f, const double* B, int naux, const double* mu, int o, int v, int ntraj,
+                          int prec, rtcc_handle_t* out) {
+  if (!out) return fail(RTCC_ERR_INVALID_ARG, "out is null");
+  *out = nullptr;
+  if (!f || !B || !mu) return fail(RTCC_ERR_INVALID_ARG, "null input pointer");
+  if (o < 1 || v < 1 || naux < 1 || ntraj < 1 || ntraj > 4096) return fail(RTCC_ERR_INVALID_ARG, "bad sizes");
+  if (prec < 0 || prec > 3) return fail(RTCC_ERR_INVALID_ARG, "unknown precision");
+  const int n = o + v;
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < p; ++q) {
+      if (f[p * n + q] != f[q * n + p]) return fail(RTCC_ERR_INVALID_ARG, "Fock matrix is not symmetric");
+      for (int x = 0; x < 3; ++x)
+        if (mu[(size_t)x * n * n + p * n + q] != mu[(size_t)x * n * n + q * n + p])
+          return fail(RTCC_ERR_INVALID_ARG, "dipole matrix is not symmetric");
+      for (int P = 0; P < naux; ++P)
+        if (B[(size_t)P * n * n + p * n + q] != B[(size_t)P * n * n + q * n + p])
+          return fail(RTCC_ERR_INVALID_ARG, "density-fitting factors are not symmetric");
+    }
+  auto* h = new rtcc_ctx();
+  rtcc_status_t st = guarded([&] {
+    int ndev = 0;
+    RTCC_CUDA(cudaGetDeviceCount(&ndev));
+    if (ndev < 1) throw Error(RTCC_ERR_CUDA, "no CUDA device");
+    RTCC_CUDA(cudaGetDevice(&h->dev));
+    cudaDeviceProp prop;
+    RTCC_CUDA(cudaGetDeviceProperties(&prop, h->dev));
+    if (prop.major < 10) throw Error(RTCC_ERR_CUDA, "this library needs an sm_103a (Blackwell) GPU");
+    RTCC_CUDA(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    h->o = o;
+    h->v = v;
+    h->nmo = n;
+    h->naux = naux;
+    h->nz = ntraj;
+    h->prec = (Prec)prec;
+    h->nT = (long long)o * v + (long long)o * o * v * v;
+    h->ns = 2 * h->nT;
+    h->f0 = h->alloc<double>((size_t)n * n);
+    h->mu = h->alloc<double>((size_t)3 * n * n);
+    h->Bd = h->alloc<double>((size_t)naux * n * n);
+    copy_in(h->f0, f, sizeof(double) * n * n, h->stream);
+    copy_in(h->mu, mu, sizeof(double) * 3 * n * n, h->stream);
+    copy_in(h->Bd, B, sizeof(double) * naux * n * n, h->stream);
+    for (int x = 0; x < 3; ++x) {
+      double tr = 0;
+      for (int i = 0; i < o; ++i) tr += mu[(size_t)x * n * n + i * n + i];
+      h->mu_ref[x] = 2.0 * tr;
+    }
+    h->ints = std::make_unique<IntegralStore>();
+    build_integrals(*h->ints, h->Bd, naux, o, v, h->stream);
+    const size_t nsz = (size_t)2 * h->ns * h->nz;
+    h->Y = h->alloc<double>(nsz);
+    h->Ys = h->alloc<double>(nsz);
+    h->Ynew = h->alloc<double>(nsz);
+    h->Rout = h->alloc<double>(nsz);
+    for (int s = 0; s < kMaxStages - 1; ++s) h->Rk[s] = h->alloc<double>(nsz);
+    h->F = h->alloc<double>((size_t)h->nz * n * n);
+    h->DIP = h->alloc<double>((size_t)2 * 3 * h->nz);
+    h->d_fields = h->alloc<rtcc_field_t>(h->nz);
+    h->ctl.t = h->alloc<double>(h->nz);
+    h->ctl.h = h->alloc<double>(h->nz);
+    h->ctl.htry = h->alloc<double>(h->nz);
+    h->ctl.status = h->alloc<int>(h->nz);
+    h->ctl.accepted = h->alloc<int>(h->nz);
+    h->ctl.steps = h->alloc<int>(h->nz);
+    h->ctl.rejects = h->alloc<int>(h->nz);
+    h->ctl.err_bits = h->alloc<unsigned long long>(h->nz);
+    h->ctl.counters = h->alloc<long long>(4);
+    h->ctl.nout = h->alloc<int>(h->nz);
+    h->E = std::make_unique<Engine>(h->prec, h->stream);
+    const IntIds I = register_integrals(*h->E, *h->ints);
+    h->rhs = build_rhs(*h->E, I, h->nz, o, v, h->Ys, h->F, h->Rout, true);
+    h->dip = build_dipole(*h->E, h->nz, o, v, h->Y, h->mu, h->DIP);
+    h->E->finalize({&h->rhs.fwd, &h->rhs.rev, &h->dip.prog[0], &h->dip.prog[1], &h->dip.prog[2]});
+    RTCC_CUDA(cudaStreamSynchronize(h->stream));
+  });
+  if (st != RTCC_OK) {
+    delete h;
+    return st;
+  }
+  *out = h;
+  return RTCC_OK;
+}
+
+rtcc_status_t rtcc_destroy(rtcc_handle_t h) {
+  if (!h) return RTCC_OK;
+  cudaStreamSynchronize(h->stream);
+  delete h;
+  return RTCC_OK;
+}
+
+rtcc_status_t rtcc_state_size(rtcc_handle_t h, size_t* n) {
+  if (!h || !n) return fail(RTCC_ERR_INVALID_ARG, "null argument");
+  *n = (size_t)h->ns;
+  return RTCC_OK;
+}
+
+rtcc_status_t rtcc_get_state(rtcc_handle_t h, int traj, double* y, double* time, double* hstep) {
+  if (!h || !y || traj < 0 || traj >= h->nz) return fail(RTCC_ERR_INVALID_ARG, "bad argument");
+  return guarded([&] {
+    copy_out(y, h->Y + (size_t)2 * h->ns * traj, sizeof(double) * 2 * h->ns, h->stream);
+    if (time) RTCC_CUDA(cudaMemcpyAsync(time, h->ctl.t + traj, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (hstep) RTCC_CUDA(cudaMemcpyAsync(hstep, h->ctl.h + traj, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    RTCC_CUDA(cudaStreamSynchronize(h->stream));
+  });
+}
+
+rtcc_status_t rtcc_set_state(rtcc_handle_t h, int traj, const double* y, double time, double hstep) {
+  if (!h || !y || traj < 0 || traj >= h->nz) return fail(RTCC_ERR_INVALID_ARG, "bad argument");
+  return guarded([&] {
+    copy_in(h->Y + (size_t)2 * h->ns * traj, y, sizeof(double) * 2 * h->ns, h->stream);
+    RTCC_CUDA(cudaMemcpyAsync(h->ctl.t + traj, &time, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    RTCC_CUDA(cudaMemcpyAsync(h->ctl.h + traj, &hstep, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    RTCC_CUDA(cudaStreamSynchronize(h->stream));
+  });
+}
+
+rtcc_status_t rtcc_rhs(rtcc_handle_t h, const double* y, const rtcc_field_t* fields, const double* times, double* dydt) {
+  if (!h || !y || !fields || !times || !dydt) return fail(RTCC_ERR_INVALID_ARG, "null argument");
+  return guarded([&] {
+    const size_t bytes = sizeof(double) * 2 * h->ns * h->nz;
+    copy_in(h->Ys, y, bytes, h->stream);
+    RTCC_CUDA(cudaMemcpyAsync(h->d_fields, fields, sizeof(rtcc_field_t) * h->nz, cudaMemcpyHostToDevice, h->stream));
+    RTCC_CUDA(cudaMemcpyAsync(h->ctl.htry, times, sizeof(double) * h->nz, cudaMemcpyHostToDevice, h->stream));
+    RTCC_CUDA(cudaMemsetAsync(h->ctl.err_bits, 0, sizeof(double) * h->nz, h->stream));
+    // F = f0 - E(times).mu : use t = 0 and c = 1 with htry = times
+    double* zeros = reinterpret_cast<double*>(h->ctl.err_bits);
+    k_fock<<<dim3(blocks_for((long long)h->nmo * h->nmo), h->nz), 256, 0, h->stream>>>(
+        h->F, h->f0, h->mu, h->d_fields, zeros, h->ctl.htry, 1.0, h->nz, h->nmo * h->nmo);
+    h->E->run(h->rhs.fwd);
+    h->E->run(h->rhs.rev);
+    k_apply_D<<<blocks_for(h->ns * h->nz), 256, 0, h->stream>>>(h->Ynew, h->Rout, h->ns, h->nT, h->nz);
+    RTCC_CUDA(cudaGetLastError());
+    h->E->check_error();
+    copy_out(dydt, h->Ynew, bytes, h->stream);
+    RTCC_CUDA(cudaStreamSynchronize(h->stream));
+  });
+}
+
+rtcc_status_t rtcc_dipole(rtcc_handle_t h, double* mu_out) {
+  if (!h || !mu_out) return fail(RTCC_ERR_INVALID_ARG, "null argument");
+  return guarded([&] {
+    run_dipole(h);
+    std::vector<double> d((size_t)6 * h->nz);
+    RTCC_CUDA(cudaMemcpyAsync(d.data(), h->DIP, sizeof(double) * d.size(), cudaMemcpyDeviceToHost, h->stream));
+    RTCC_CUDA(cudaStreamSynchronize(h->stream));
+    h->E->check_error();
+    std::vector<double> o((size_t)6 * h->nz);
+    for (int z = 0; z < h->nz; ++z)
+      for (int x = 0; x < 3; ++x) {
+        o[2 * (z * 3 + x)] = d[2 * (x * h->nz + z)] + h->mu_ref[x];
+        o[2 * (z * 3 + x) + 1] = d[2 * (x * h->nz + z) + 1];
+      }
+    copy_in(h->Ynew, o.data(), sizeof(double) * o.size(), h->stream);
+    copy_out(mu_out, h->Ynew, sizeof(double) * o.size(), h->stream);
+    RTCC_CUDA(cudaStreamSynchronize(h->stream));
+  });
+}
+
+rtcc_status_t rtcc_ground_state(rtcc_handle_t h, double tol, int maxiter, double* e_corr, double* mu0) {
+  if (!h || tol <= 0 || maxiter < 1) return fail(RTCC_ERR_INVALID_ARG, "bad argument");
+  return guarded([&] {
+    GroundEngine* g = ground_engine(h);
+    RTCC_CUDA(cudaMemsetAsync(g->Y, 0, sizeof(double) * 2 * h->ns, h->stream));
+    solve_block(h, g, false, tol, maxiter);
+    solve_block(h, g, true, tol, maxiter);
+    g->E->run(g->rhs.fwd);
+    g->E->run(g->energy);
+    double ec[2];
+    RTCC_CUDA(cudaMemcpyAsync(ec, g->Ec, sizeof(ec), cudaMemcpyDeviceToHost, h->stream));
+    for (int z = 0; z < h->nz; ++z)
+      RTCC_CUDA(cudaMemcpyAsync(h->Y + (size_t)2 * h->ns * z, g->Y, sizeof(double) * 2 * h->ns,
+                                cudaMemcpyDeviceToDevice, h->stream));
+    RTCC_CUDA(cudaMemsetAsync(h->ctl.t, 0, sizeof(double) * h->nz, h->stream));
+    RTCC_CUDA(cudaStreamSynchronize(h->stream));
+    g->E->check_error();
+    if (e_corr) *e_corr = ec[0];
+    if (mu0) {
+      run_dipole(h);
+      std::vector<double> d((size_t)6 * h->nz);
+      RTCC_CUDA(cudaMemcpyAsync(d.data(), h->DIP, sizeof(double) * d.size(), cudaMemcpyDeviceToHost, h->stream));
+      RTCC_CUDA(cudaStreamSynchronize(h->stream));
+      for (int x = 0; x < 3; ++x) mu0[x] = d[2 * x * h->nz] + h->mu_ref[x];
+    }
+  });
+}
+
+rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const rtcc_integrator_t* integ, int max_out,
+                             double* t_out, double* mu_out, int* n_out) {
+  if (!h || !fields || !integ || max_out < 1 || !t_out || !mu_out || !n_out)
+    return fail(RTCC_ERR_INVALID_ARG, "null argument or max_out < 1");
+  const rtcc_integrator_t in = *integ;
+  if (in.method < 0 || in.method > 2) return fail(RTCC_ERR_INVALID_ARG, "unknown integrator");
+  if (in.nsteps <= 0 && !(in.t_end > 0)) return fail(RTCC_ERR_INVALID_ARG, "need nsteps > 0 or t_end > 0");
+  if (in.method == RTCC_RK4 && !(in.h > 0)) return fail(RTCC_ERR_INVALID_ARG, "h must be positive");
+  if (in.method == RTCC_MIXED_RK4 && !(in.h1 > 0 && in.h2 > 0)) return fail(RTCC_ERR_INVALID_ARG, "h1, h2 must be positive");
+  if (in.method == RTCC_CK && !(in.h > 0 && in.tol > 0 && in.safety > 0 && in.h_min > 0 && in.h_max >= in.h_min))
+    return fail(RTCC_ERR_INVALID_ARG, "bad Cash-Karp settings");
+  if (in.method == RTCC_CK && in.nsteps > 0) return fail(RTCC_ERR_INVALID_ARG, "Cash-Karp runs to t_end");
+  return guarded([&] {
+    cudaStream_t s = h->stream;
+    const int nz = h->nz;
+    const bool dev_out = is_device_ptr(t_out);
+    double* tout = dev_out ? t_out : h->alloc<double>((size_t)nz * max_out);
+    double* muout = dev_out ? mu_out : h->alloc<double>((size_t)nz * max_out * 6);
+    RTCC_CUDA(cudaMemcpyAsync(h->d_fields, fields, sizeof(rtcc_field_t) * nz, cudaMemcpyHostToDevice, s));
+    RTCC_CUDA(cudaMemsetAsync(h->ctl.status, 0, sizeof(int) * nz, s));
+    RTCC_CUDA(cudaMemsetAsync(h->ctl.steps, 0, sizeof(int) * nz, s));
+    RTCC_CUDA(cudaMemsetAsync(h->ctl.rejects, 0, sizeof(int) * nz, s));
+    RTCC_CUDA(cudaMemsetAsync(h->ctl.nout, 0, sizeof(int) * nz, s));
+    RTCC_CUDA(cudaMemsetAsync(h->ctl.counters, 0, sizeof(long long) * 4, s));
+    if (in.method == RTCC_CK) {
+      std::vector<double> h0(nz, in.h);
+      RTCC_CUDA(cudaMemcpyAsync(h->ctl.h, h0.data(), sizeof(double) * nz, cudaMemcpyHostToDevice, s));
+    }
+    const Tableau tb = (in.method == RTCC_CK) ? ck_tableau() : rk4_tableau();
+    run_dipole(h);
+    k_record<<<(nz + 127) / 128, 128, 0, s>>>(h->ctl, h->DIP, h->mu_ref[0], h->mu_ref[1], h->mu_ref[2], tout, muout,
+                                             max_out, nz, 1);
+    RTCC_CUDA(cudaGetLastError());
+    const char* ng = std::getenv("RTCC_NO_GRAPH");
+    const bool use_graph = !(ng && ng[0] == '1');
+    // first attempt eagerly (sets kernel attributes), then replay a captured graph
+    run_attempt(h, tb, in, tout, muout, max_out);
+    cudaGraphExec_t exec = nullptr;
+    if (use_graph) {
+      cudaGraph_t graph = nullptr;
+      RTCC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      try {
+        run_attempt(h, tb, in, tout, muout, max_out);
+      } catch (...) {
+        cudaStreamEndCapture(s, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        throw;
+      }
+      RTCC_CUDA(cudaStreamEndCapture(s, &graph));
+      RTCC_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+      cudaGraphDestroy(graph);
+    }
+    std::vector<int> stat(nz);
+    long long attempts = 1;
+    const long long max_attempts = (in.nsteps > 0) ? (long long)in.nsteps * 64 + 64 : (1ll << 40);
+    int check_every = 4;
+    while (true) {
+      RTCC_CUDA(cudaMemcpyAsync(stat.data(), h->ctl.status, sizeof(int) * nz, cudaMemcpyDeviceToHost, s));
+      RTCC_CUDA(cudaStreamSynchronize(s));
+      h->E->check_error();
+      bool running = false;
+      for (int z = 0; z < nz; ++z) {
+        if (stat[z] == TS_DIVERGED) throw Error(RTCC_ERR_DIVERGED, "trajectory " + std::to_string(z) + " diverged");
+        if (stat[z] == TS_UNDERFLOW)
+          throw Error(RTCC_ERR_STEP_UNDERFLOW, "trajectory " + std::to_string(z) + ": step size underflow");
+        running |= (stat[z] == TS_RUN);
+      }
+      if (!running) break;
+      if (attempts >= max_attempts) throw Error(RTCC_ERR_TIMEOUT, "attempt limit reached");
+      long long k = check_every;
+      if (in.nsteps > 0 && in.method != RTCC_CK) k = std::max(1ll, std::min<long long>(k, in.nsteps - attempts));
+      for (long long q = 0; q < k; ++q) {
+        if (exec) RTCC_CUDA(cudaGraphLaunch(exec, s));
+        else run_attempt(h, tb, in, tout, muout, max_out);
+      }
+      attempts += k;
+      check_every = std::min(check_every * 2, 64);
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    std::vector<int> nout(nz);
+    long long cnt[4];
+    RTCC_CUDA(cudaMemcpyAsync(nout.data(), h->ctl.nout, sizeof(int) * nz, cudaMemcpyDeviceToHost, s));
+    RTCC_CUDA(cudaMemcpyAsync(cnt, h->ctl.counters, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+    if (!dev_out) {
+      RTCC_CUDA(cudaMemcpyAsync(t_out, tout, sizeof(double) * nz * max_out, cudaMemcpyDeviceToHost, s));
+      RTCC_CUDA(cudaMemcpyAsync(mu_out, muout, sizeof(double) * nz * max_out * 6, cudaMemcpyDeviceToHost, s));
+    }
+    RTCC_CUDA(cudaStreamSynchronize(s));
+    for (int z = 0; z < nz; ++z) n_out[z] = nout[z];
+    h->last_stats[0] = cnt[0];
+    h->last_stats[1] = cnt[1];
+    h->last_stats[2] = (cnt[0] + cnt[1]) * tb.s;
+    if (!dev_out) {
+      // temporary device output buffers are released with the handle's allocation list
+    }
+  });
+}
+
+rtcc_status_t rtcc_last_stats(rtcc_handle_t h, long long* accepted, long long* rejected, long long* rhs_evals) {
+  if (!h) return fail(RTCC_ERR_INVALID_ARG, "null handle");
+  if (accepted) *accepted = h->last_stats[0];
+  if (rejected) *rejected = h->last_stats[1];
+  if (rhs_evals) *rhs_evals = h->last_stats[2];
+  return RTCC_OK;
+}
+
+rtcc_status_t rtcc_spectrum(const double* t, const double* mu, int n, const rtcc_field_t* field, double kappa,
+                            double gamma, double dt, const double* omega, int n_omega, double* I) {
+  if (!t || !mu || !field || !omega || !I || n < 4 || n_omega < 1) return fail(RTCC_ERR_INVALID_ARG, "bad argument");
+  for (int k = 1; k < n; ++k)
+    if (!(t[k] > t[k - 1])) return fail(RTCC_ERR_INVALID_ARG, "sample times must increase");
+  return guarded([&] {
+    bool uniform = true;
+    double hmin = t[1] - t[0];
+    for (int k = 1; k < n; ++k) {
+      const double hk = t[k] - t[k - 1];
+      hmin = std::min(hmin, hk);
+      if (std::fabs(hk - (t[1] - t[0])) > 1e-9 * std::fabs(t[1] - t[0])) uniform = false;
+    }
+    if (dt <= 0) dt = hmin;
+    cudaStream_t s;
+    RTCC_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    std::vector<void*> al;
+    auto A = [&](size_t bytes) {
+      void* p = dev_alloc(bytes);
+      al.push_back(p);
+      return static_cast<double*>(p);
+    };
+    try {
+      double* dt_ = A(sizeof(double) * n);
+      double* dy = A(sizeof(double) * 3 * n);
+      double* dw = A(sizeof(double) * n_omega);
+      double* dI = A(sizeof(double) * n_omega);
+      RTCC_CUDA(cudaMemcpyAsync(dt_, t, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+      RTCC_CUDA(cudaMemcpyAsync(dy, mu, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+      RTCC_CUDA(cudaMemcpyAsync(dw, omega, sizeof(double) * n_omega, cudaMemcpyHostToDevice, s));
+      const double* ts = dt_;
+      const double* ys = dy;
+      int nu = n;
+      double step = t[1] - t[0];
+      if (!uniform) {
+        nu = (int)std::floor((t[n - 1] - t[0]) / dt + 1e-9) + 1;
+        double* M = A(sizeof(double) * 3 * n);
+        double* cp = A(sizeof(double) * 3 * n);
+        double* dp = A(sizeof(double) * 3 * n);
+        double* tu = A(sizeof(double) * nu);
+        double* yu = A(sizeof(double) * 3 * nu);
+        k_spline_m<<<1, 32, 0, s>>>(dt_, dy, n, M, cp, dp);
+        k_spline_eval<<<blocks_for(nu), 256, 0, s>>>(dt_, dy, M, n, t[0], dt, nu, yu);
+        std::vector<double> th(nu);
+        for (int q = 0; q < nu; ++q) th[q] = t[0] + dt * q;
+        RTCC_CUDA(cudaMemcpyAsync(tu, th.data(), sizeof(double) * nu, cudaMemcpyHostToDevice, s));
+        ts = tu;
+        ys = yu;
+        step = dt;
+        RTCC_CUDA(cudaStreamSynchronize(s));
+      }
+      k_dft<<<n_omega, 256, 0, s>>>(ts, ys, nu, step, *field, kappa, gamma, dw, n_omega, dI);
+      RTCC_CUDA(cudaGetLastError());
+      RTCC_CUDA(cudaMemcpyAsync(I, dI, sizeof(double) * n_omega, cudaMemcpyDeviceToHost, s));
+      RTCC_CUDA(cudaStreamSynchronize(s));
+    } catch (...) {
+      for (void* p : al) cudaFree(p);
+      cudaStreamDestroy(s);
+      throw;
+    }
+    for (void* p : al) cudaFree(p);
+    cudaStreamDestroy(s);
+  });
+}
+
+rtcc_status_t rtcc_selftest_gemm(int prec, int batch, int M, int N, int K, const double* A, const double* Bm, double* C) {
+  if (prec < 0 || prec > 3 || batch < 1 || M < 1 || N < 1 || K < 1 || !A || !Bm || !C)
+    return fail(RTCC_ERR_INVALID_ARG, "bad argument");
+  return guarded([&] {
+    cudaStream_t s;
+    RTCC_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    std::vector<void*> al;
+    try {
+      auto Al = [&](size_t bytes) {
+        void* p = dev_alloc(bytes);
+        al.push_back(p);
+        return static_cast<double*>(p);
+      };
+      const size_t na = (size_t)batch * M * K, nb = (size_t)batch * N * K, nc = (size_t)batch * M * N;
+      double* dA = Al(na * 8);
+      double* dB = Al(nb * 8);
+      double* dC = Al(nc * 8);
+      copy_in(dA, A, na * 8, s);
+      copy_in(dB, Bm, nb * 8, s);
+      RTCC_CUDA(cudaMemsetAsync(dC, 0, nc * 8, s));
+      Engine E((Prec)prec, s);
+      E.set_force_gemm(true);
+      const int ta = E.external("A", {batch, M, K}, false, dA);
+      const int tb = E.external("B", {batch, N, K}, false, dB);
+      const int tc = E.external("C", {batch, M, N}, false, dC);
+      Program P;
+      P.name = "selftest";
+      Engine::ein(P, tc, "zmn", ta, "zmk", tb, "znk");
+      E.finalize({&P});
+      E.run(P);
+      E.check_error();
+      copy_out(C, dC, nc * 8, s);
+      RTCC_CUDA(cudaStreamSynchronize(s));
+    } catch (...) {
+      for (void* p : al) cudaFree(p);
+      cudaStreamDestroy(s);
+      throw;
+    }
+    for (void* p : al) cudaFree(p);
+    cudaStreamDestroy(s);
+  });
+}
+
+}  // extern "C"

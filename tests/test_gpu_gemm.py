@@ -1,0 +1,25 @@
+"""The packed GEMM path (tcgen05 TF32 / 3xTF32 / BF16x3, float64 SIMT) against numpy float64."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+# bound on max|C - C_ref| / (max|A| max|B| K) for each precision mode
+TOL = {0: 1e-15, 1: 2e-3, 2: 2e-6, 3: 3e-5}
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("shape", [(1, 8, 8, 4), (2, 300, 200, 77), (1, 129, 257, 130), (3, 64, 40, 1000)])
+def test_gemm_matches_float64(prec, shape):
+    from paper_2205_05175_gb300 import rtcc
+    nb, M, N, K = shape
+    rng = np.random.default_rng(1234 + M)
+    A = rng.standard_normal((nb, M, K))
+    B = rng.standard_normal((nb, N, K))
+    ref = np.einsum("bmk,bnk->bmn", A, B)
+    C = rtcc.rtcc_selftest_gemm(prec, A, B)
+    err = np.abs(C - ref).max() / (np.abs(A).max() * np.abs(B).max() * K)
+    assert err < TOL[prec], err
+    # the tensor-core modes must not be exact (they run in reduced precision on the tensor cores)
+    if prec in (1, 3) and K > 8:
+        assert np.abs(C - ref).max() > 0

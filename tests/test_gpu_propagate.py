@@ -1,0 +1,128 @@
+"""Trajectory parity (RK4, Cash-Karp, mixed-step RK4) of the CUDA path against the oracle, the
+zero-field fixed point, two-electron exactness against FCI, and batched-trajectory independence."""
+import numpy as np
+import pytest
+
+from oracle import fci, rk
+from paper_2205_05175_gb300 import synth
+from tests.gpu_common import system
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_traj(o, v, f, B, mu, fields, integ, max_out, prec=0, y0=None, tol=1e-11):
+    from paper_2205_05175_gb300 import rtcc
+    with rtcc.Handle(f, B, mu, o, v, ntraj=len(fields), prec=prec) as h:
+        if y0 is None:
+            h.ground_state(tol=tol)
+        else:
+            for z in range(len(fields)):
+                h.set_state(z, y0, 0.0, 0.0)
+        t, m, n = h.propagate(fields, integ, max_out)
+        stats = h.last_stats()
+    return t, m, n, stats
+
+
+def test_rk4_monomer_shape_matches_oracle():
+    """Config: o=5, v=19, z-polarised sine pulse E0=0.01, omega=0.5, sigma=0.5, t0=1, RK4 h=0.05, 40 steps."""
+    from paper_2205_05175_gb300 import rtcc
+    o, v = 5, 19
+    f, B, mu = system(o, v)
+    s = rk.RTCC(f, B, mu, o)
+    y0, _, _ = s.ground_state(tol=1e-11)
+    fld = rk.Field(E0=0.01, omega=0.5, sigma=0.5, t0=1.0)
+    tt, mm, _, _ = rk.propagate(s, y0, fld, rk.Integrator(method="rk4", h=0.05, nsteps=40))
+    t, m, n, _ = _gpu_traj(o, v, f, B, mu, [rtcc.make_field()], rtcc.make_integrator(rtcc.RK4, h=0.05, nsteps=40),
+                           64, prec=0, y0=y0)
+    assert n[0] == 41
+    assert np.abs(t[0, :41] - tt).max() < 1e-12
+    assert np.abs(m[0, :41] - mm).max() < 1e-10
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-4), (2, 1e-7), (3, 1e-6)])
+def test_rk4_reduced_precision_dipole_error(prec, tol):
+    from paper_2205_05175_gb300 import rtcc
+    o, v = 5, 19
+    f, B, mu = system(o, v)
+    s = rk.RTCC(f, B, mu, o)
+    y0, _, _ = s.ground_state(tol=1e-11)
+    fld = rk.Field(E0=0.01, omega=0.5, sigma=0.5, t0=1.0)
+    _, mm, _, _ = rk.propagate(s, y0, fld, rk.Integrator(method="rk4", h=0.05, nsteps=40))
+    _, m, n, _ = _gpu_traj(o, v, f, B, mu, [rtcc.make_field()], rtcc.make_integrator(rtcc.RK4, h=0.05, nsteps=40),
+                           64, prec=prec, y0=y0)
+    assert np.abs(m[0, :41] - mm).max() < tol
+
+
+def test_cash_karp_matches_oracle():
+    from paper_2205_05175_gb300 import rtcc
+    o, v = 2, 6
+    f, B, mu = system(o, v)
+    s = rk.RTCC(f, B, mu, o)
+    y0, _, _ = s.ground_state(tol=1e-11)
+    fld = rk.Field(E0=0.5, omega=0.5, sigma=0.3, t0=1.0)
+    integ = rk.Integrator(method="ck", h=0.01, tol=1e-6, t_end=2.5)
+    tt, mm, _, st = rk.propagate(s, y0, fld, integ)
+    t, m, n, stats = _gpu_traj(o, v, f, B, mu, [rtcc.make_field(E0=0.5, sigma=0.3)],
+                               rtcc.make_integrator(rtcc.CK, h=0.01, tol=1e-6, t_end=2.5), 4096, prec=0, y0=y0)
+    assert n[0] == len(tt)
+    assert stats[0] == st["accepted"] and stats[1] == st["rejected"]
+    assert np.abs(t[0, :n[0]] - tt).max() < 1e-12
+    assert np.abs(m[0, :n[0]] - mm).max() < 1e-10
+
+
+def test_mixed_step_matches_oracle():
+    from paper_2205_05175_gb300 import rtcc
+    o, v = 2, 6
+    f, B, mu = system(o, v)
+    s = rk.RTCC(f, B, mu, o)
+    y0, _, _ = s.ground_state(tol=1e-11)
+    fld = rk.Field(E0=0.5, omega=0.5, sigma=0.3, t0=1.8)
+    integ = rk.Integrator(method="mixed", h1=0.005, h2=0.05, t_switch=3.6, t_end=4.0)
+    tt, mm, _, _ = rk.propagate(s, y0, fld, integ)
+    t, m, n, _ = _gpu_traj(o, v, f, B, mu, [rtcc.make_field(E0=0.5, sigma=0.3, t0=1.8)],
+                           rtcc.make_integrator(rtcc.MIXED_RK4, h1=0.005, h2=0.05, t_switch=3.6, t_end=4.0),
+                           4096, prec=0, y0=y0)
+    assert n[0] == len(tt)
+    assert np.abs(t[0, :n[0]] - tt).max() < 1e-12
+    assert np.abs(m[0, :n[0]] - mm).max() < 1e-10
+
+
+def test_zero_field_fixed_point_on_device():
+    from paper_2205_05175_gb300 import rtcc
+    o, v = 5, 19
+    f, B, mu = system(o, v)
+    t, m, n, _ = _gpu_traj(o, v, f, B, mu, [rtcc.make_field(E0=0.0)], rtcc.make_integrator(rtcc.RK4, h=0.05, nsteps=40),
+                           64, prec=0, tol=1e-12)
+    assert np.abs(m[0, :n[0]] - m[0, 0]).max() < 1e-10
+
+
+def test_two_electron_dipole_follows_fci_on_device():
+    from paper_2205_05175_gb300 import rtcc
+    o, v = 1, 4
+    f, B, mu = synth.make_system(o, v, seed=5)
+    F = fci.FCI(f, B, mu, o)
+    _, psi0, _, _ = F.ground()
+    fld = rk.Field(E0=0.05, omega=0.5, sigma=0.5, t0=1.0)
+    _, mf = F.propagate(psi0, fld, 2.0, 1e-4, 1000)
+    errs = []
+    for hh in (0.1, 0.05):
+        t, m, n, _ = _gpu_traj(o, v, f, B, mu, [rtcc.make_field(E0=0.05)],
+                               rtcc.make_integrator(rtcc.RK4, h=hh, nsteps=int(round(2.0 / hh))), 64, prec=0)
+        errs.append(np.abs(m[0, n[0] - 1] - mf[-1]).max())
+        assert np.abs(m[0, n[0] - 1].imag).max() < 1e-8
+    assert errs[1] < 1e-6 and 10 < errs[0] / errs[1] < 25
+
+
+def test_batched_trajectories_are_independent():
+    """x/y/z polarisations in one batch equal three single-trajectory runs."""
+    from paper_2205_05175_gb300 import rtcc
+    o, v = 3, 8
+    f, B, mu = system(o, v)
+    pols = [(1.0, 0, 0), (0, 1.0, 0), (0, 0, 1.0)]
+    integ = rtcc.make_integrator(rtcc.RK4, h=0.05, nsteps=20)
+    fields = [rtcc.make_field(E0=0.05, pol=p) for p in pols]
+    _, mb, nb, _ = _gpu_traj(o, v, f, B, mu, fields, integ, 32, prec=0)
+    for z in range(3):
+        _, ms, ns, _ = _gpu_traj(o, v, f, B, mu, [fields[z]], integ, 32, prec=0)
+        assert nb[z] == ns[0] == 21
+        assert np.abs(mb[z, :21] - ms[0, :21]).max() < 1e-12
