@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Benchmark of the batched RT-CCSD hot path on GB300.
+
+Workload (default): water-hexamer-shaped closed-shell system, o=30 occupied and v=114
+virtual orbitals, naux=576, seeded synthetic integrals; 12 trajectories sharing one
+integral set (x/y/z polarisation x E0 in {0.001, 0.01, 0.05, 0.1} au, sine pulse
+omega=0.5, sigma=0.5, t0=1), each with its own Cash-Karp step size (tol 1e-6, h0=0.01),
+starting from the field-free CCSD/Lambda ground state.  One "step" is one accepted
+Cash-Karp step of one trajectory (six right-hand-side evaluations of the T and Lambda
+equations, the fifth-order combination, the error estimate, the controller and the
+dipole); rejected attempts are part of the timed work.
+
+value  = trajectory-steps per second, all GPUs (inputs resident in HBM).
+e2e    = the same through the public C-ABI with the initial states copied from pinned
+         host memory and the dipole samples copied back inside the timed region.
+The reference arm (--impl reference) times the CPU oracle on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RT-CCSD steps/s at o=30,v=114; tensor-pipe % of peak; max |dmu(t)| vs FP64"
+UNIT = "trajectory-steps/s"
+WORKLOAD = "water-hexamer-shaped RT-CCSD, o=30 v=114 naux=576, 12 Cash-Karp trajectories (tol 1e-6)"
+E0S = (0.001, 0.01, 0.05, 0.1)
+POLS = ((1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0))
+NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25      # dense tensor-core rate ratio (nominal)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reduce_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("bf16_tflops_sustained", 1700.0), "measured"
+    return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and parts[1].isdigit():
+                    rows.append(parts)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [int(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": int(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+# --- CPU oracle timing (reference arm and cpu_baseline) ------------------------------
+
+def oracle_sample(o=30, v=114, repeats=1):
+    """Time the oracle on a bounded sample of the workload: one T-residual evaluation of one
+    trajectory at the full shape, scaled to a full right-hand side by the RHS / T-residual cost
+    ratio measured at the dimer shape, and to a Cash-Karp step by its six evaluations."""
+    import numpy as np
+
+    from oracle import closed, rk
+    from paper_2205_05175_gb300 import synth
+    # ratio at the dimer shape
+    f, B, mu = synth.make_system(10, 38)
+    s = rk.RTCC(f, B, mu, 10)
+    t1, t2 = synth.random_amplitudes(10, 38, seed=1, s1=0.01, s2=0.005)
+    l1, l2 = synth.random_amplitudes(10, 38, seed=2, s1=0.01, s2=0.005)
+    closed.omega(t1, t2, s.f, s.V)
+    a = time.perf_counter()
+    closed.omega(t1, t2, s.f, s.V)
+    tom = time.perf_counter() - a
+    a = time.perf_counter()
+    closed.rhs(t1, t2, l1, l2, s.f, s.V)
+    trhs = time.perf_counter() - a
+    ratio = trhs / tom
+    f, B, mu = synth.make_system(o, v)
+    s = rk.RTCC(f, B, mu, o)
+    t1, t2 = synth.random_amplitudes(o, v, seed=1, s1=0.01, s2=0.005)
+    for blk in ("vvvv", "ovvv", "oovv", "ovvo", "ovov", "ooov", "oovo", "oooo", "ovoo", "vvvo"):
+        s.V(blk)
+    times = []
+    for _ in range(repeats):
+        a = time.perf_counter()
+        closed.omega(t1, t2, s.f, s.V)
+        times.append(time.perf_counter() - a)
+    t_step = min(times) * ratio * 6.0
+    return {"value": 1.0 / t_step, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"one T-residual evaluation of one trajectory at o={o},v={v} ({min(times):.1f} s, "
+                       f"min of {repeats}) x RHS/T-residual ratio {ratio:.2f} (measured at o=10,v=38) x 6 "
+                       f"right-hand sides per Cash-Karp step; numpy float64/complex128, BLAS threads = all cores")}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    steps = max(1, min(args.steps, 4))
+    t0 = time.perf_counter()
+    r = oracle_sample(repeats=steps)
+    wall = time.perf_counter() - t0
+    line = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": 0, "ms_per_step": 1e3 / r["value"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": r["sample"]},
+            "cpu_baseline": {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --- GPU arm -------------------------------------------------------------------------
+
+def dipole_error(prec: int, o=10, v=38, nsteps=50, h=0.02):
+    """max |mu_prec(t) - mu_f64(t)| over an RK4 segment of the dimer-shaped system (both on the GPU)."""
+    import numpy as np
+
+    from paper_2205_05175_gb300 import rtcc, synth
+    f, B, mu = synth.make_system(o, v)
+    out = {}
+    for p in (rtcc.P64, prec):
+        with rtcc.Handle(f, B, mu, o, v, ntraj=1, prec=p) as H:
+            H.ground_state(tol=1e-10)
+            _, m, n = H.propagate([rtcc.make_field(E0=0.01)], rtcc.make_integrator(rtcc.RK4, h=h, nsteps=nsteps),
+                                  nsteps + 1)
+            out[p] = m[0, :n[0]]
+    return float(np.abs(out[prec] - out[rtcc.P64]).max())
+
+
+def run_gpu(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_2205_05175_gb300 import rtcc, synth
+    torch.cuda.set_device(local)
+    prec = rtcc.PRECISIONS[args.prec]
+    o, v = args.o, args.v
+    fields = [rtcc.make_field(E0=e, omega=0.5, sigma=0.5, t0=1.0, pol=p) for p in POLS for e in E0S]
+    nz = len(fields)
+    f, B, mu = synth.make_system(o, v)
+    t_setup = time.perf_counter()
+    H = rtcc.Handle(f, B, mu, o, v, ntraj=nz, prec=prec)
+    ecorr, mu0 = H.ground_state(tol=args.gs_tol, maxiter=300)
+    t_setup = time.perf_counter() - t_setup
+    y0 = np.stack([H.get_state(z)[0] for z in range(nz)])
+    integ = rtcc.make_integrator(rtcc.CK, h=0.01, tol=1e-6, nsteps=args.warmup)
+    max_out = args.steps + args.warmup + 2
+    tout = torch.zeros((nz, max_out), dtype=torch.float64, device="cuda")
+    mout = torch.zeros((nz, max_out, 3, 2), dtype=torch.float64, device="cuda")
+    # warm-up: W accepted steps per trajectory (continues from the ground state)
+    H.propagate(fields, integ, max_out, tout, mout)
+    torch.cuda.synchronize()
+    # timed region: K accepted Cash-Karp steps of every trajectory, every launch timed by CUDA events
+    integ = rtcc.make_integrator(rtcc.CK, h=0.01, tol=1e-6, nsteps=args.steps)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        H.profile_start()
+        ev0.record()
+        H.propagate(fields, integ, max_out, tout, mout)
+        ev1.record()
+        torch.cuda.synchronize()
+        prof = H.profile_stop()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    acc, rej, nrhs, launches = H.last_stats()
+    ms_max = reduce_max(ms, world)
+    value = world * acc / (ms_max / 1e3)
+    # dominant kernel (largest total device time in the timed region)
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    hbm, bf16, bf16_sus, src = measured_peaks()
+    if dom in ("tc_gemm", "f64_gemm"):
+        peak = bf16_sus if prec == rtcc.P32_BF16X3 else bf16_sus * NOMINAL_TF32_OVER_BF16
+        roof = {"bound": "tensor", "achieved": d["flops"] / (d["ms"] / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s"}
+        if dom == "f64_gemm":
+            roof["bound"] = "alu"
+    else:
+        roof = {"bound": "hbm", "achieved": d["bytes"] / (d["ms"] / 1e3) / 1e9, "peak": hbm, "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = dom
+    roof["launches"] = d["launches"]
+    roof["avg_launch_ms"] = d["ms"] / max(1, d["launches"])
+    roof["peak_source"] = f"{src} (bf16 sustained{'' if prec == rtcc.P32_BF16X3 else ' x nominal tf32/bf16 ratio 0.49'})"
+    share = {k: round(prof[k]["ms"] / max(1e-9, sum(p["ms"] for p in prof.values())), 4) for k in prof}
+    # end to end: initial states from pinned host memory, dipoles back to the host, inside the timed region
+    yh = torch.from_numpy(y0.view(np.float64).copy()).pin_memory()
+    th = np.zeros((nz, max_out))
+    mh = np.zeros((nz, max_out, 3), complex)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for z in range(nz):
+        H.set_state(z, yh[z].numpy().view(np.complex128), 0.0, 0.0)
+    H.propagate(fields, integ, max_out, th, mh)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_e2e = reduce_max(e0.elapsed_time(e1), world)
+    acc_e2e = H.last_stats()[0]
+    h2d = yh.numel() * 8 / max(1, acc_e2e)
+    d2h = (th.nbytes + mh.nbytes) / max(1, acc_e2e)
+    H.close()
+    line = None
+    if rank == 0:
+        derr = dipole_error(prec) if not args.skip_dipole_error else None
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / max(1, acc / nz), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+                "config": {"workload": WORKLOAD, "o": o, "v": v, "naux": 4 * (o + v), "trajectories_per_gpu": nz,
+                           "precision": args.prec, "accepted_steps": acc, "rejected_attempts": rej,
+                           "rhs_evaluations": nrhs, "l2": "inputs larger than L2 (state 4.5 GB, vvvv 1.35 GB)",
+                           "parallelism": f"replicas x{world}", "ground_state_setup_s": round(t_setup, 2),
+                           "e_corr": ecorr},
+                "roofline": roof, "kernel_share": share,
+                "e2e": {"value": world * acc_e2e / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "clocks": clk.summary(),
+                "dipole_error_vs_f64": {"value": derr, "unit": "au",
+                                        "config": "o=10,v=38, RK4 h=0.02, 50 steps, E0=0.01 z sine pulse"}}
+        if not args.skip_cpu_baseline and world == 1:
+            line["cpu_baseline"] = oracle_sample(repeats=1)
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="bf16x3", choices=["p64", "tf32", "3xtf32", "bf16x3"])
+    ap.add_argument("--o", type=int, default=30)
+    ap.add_argument("--v", type=int, default=114)
+    ap.add_argument("--gs-tol", type=float, default=1e-8)
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-dipole-error", action="store_true")
+    args = ap.parse_args(argv)
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    try:
+        if args.impl == "reference":
+            return run_reference(args, rank, world)
+        return run_gpu(args, rank, world, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

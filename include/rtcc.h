@@ -158,9 +158,27 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields,
                              double* t_out, double* mu_out, int* n_out);
 
 /* Counters of the last rtcc_propagate: accepted steps, rejected attempts and
- * right-hand-side evaluations summed over trajectories (host, may be null). */
+ * right-hand-side evaluations summed over trajectories, and the number of kernels the
+ * library launched (host, each may be null). */
 rtcc_status_t rtcc_last_stats(rtcc_handle_t h, long long* accepted, long long* rejected,
-                              long long* rhs_evals);
+                              long long* rhs_evals, long long* launches);
+
+/* Launch profile (Sec. 4.3 reports time per step; this splits it by kernel class).
+ * Class index: 0 tcgen05 GEMM, 1 float64 GEMM, 2 pack, 3 unpack, 4 direct contraction,
+ * 5 split-K reduction, 6 add/permute, 7 Runge-Kutta/field/controller kernels.
+ * flops: algorithmic real flops of the launches (GEMMs: 2 x rows x cols x unpadded K of the
+ * packed product); bytes: algorithmic bytes moved (memory-bound classes). */
+typedef struct {
+    long long launches[8];
+    double ms[8];
+    double flops[8];
+    double bytes[8];
+} rtcc_profile_t;
+
+/* enable = 1: start timing every library launch of this handle with CUDA events on its
+ * stream (rtcc_propagate then runs without CUDA-graph replay).  enable = 0: stop, wait for
+ * the recorded events and write the per-class totals since the start into *out (may be null). */
+rtcc_status_t rtcc_profile(rtcc_handle_t h, int enable, rtcc_profile_t* out);
 
 /* Absorption spectrum (Sec. 2.2: I(w) = Im Tr alpha(w); Sec. 4.2: non-uniform samples
  * are interpolated onto a uniform grid).  Runs on the current CUDA device.

@@ -56,6 +56,53 @@ struct Compiled {
   long long exec_flops = 0;   // flops issued by the GEMM kernel (passes and padding included)
 };
 
+Profiler::~Profiler() {
+  for (cudaEvent_t e : pool_) cudaEventDestroy(e);
+}
+void Profiler::begin() {
+  on_ = true;
+  used_ = 0;
+  recs_.clear();
+}
+cudaEvent_t Profiler::get() {
+  if (used_ == pool_.size()) {
+    cudaEvent_t e;
+    RTCC_CUDA(cudaEventCreate(&e));
+    pool_.push_back(e);
+  }
+  return pool_[used_++];
+}
+void Profiler::start(cudaStream_t s) {
+  if (!on_) return;
+  pending_ = (int)used_;
+  RTCC_CUDA(cudaEventRecord(get(), s));
+}
+void Profiler::stop(cudaStream_t s, int cls, double flops, double bytes) {
+  ++count[cls];
+  if (!on_) return;
+  const int b = (int)used_;
+  RTCC_CUDA(cudaEventRecord(get(), s));
+  recs_.push_back(Rec{cls, pending_, b, flops, bytes});
+}
+void Profiler::end(long long launches[KC_N], double ms[KC_N], double flops[KC_N], double bytes[KC_N]) {
+  for (int c = 0; c < KC_N; ++c) {
+    launches[c] = 0;
+    ms[c] = flops[c] = bytes[c] = 0.0;
+  }
+  if (!recs_.empty()) RTCC_CUDA(cudaEventSynchronize(pool_[recs_.back().b]));
+  for (const Rec& r : recs_) {
+    float t = 0.f;
+    RTCC_CUDA(cudaEventElapsedTime(&t, pool_[r.a], pool_[r.b]));
+    launches[r.cls] += 1;
+    ms[r.cls] += t;
+    flops[r.cls] += r.flops;
+    bytes[r.cls] += r.bytes;
+  }
+  on_ = false;
+  recs_.clear();
+  used_ = 0;
+}
+
 void* dev_alloc(size_t bytes) {
   void* p = nullptr;
   if (bytes == 0) bytes = 16;
@@ -479,20 +526,54 @@ void Engine::run(const Program& P) {
     RTCC_CUDA(cudaMemsetAsync(x.ptr, 0, (size_t)x.numel() * (x.cplx ? 16 : 8), stream_));
   }
   for (const auto& z : P.zero2d) RTCC_CUDA(cudaMemset2DAsync(z.ptr, z.pitch, 0, z.width, z.height, stream_));
+  Profiler dummy;
+  Profiler& pr = prof_ ? *prof_ : dummy;
   for (const auto& cp : P.comp) {
     const Compiled& k = *cp;
     switch (k.kind) {
-      case CK_ADD: launch_add(k.add, stream_); break;
-      case CK_DIRECT: launch_direct(k.dir, stream_); break;
-      case CK_REDUCE: launch_reduce(k.dir, k.splits, stream_); break;
-      default:
-        if (!k.a_const) launch_pack(k.pa, stream_);
-        if (!k.b_const) launch_pack(k.pb, stream_);
+      case CK_ADD:
+        pr.start(stream_);
+        launch_add(k.add, stream_);
+        pr.stop(stream_, KC_ADD, 0.0, (double)k.add.n * ((k.add.a_cplx ? 16 : 8) + 2 * (k.add.c_cplx ? 16 : 8)));
+        break;
+      case CK_DIRECT:
+        pr.start(stream_);
+        launch_direct(k.dir, stream_);
+        pr.stop(stream_, KC_DIRECT, (double)k.alg_flops, 0.0);
+        break;
+      case CK_REDUCE:
+        pr.start(stream_);
+        launch_reduce(k.dir, k.splits, stream_);
+        pr.stop(stream_, KC_REDUCE, (double)k.alg_flops, 0.0);
+        break;
+      default: {
+        const double esz = (k.pa.elem == PE_F64) ? 8 : (k.pa.elem == PE_F32 ? 4 : 2);
+        if (!k.a_const) {
+          pr.start(stream_);
+          launch_pack(k.pa, stream_);
+          pr.stop(stream_, KC_PACK, 0.0,
+                  (double)k.NB * k.pa.R * k.pa.K * (k.pa.src_cplx ? 16 : 8) + (double)k.NB * k.GM * k.Kpad * esz);
+        }
+        if (!k.b_const) {
+          pr.start(stream_);
+          launch_pack(k.pb, stream_);
+          pr.stop(stream_, KC_PACK, 0.0,
+                  (double)k.NB * k.pb.R * k.pb.K * (k.pb.src_cplx ? 16 : 8) + (double)k.NB * k.GN * k.Kpad * esz);
+        }
+        // kernel-level algorithmic flops: the real multiply-adds of the packed product without padding
+        const double kflops = 2.0 * k.NB * k.GM * k.GN * (double)(k.pa.nss * k.pa.ncs * k.pa.K);
+        pr.start(stream_);
         if (k.tc_kind >= 0) launch_tc_gemm(k.tcp, stream_);
         else
           launch_gemm_f64(static_cast<const double*>(k.pa.dst), static_cast<const double*>(k.pb.dst),
                           static_cast<double*>(wsC_), k.GM, k.GN, k.Kpad, k.NB, stream_);
+        pr.stop(stream_, k.tc_kind >= 0 ? KC_TC_GEMM : KC_F64_GEMM, kflops,
+                (double)k.NB * (k.GM + k.GN) * k.Kpad * esz + (double)k.NB * k.GM * k.GN * (k.tc_kind >= 0 ? 4 : 8));
+        pr.start(stream_);
         launch_unpack(k.up, stream_);
+        pr.stop(stream_, KC_UNPACK, 0.0,
+                (double)k.NB * k.GM * k.GN * (k.tc_kind >= 0 ? 4 : 8) + 2.0 * k.NB * k.up.M * k.up.N * (k.up.c_cplx ? 16 : 8));
+      }
     }
   }
 }

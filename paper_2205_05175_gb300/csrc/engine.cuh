@@ -55,6 +55,31 @@ struct Program {
   std::vector<std::shared_ptr<Compiled>> comp;
 };
 
+// Kernel classes of the launch profile (rtcc_profile_t in include/rtcc.h uses the same order).
+enum KClass : int { KC_TC_GEMM = 0, KC_F64_GEMM = 1, KC_PACK = 2, KC_UNPACK = 3, KC_DIRECT = 4, KC_REDUCE = 5,
+                    KC_ADD = 6, KC_RK = 7, KC_N = 8 };
+
+// Optional CUDA-event timing of every launch (eager execution only).
+class Profiler {
+ public:
+  ~Profiler();
+  void begin();
+  bool on() const { return on_; }
+  void start(cudaStream_t s);
+  void stop(cudaStream_t s, int cls, double flops, double bytes);
+  // synchronises, accumulates per class and turns profiling off
+  void end(long long launches[KC_N], double ms[KC_N], double flops[KC_N], double bytes[KC_N]);
+  long long count[KC_N] = {0};   // launches per class, counted whether or not timing is on
+ private:
+  struct Rec { int cls; int a, b; double flops, bytes; };
+  cudaEvent_t get();
+  bool on_ = false;
+  std::vector<cudaEvent_t> pool_;
+  size_t used_ = 0;
+  std::vector<Rec> recs_;
+  int pending_ = -1;
+};
+
 struct EngineStats {
   long long gemm_flops = 0;   // real multiply-adds x2 issued on the GEMM path per run (all programs)
   long long direct_flops = 0;
@@ -103,6 +128,7 @@ class Engine {
   void finalize(std::vector<Program*> progs);
 
   void run(const Program& P);
+  void set_profiler(Profiler* p) { prof_ = p; }
   EngineStats stats_of(const Program& P) const;
   void check_error();   // throws on a device-side timeout recorded by a kernel
   size_t device_bytes() const { return bytes_; }
@@ -126,6 +152,7 @@ class Engine {
   size_t bytes_ = 0;
   bool finalized_ = false;
   bool force_gemm_ = false;
+  Profiler* prof_ = nullptr;
 };
 
 // Allocation helper that records ownership (freed with the engine).

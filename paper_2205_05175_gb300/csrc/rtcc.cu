@@ -438,6 +438,8 @@ struct GroundEngine {
   RhsPrograms rhs;
   Program energy;
   double *Y = nullptr, *R = nullptr, *F = nullptr, *Ec = nullptr;
+  double *hx = nullptr, *he = nullptr, *dots = nullptr;   // DIIS history (one amplitude block)
+  unsigned long long* scratch = nullptr;
 };
 
 struct rtcc_ctx {
@@ -457,10 +459,11 @@ struct rtcc_ctx {
   rtcc_field_t* d_fields = nullptr;
   Ctl ctl{};
   std::vector<void*> allocs;
-  std::unique_ptr<GroundEngine> gs;
-  long long last_stats[3] = {0, 0, 0};
+  std::unique_ptr<GroundEngine> gs[4];   // per precision, one trajectory
+  long long last_stats[4] = {0, 0, 0, 0};
+  Profiler prof;
   ~rtcc_ctx() {
-    gs.reset();
+    for (auto& g : gs) g.reset();
     E.reset();
     ints.reset();
     for (void* p : allocs) cudaFree(p);
@@ -508,10 +511,14 @@ void run_dipole(rtcc_ctx* h) {
 // One Runge-Kutta attempt over all trajectories (stages, combination, controller, accept, dipole, record).
 void run_attempt(rtcc_ctx* h, const Tableau& tb, const rtcc_integrator_t& in, double* tout, double* muout, int max_out) {
   cudaStream_t s = h->stream;
+  Profiler& pr = h->prof;
   const int nz = h->nz;
   const long long ns = h->ns, nT = h->nT;
+  const double sb = 16.0 * (double)ns * nz;   // bytes of one state-sized complex buffer
   const dim3 gst(blocks_for(ns) / nz + 1 > 4096 ? 4096 : blocks_for(ns) / nz + 1, nz);
+  pr.start(s);
   k_prestep<<<(nz + 127) / 128, 128, 0, s>>>(h->ctl, in, nz);
+  pr.stop(s, KC_RK, 0, 0);
   for (int st = 0; st < tb.s; ++st) {
     StageArgs A{};
     A.nterms = 0;
@@ -525,9 +532,13 @@ void run_attempt(rtcc_ctx* h, const Tableau& tb, const rtcc_integrator_t& in, do
       A.copy_src = h->Rout;
       A.copy_dst = h->Rk[st - 1];
     }
+    pr.start(s);
     k_stage<<<gst, 256, 0, s>>>(h->Ys, h->Y, A, h->ctl.htry, ns, nT);
+    pr.stop(s, KC_RK, 0, sb * (A.nterms + 2 + (st > 0 ? 1 : 0)));
+    pr.start(s);
     k_fock<<<dim3(blocks_for((long long)h->nmo * h->nmo), nz), 256, 0, s>>>(h->F, h->f0, h->mu, h->d_fields, h->ctl.t,
                                                                            h->ctl.htry, tb.c[st], nz, h->nmo * h->nmo);
+    pr.stop(s, KC_RK, 0, 8.0 * h->nmo * h->nmo * (4 + nz));
     h->E->run(h->rhs.fwd);
     h->E->run(h->rhs.rev);
   }
@@ -538,31 +549,52 @@ void run_attempt(rtcc_ctx* h, const Tableau& tb, const rtcc_integrator_t& in, do
     Ew.coef[j] = tb.e[j];
   }
   B.nterms = tb.s;
+  pr.start(s);
   k_final<<<gst, 256, 0, s>>>(h->Ynew, h->Y, B, Ew, h->ctl.htry, ns, nT, h->ctl.err_bits, tb.adaptive ? 1 : 0);
+  pr.stop(s, KC_RK, 0, sb * (tb.s + 2));
+  pr.start(s);
   k_controller<<<(nz + 127) / 128, 128, 0, s>>>(h->ctl, in, nz);
+  pr.stop(s, KC_RK, 0, 0);
+  pr.start(s);
   k_accept<<<gst, 256, 0, s>>>(h->Y, h->Ynew, h->ctl.accepted, ns);
+  pr.stop(s, KC_RK, 0, 2 * sb);
   run_dipole(h);
+  pr.start(s);
   k_record<<<(nz + 127) / 128, 128, 0, s>>>(h->ctl, h->DIP, h->mu_ref[0], h->mu_ref[1], h->mu_ref[2], tout, muout, max_out,
                                             nz, 0);
+  pr.stop(s, KC_RK, 0, 0);
   RTCC_CUDA(cudaGetLastError());
 }
 
-GroundEngine* ground_engine(rtcc_ctx* h) {
-  if (h->gs) return h->gs.get();
+long long total_count(const Profiler& p) {
+  long long c = 0;
+  for (int k = 0; k < KC_N; ++k) c += p.count[k];
+  return c;
+}
+
+constexpr int kDiis = 8;
+
+GroundEngine* ground_engine(rtcc_ctx* h, Prec p) {
+  auto& slot = h->gs[(int)p];
+  if (slot) return slot.get();
   auto g = std::make_unique<GroundEngine>();
-  g->E = std::make_unique<Engine>(Prec::P64, h->stream);
+  g->E = std::make_unique<Engine>(p, h->stream);
   Engine& E = *g->E;
   const IntIds I = register_integrals(E, *h->ints);
   g->Y = h->alloc<double>(2 * h->ns);
   g->R = h->alloc<double>(2 * h->ns);
   g->F = h->alloc<double>((size_t)h->nmo * h->nmo);
   g->Ec = h->alloc<double>(2);
+  g->hx = h->alloc<double>((size_t)2 * h->nT * kDiis);
+  g->he = h->alloc<double>((size_t)2 * h->nT * kDiis);
+  g->dots = h->alloc<double>(kDiis);
+  g->scratch = h->alloc<unsigned long long>(1);
   RTCC_CUDA(cudaMemcpyAsync(g->F, h->f0, sizeof(double) * h->nmo * h->nmo, cudaMemcpyDeviceToDevice, h->stream));
   g->rhs = build_rhs(E, I, 1, h->o, h->v, g->Y, g->F, g->R, true);
   g->energy = build_energy(E, I, g->rhs, 1, h->o, h->v, g->F, g->Ec);
   E.finalize({&g->rhs.fwd, &g->rhs.rev, &g->energy});
-  h->gs = std::move(g);
-  return h->gs.get();
+  slot = std::move(g);
+  return slot.get();
 }
 
 double read_max(rtcc_ctx* h, const double* r, long long n, unsigned long long* scratch) {
@@ -576,45 +608,49 @@ double read_max(rtcc_ctx* h, const double* r, long long n, unsigned long long* s
   return m;
 }
 
-// Jacobi + DIIS on one amplitude block (T or Lambda) of the ground-state engine.
-void solve_block(rtcc_ctx* h, GroundEngine* g, bool lambda, double tol, int maxiter) {
+// Jacobi + DIIS on one amplitude block (T or Lambda) of a ground-state engine.  Returns the final
+// max-abs residual.  With `floor_ok` the iteration also stops (without error) once the residual
+// has not improved for 10 iterations: the rounding floor of a reduced-precision engine.
+double solve_block(rtcc_ctx* h, GroundEngine* g, bool lambda, double tol, int maxiter, bool floor_ok) {
   const long long nT = h->nT;
   double* x = g->Y + (lambda ? 2 * nT : 0);
   double* r = g->R + (lambda ? 2 * nT : 0);
-  const int ndiis = 8;
-  double* hx = h->alloc<double>((size_t)2 * nT * ndiis);
-  double* he = h->alloc<double>((size_t)2 * nT * ndiis);
-  double* dots = h->alloc<double>(ndiis * ndiis);
-  unsigned long long* scratch = h->alloc<unsigned long long>(1);
-  std::vector<int> slot_age;
   int count = 0;
-  double Bm[ndiis][ndiis] = {};
+  double Bm[kDiis][kDiis] = {};
+  double best = INFINITY;
+  int since_best = 0;
   if (lambda) g->E->run(g->rhs.fwd);   // intermediates of the converged t stay valid
   for (int it = 0; it < maxiter; ++it) {
     if (lambda) g->E->run(g->rhs.rev);
     else g->E->run(g->rhs.fwd);
-    const double err = read_max(h, r, nT, scratch);
+    const double err = read_max(h, r, nT, g->scratch);
     if (!std::isfinite(err)) throw Error(RTCC_ERR_DIVERGED, "ground-state residual is not finite");
-    if (err < tol) return;
-    const int slot = count % ndiis;
-    double* xs = hx + (size_t)2 * nT * slot;
-    double* es = he + (size_t)2 * nT * slot;
+    if (err < tol) return err;
+    if (err < 0.999 * best) {
+      best = err;
+      since_best = 0;
+    } else if (floor_ok && ++since_best >= 10) {
+      return err;
+    }
+    const int slot = count % kDiis;
+    double* xs = g->hx + (size_t)2 * nT * slot;
+    double* es = g->he + (size_t)2 * nT * slot;
     k_jacobi<<<blocks_for(nT), 256, 0, h->stream>>>(x, r, h->f0, h->o, h->v, h->nmo, es);
     RTCC_CUDA(cudaMemcpyAsync(xs, x, sizeof(double) * 2 * nT, cudaMemcpyDeviceToDevice, h->stream));
     ++count;
-    const int m = std::min(count, ndiis);
-    // refresh the row/column of the new slot
-    RTCC_CUDA(cudaMemsetAsync(dots, 0, sizeof(double) * ndiis, h->stream));
+    const int m = std::min(count, kDiis);
+    RTCC_CUDA(cudaMemsetAsync(g->dots, 0, sizeof(double) * kDiis, h->stream));
     for (int j = 0; j < m; ++j)
-      k_dot<<<blocks_for(nT), 256, 0, h->stream>>>(es, he + (size_t)2 * nT * j, nT, dots + j);
-    double row[ndiis];
-    RTCC_CUDA(cudaMemcpyAsync(row, dots, sizeof(double) * ndiis, cudaMemcpyDeviceToHost, h->stream));
+      k_dot<<<blocks_for(nT), 256, 0, h->stream>>>(es, g->he + (size_t)2 * nT * j, nT, g->dots + j);
+    double row[kDiis];
+    RTCC_CUDA(cudaMemcpyAsync(row, g->dots, sizeof(double) * kDiis, cudaMemcpyDeviceToHost, h->stream));
     RTCC_CUDA(cudaStreamSynchronize(h->stream));
     for (int j = 0; j < m; ++j) Bm[slot][j] = Bm[j][slot] = row[j];
     if (m >= 3) {
-      // solve [B 1; 1 0][c; l] = [0; 1] (Gaussian elimination with partial pivoting, m+1 <= 9)
+      // DIIS: minimise |sum c_j e_j| with sum c_j = 1, i.e. [B -1; -1 0][c; l] = [0; -1]
+      // (Gauss-Jordan elimination with partial pivoting on the (m+1) x (m+1) system)
       const int N = m + 1;
-      double A[ndiis + 1][ndiis + 2] = {};
+      double A[kDiis + 1][kDiis + 2] = {};
       for (int i = 0; i < m; ++i) {
         for (int j = 0; j < m; ++j) A[i][j] = Bm[i][j];
         A[i][m] = -1.0;
@@ -626,7 +662,10 @@ void solve_block(rtcc_ctx* h, GroundEngine* g, bool lambda, double tol, int maxi
         int p = c;
         for (int i = c + 1; i < N; ++i)
           if (std::fabs(A[i][c]) > std::fabs(A[p][c])) p = i;
-        if (std::fabs(A[p][c]) < 1e-300) { ok = false; break; }
+        if (std::fabs(A[p][c]) < 1e-300) {
+          ok = false;
+          break;
+        }
         for (int j = 0; j <= N; ++j) std::swap(A[c][j], A[p][j]);
         for (int i = 0; i < N; ++i) {
           if (i == c) continue;
@@ -638,7 +677,7 @@ void solve_block(rtcc_ctx* h, GroundEngine* g, bool lambda, double tol, int maxi
         Combo C{};
         C.m = m;
         for (int j = 0; j < m; ++j) {
-          C.x[j] = hx + (size_t)2 * nT * j;
+          C.x[j] = g->hx + (size_t)2 * nT * j;
           C.c[j] = A[j][N] / A[j][j];
         }
         k_combine<<<blocks_for(2 * nT), 256, 0, h->stream>>>(x, C, nT);
@@ -646,6 +685,7 @@ void solve_block(rtcc_ctx* h, GroundEngine* g, bool lambda, double tol, int maxi
     }
     k_sym_pair<<<blocks_for(nT), 256, 0, h->stream>>>(x + 2ll * h->o * h->v, h->o, h->v);
   }
+  if (floor_ok) return best;
   throw Error(RTCC_ERR_NOCONV, std::string("ground-state ") + (lambda ? "Lambda" : "T") + " equations did not converge");
 }
 
@@ -728,6 +768,7 @@ rtcc_status_t rtcc_create(const double* f, const double* B, int naux, const doub
     h->rhs = build_rhs(*h->E, I, h->nz, o, v, h->Ys, h->F, h->Rout, true);
     h->dip = build_dipole(*h->E, h->nz, o, v, h->Y, h->mu, h->DIP);
     h->E->finalize({&h->rhs.fwd, &h->rhs.rev, &h->dip.prog[0], &h->dip.prog[1], &h->dip.prog[2]});
+    h->E->set_profiler(&h->prof);
     RTCC_CUDA(cudaStreamSynchronize(h->stream));
   });
   if (st != RTCC_OK) {
@@ -816,10 +857,18 @@ rtcc_status_t rtcc_dipole(rtcc_handle_t h, double* mu_out) {
 rtcc_status_t rtcc_ground_state(rtcc_handle_t h, double tol, int maxiter, double* e_corr, double* mu0) {
   if (!h || tol <= 0 || maxiter < 1) return fail(RTCC_ERR_INVALID_ARG, "bad argument");
   return guarded([&] {
-    GroundEngine* g = ground_engine(h);
+    GroundEngine* g = ground_engine(h, Prec::P64);
     RTCC_CUDA(cudaMemsetAsync(g->Y, 0, sizeof(double) * 2 * h->ns, h->stream));
-    solve_block(h, g, false, tol, maxiter);
-    solve_block(h, g, true, tol, maxiter);
+    if (h->prec != Prec::P64) {
+      // reduced-precision iterations down to their rounding floor, then float64 cleanup iterations
+      GroundEngine* gl = ground_engine(h, h->prec);
+      RTCC_CUDA(cudaMemsetAsync(gl->Y, 0, sizeof(double) * 2 * h->ns, h->stream));
+      solve_block(h, gl, false, std::max(tol, 1e-9), maxiter, true);
+      solve_block(h, gl, true, std::max(tol, 1e-9), maxiter, true);
+      RTCC_CUDA(cudaMemcpyAsync(g->Y, gl->Y, sizeof(double) * 2 * h->ns, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    solve_block(h, g, false, tol, maxiter, false);
+    solve_block(h, g, true, tol, maxiter, false);
     g->E->run(g->rhs.fwd);
     g->E->run(g->energy);
     double ec[2];
@@ -852,7 +901,6 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
   if (in.method == RTCC_MIXED_RK4 && !(in.h1 > 0 && in.h2 > 0)) return fail(RTCC_ERR_INVALID_ARG, "h1, h2 must be positive");
   if (in.method == RTCC_CK && !(in.h > 0 && in.tol > 0 && in.safety > 0 && in.h_min > 0 && in.h_max >= in.h_min))
     return fail(RTCC_ERR_INVALID_ARG, "bad Cash-Karp settings");
-  if (in.method == RTCC_CK && in.nsteps > 0) return fail(RTCC_ERR_INVALID_ARG, "Cash-Karp runs to t_end");
   return guarded([&] {
     cudaStream_t s = h->stream;
     const int nz = h->nz;
@@ -875,9 +923,12 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
                                              max_out, nz, 1);
     RTCC_CUDA(cudaGetLastError());
     const char* ng = std::getenv("RTCC_NO_GRAPH");
-    const bool use_graph = !(ng && ng[0] == '1');
-    // first attempt eagerly (sets kernel attributes), then replay a captured graph
+    const bool use_graph = !(ng && ng[0] == '1') && !h->prof.on();
+    // first attempt eagerly (sets kernel attributes and counts the launches of one attempt),
+    // then replay a captured graph
+    const long long c0 = total_count(h->prof);
     run_attempt(h, tb, in, tout, muout, max_out);
+    const long long per_attempt = total_count(h->prof) - c0;
     cudaGraphExec_t exec = nullptr;
     if (use_graph) {
       cudaGraph_t graph = nullptr;
@@ -933,18 +984,34 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
     h->last_stats[0] = cnt[0];
     h->last_stats[1] = cnt[1];
     h->last_stats[2] = (cnt[0] + cnt[1]) * tb.s;
+    h->last_stats[3] = per_attempt * attempts;
     if (!dev_out) {
       // temporary device output buffers are released with the handle's allocation list
     }
   });
 }
 
-rtcc_status_t rtcc_last_stats(rtcc_handle_t h, long long* accepted, long long* rejected, long long* rhs_evals) {
+rtcc_status_t rtcc_last_stats(rtcc_handle_t h, long long* accepted, long long* rejected, long long* rhs_evals,
+                              long long* launches) {
   if (!h) return fail(RTCC_ERR_INVALID_ARG, "null handle");
   if (accepted) *accepted = h->last_stats[0];
   if (rejected) *rejected = h->last_stats[1];
   if (rhs_evals) *rhs_evals = h->last_stats[2];
+  if (launches) *launches = h->last_stats[3];
   return RTCC_OK;
+}
+
+rtcc_status_t rtcc_profile(rtcc_handle_t h, int enable, rtcc_profile_t* out) {
+  if (!h) return fail(RTCC_ERR_INVALID_ARG, "null handle");
+  return guarded([&] {
+    if (enable) {
+      h->prof.begin();
+      return;
+    }
+    rtcc_profile_t p{};
+    h->prof.end(p.launches, p.ms, p.flops, p.bytes);
+    if (out) *out = p;
+  });
 }
 
 rtcc_status_t rtcc_spectrum(const double* t, const double* mu, int n, const rtcc_field_t* field, double kappa,

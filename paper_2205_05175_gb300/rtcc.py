@@ -39,6 +39,14 @@ class rtcc_integrator_t(C.Structure):
                 ("nsteps", C.c_int), ("t_end", C.c_double)]
 
 
+class rtcc_profile_t(C.Structure):
+    _fields_ = [("launches", C.c_longlong * 8), ("ms", C.c_double * 8), ("flops", C.c_double * 8),
+                ("bytes", C.c_double * 8)]
+
+
+KERNEL_CLASSES = ["tc_gemm", "f64_gemm", "pack", "unpack", "direct", "reduce", "add", "rk"]
+
+
 class RtccError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{STATUS.get(code, code)}: {msg}")
@@ -57,7 +65,9 @@ _sig = {
     "rtcc_rhs": [_vp, _vp, C.POINTER(rtcc_field_t), _vp, _vp],
     "rtcc_dipole": [_vp, _vp],
     "rtcc_propagate": [_vp, C.POINTER(rtcc_field_t), C.POINTER(rtcc_integrator_t), C.c_int, _vp, _vp, _ip],
-    "rtcc_last_stats": [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)],
+    "rtcc_last_stats": [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                        C.POINTER(C.c_longlong)],
+    "rtcc_profile": [_vp, C.c_int, C.POINTER(rtcc_profile_t)],
     "rtcc_spectrum": [_vp, _vp, C.c_int, C.POINTER(rtcc_field_t), C.c_double, C.c_double, C.c_double, _vp,
                       C.c_int, _vp],
     "rtcc_selftest_gemm": [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp],
@@ -191,9 +201,19 @@ class Handle:
         return t_out, mu_out, n_out
 
     def last_stats(self):
-        a, r, e = C.c_longlong(), C.c_longlong(), C.c_longlong()
-        _check(_lib.rtcc_last_stats(self.h, C.byref(a), C.byref(r), C.byref(e)))
-        return a.value, r.value, e.value
+        """(accepted steps, rejected attempts, rhs evaluations, kernel launches) of the last propagate."""
+        a, r, e, n = C.c_longlong(), C.c_longlong(), C.c_longlong(), C.c_longlong()
+        _check(_lib.rtcc_last_stats(self.h, C.byref(a), C.byref(r), C.byref(e), C.byref(n)))
+        return a.value, r.value, e.value, n.value
+
+    def profile_start(self):
+        _check(_lib.rtcc_profile(self.h, 1, None))
+
+    def profile_stop(self):
+        p = rtcc_profile_t()
+        _check(_lib.rtcc_profile(self.h, 0, C.byref(p)))
+        return {KERNEL_CLASSES[k]: {"launches": p.launches[k], "ms": p.ms[k], "flops": p.flops[k],
+                                    "bytes": p.bytes[k]} for k in range(8)}
 
 
 def rtcc_spectrum(t, mu_re, field, omegas, kappa=0.0, gamma=0.01, dt=0.0):

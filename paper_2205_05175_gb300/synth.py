@@ -35,11 +35,23 @@ def rng_for(seed: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(int(seed)))
 
 
+def b_sigma(o: int, v: int, naux: int) -> float:
+    """Standard deviation of the density-fitting factors.
+
+    0.05 for the monomer shape (o=5, v=19, naux=96).  For other shapes the
+    variance is scaled so that the collective coupling sqrt(o v naux) sigma^2 of
+    the dense random integrals stays at the monomer's value: with a fixed 0.05,
+    (pq|pq) = naux sigma^2 grows with the basis and from the dimer shape on the
+    CCSD ground-state equations have no convergent Jacobi/DIIS solution.
+    """
+    return 0.05 * (95.0 * 96.0 / (o * v * naux)) ** 0.25
+
+
 def make_system(o: int, v: int, seed: int = SEED_BASE, naux: int | None = None):
     """Draw (f, B, mu) for a closed-shell system with o occupied and v virtual orbitals.
 
     f  : float64 (nmo, nmo), diag(sorted U[-1.4,-0.3] occupied, sorted U[0.15,3.0] virtual)
-    B  : float64 (naux, nmo, nmo), entries N(0, 0.05^2), symmetric in (p, q); naux = 4*nmo
+    B  : float64 (naux, nmo, nmo), entries N(0, b_sigma^2), symmetric in (p, q); naux = 4*nmo
     mu : float64 (3, nmo, nmo), entries N(0, 0.3^2), symmetric
     """
     if o <= 0 or v <= 0:
@@ -50,7 +62,7 @@ def make_system(o: int, v: int, seed: int = SEED_BASE, naux: int | None = None):
     eps_o = np.sort(rng.uniform(-1.4, -0.3, o))
     eps_v = np.sort(rng.uniform(0.15, 3.0, v))
     f = np.diag(np.concatenate([eps_o, eps_v])).astype(np.float64)
-    raw = rng.normal(0.0, 0.05, (naux, nmo, nmo))
+    raw = rng.normal(0.0, b_sigma(o, v, naux), (naux, nmo, nmo))
     upper = np.triu(raw)
     B = upper + np.transpose(np.triu(raw, 1), (0, 2, 1))
     rawm = rng.normal(0.0, 0.3, (3, nmo, nmo))
