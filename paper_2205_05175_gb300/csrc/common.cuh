@@ -78,6 +78,7 @@ struct PackDesc {
   long long Kpad;   // padded row length of the packed matrix
   int elem;         // PackElem
   int round_tf32;   // round float32 values to TF32 (round-to-nearest) when packing
+  int transpose;    // 1: the source's unit-stride index is a row index (shared-memory tile transpose)
   void* dst;
 };
 
@@ -94,6 +95,7 @@ struct UnpackDesc {
   double* C;
   int c_cplx;
   double ar, ai;
+  int transpose;         // 1: the output's unit-stride index is an M index (shared-memory tile transpose)
 };
 
 // Direct (small) contraction C[bt,m,n] += alpha * sum_k A[bt,m,k] B[bt,n,k] in float64.

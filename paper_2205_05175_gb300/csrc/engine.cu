@@ -2,6 +2,7 @@
 #include "engine.cuh"
 #include <algorithm>
 #include <set>
+#include <cstdlib>
 
 namespace rtcc {
 
@@ -34,6 +35,30 @@ long long prod_dims(const IndexMap& m) {
 }
 
 long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
+
+// Order labels by decreasing |stride| in tensor t (so the unit-stride label comes last).
+std::string by_stride(const std::string& labs, const Tensor& t, const std::string& tl) {
+  std::string out = labs;
+  std::stable_sort(out.begin(), out.end(), [&](char a, char b) {
+    return std::llabs(t.strides[tl.find(a)]) > std::llabs(t.strides[tl.find(b)]);
+  });
+  return out;
+}
+
+// True when the smallest-stride label of t among (rows + cols) is the last row label.
+bool row_is_unit(const Tensor& t, const std::string& tl, const std::string& rows, const std::string& cols) {
+  if (rows.empty()) return false;
+  char best = 0;
+  long long bs = -1;
+  for (char l : rows + cols) {
+    const long long st = std::llabs(t.strides[tl.find(l)]);
+    if (bs < 0 || st < bs) {
+      bs = st;
+      best = l;
+    }
+  }
+  return best == rows.back();
+}
 
 }  // namespace
 
@@ -77,12 +102,12 @@ void Profiler::start(cudaStream_t s) {
   pending_ = (int)used_;
   RTCC_CUDA(cudaEventRecord(get(), s));
 }
-void Profiler::stop(cudaStream_t s, int cls, double flops, double bytes) {
+void Profiler::stop(cudaStream_t s, int cls, double flops, double bytes, const char* tag) {
   ++count[cls];
   if (!on_) return;
   const int b = (int)used_;
   RTCC_CUDA(cudaEventRecord(get(), s));
-  recs_.push_back(Rec{cls, pending_, b, flops, bytes});
+  recs_.push_back(Rec{cls, pending_, b, flops, bytes, tag ? std::string(tag) : std::string()});
 }
 void Profiler::end(long long launches[KC_N], double ms[KC_N], double flops[KC_N], double bytes[KC_N]) {
   for (int c = 0; c < KC_N; ++c) {
@@ -90,6 +115,8 @@ void Profiler::end(long long launches[KC_N], double ms[KC_N], double flops[KC_N]
     ms[c] = flops[c] = bytes[c] = 0.0;
   }
   if (!recs_.empty()) RTCC_CUDA(cudaEventSynchronize(pool_[recs_.back().b]));
+  const char* dump = std::getenv("RTCC_PROFILE_OPS");
+  std::map<std::string, std::vector<double>> per;   // tag -> {class, launches, ms, flops, bytes}
   for (const Rec& r : recs_) {
     float t = 0.f;
     RTCC_CUDA(cudaEventElapsedTime(&t, pool_[r.a], pool_[r.b]));
@@ -97,6 +124,24 @@ void Profiler::end(long long launches[KC_N], double ms[KC_N], double flops[KC_N]
     ms[r.cls] += t;
     flops[r.cls] += r.flops;
     bytes[r.cls] += r.bytes;
+    if (dump) {
+      auto& v = per[r.tag + "|" + std::to_string(r.cls)];
+      if (v.empty()) v = {(double)r.cls, 0, 0, 0, 0};
+      v[1] += 1;
+      v[2] += t;
+      v[3] += r.flops;
+      v[4] += r.bytes;
+    }
+  }
+  if (dump) {
+    FILE* fp = std::fopen(dump, "w");
+    if (fp) {
+      std::fprintf(fp, "tag,class,launches,ms,flops,bytes\n");
+      for (const auto& kv : per)
+        std::fprintf(fp, "%s,%d,%.0f,%.4f,%.6g,%.6g\n", kv.first.substr(0, kv.first.rfind('|')).c_str(),
+                     (int)kv.second[0], kv.second[1], kv.second[2], kv.second[3], kv.second[4]);
+      std::fclose(fp);
+    }
   }
   on_ = false;
   recs_.clear();
@@ -234,6 +279,7 @@ Program Engine::reverse(const Program& fwd, const std::vector<int>& active_input
 
 void Engine::plan(Program& P) {
   P.comp.clear();
+  const Prec prec = P.force_p64 ? Prec::P64 : prec_;
   for (const Op& op : P.ops) {
     auto cp = std::make_shared<Compiled>();
     Compiled& k = *cp;
@@ -286,6 +332,10 @@ void Engine::plan(Program& P) {
     for (char l : op.lb)
       if (op.lc.find(l) == std::string::npos)
         RTCC_REQUIRE(op.la.find(l) != std::string::npos, std::string("dangling label ") + l + " in " + P.name);
+    // label orders: unit-stride labels last for the operands that are packed every run
+    Lm = A.constant ? by_stride(Lm, C, op.lc) : by_stride(Lm, A, op.la);
+    Ln = B.constant ? by_stride(Ln, C, op.lc) : by_stride(Ln, B, op.lb);
+    Lk = !A.constant ? by_stride(Lk, A, op.la) : (!B.constant ? by_stride(Lk, B, op.lb) : Lk);
     // extent consistency
     auto ext = [&](const Tensor& t, const std::string& tl, char l) { return t.dims[tl.find(l)]; };
     for (char l : op.lc) {
@@ -342,10 +392,10 @@ void Engine::plan(Program& P) {
       k.kind = CK_GEMM;
     }
     if (k.kind == CK_GEMM) {
-      const int nss = (prec_ == Prec::TF32X3 || prec_ == Prec::BF16X3) ? 3 : 1;
-      const int elem = (prec_ == Prec::P64) ? PE_F64 : (prec_ == Prec::BF16X3 ? PE_BF16 : PE_F32);
+      const int nss = (prec == Prec::TF32X3 || prec == Prec::BF16X3) ? 3 : 1;
+      const int elem = (prec == Prec::P64) ? PE_F64 : (prec == Prec::BF16X3 ? PE_BF16 : PE_F32);
       const int esz = (elem == PE_F64) ? 8 : (elem == PE_F32 ? 4 : 2);
-      k.tc_kind = (prec_ == Prec::P64) ? -1 : (prec_ == Prec::BF16X3 ? 1 : 0);
+      k.tc_kind = (prec == Prec::P64) ? -1 : (prec == Prec::BF16X3 ? 1 : 0);
       const long long kblk = (k.tc_kind < 0) ? 16 : tc_kblock_elems(k.tc_kind);
       PackDesc& pa = k.pa;
       PackDesc& pb = k.pb;
@@ -413,6 +463,8 @@ void Engine::plan(Program& P) {
       pa.Kpad = pb.Kpad = Kp;
       pa.elem = pb.elem = elem;
       pa.round_tf32 = pb.round_tf32 = 1;
+      pa.transpose = row_is_unit(A, op.la, Lm, Lk) ? 1 : 0;
+      pb.transpose = row_is_unit(B, op.lb, Ln, Lk) ? 1 : 0;
       k.GM = (long long)pa.nrb * M;
       k.GN = (long long)pb.nrb * N;
       k.Kpad = Kp;
@@ -438,6 +490,7 @@ void Engine::plan(Program& P) {
       u.c_cplx = C.cplx;
       u.ar = d.ar;
       u.ai = d.ai;
+      u.transpose = row_is_unit(C, op.lc, Lm, Ln) ? 1 : 0;
       if (!k.a_const) wsA_bytes_ = std::max(wsA_bytes_, k.a_bytes);
       if (!k.b_const) wsB_bytes_ = std::max(wsB_bytes_, k.b_bytes);
       wsC_bytes_ = std::max(wsC_bytes_, k.c_bytes);
@@ -528,23 +581,31 @@ void Engine::run(const Program& P) {
   for (const auto& z : P.zero2d) RTCC_CUDA(cudaMemset2DAsync(z.ptr, z.pitch, 0, z.width, z.height, stream_));
   Profiler dummy;
   Profiler& pr = prof_ ? *prof_ : dummy;
-  for (const auto& cp : P.comp) {
-    const Compiled& k = *cp;
+  std::string tagbuf;
+  for (size_t oi = 0; oi < P.comp.size(); ++oi) {
+    const Compiled& k = *P.comp[oi];
+    const char* tag = nullptr;
+    if (pr.on()) {
+      const Op& op = P.ops[oi];
+      tagbuf = P.name + "#" + std::to_string(oi) + " " + tensors_[op.c].name + "[" + op.lc + "]<-" +
+               tensors_[op.a].name + "[" + op.la + "]" + (op.kind == OP_EIN ? "*" + tensors_[op.b].name + "[" + op.lb + "]" : "");
+      tag = tagbuf.c_str();
+    }
     switch (k.kind) {
       case CK_ADD:
         pr.start(stream_);
         launch_add(k.add, stream_);
-        pr.stop(stream_, KC_ADD, 0.0, (double)k.add.n * ((k.add.a_cplx ? 16 : 8) + 2 * (k.add.c_cplx ? 16 : 8)));
+        pr.stop(stream_, KC_ADD, 0.0, (double)k.add.n * ((k.add.a_cplx ? 16 : 8) + 2 * (k.add.c_cplx ? 16 : 8)), tag);
         break;
       case CK_DIRECT:
         pr.start(stream_);
         launch_direct(k.dir, stream_);
-        pr.stop(stream_, KC_DIRECT, (double)k.alg_flops, 0.0);
+        pr.stop(stream_, KC_DIRECT, (double)k.alg_flops, 0.0, tag);
         break;
       case CK_REDUCE:
         pr.start(stream_);
         launch_reduce(k.dir, k.splits, stream_);
-        pr.stop(stream_, KC_REDUCE, (double)k.alg_flops, 0.0);
+        pr.stop(stream_, KC_REDUCE, (double)k.alg_flops, 0.0, tag);
         break;
       default: {
         const double esz = (k.pa.elem == PE_F64) ? 8 : (k.pa.elem == PE_F32 ? 4 : 2);
@@ -552,13 +613,13 @@ void Engine::run(const Program& P) {
           pr.start(stream_);
           launch_pack(k.pa, stream_);
           pr.stop(stream_, KC_PACK, 0.0,
-                  (double)k.NB * k.pa.R * k.pa.K * (k.pa.src_cplx ? 16 : 8) + (double)k.NB * k.GM * k.Kpad * esz);
+                  (double)k.NB * k.pa.R * k.pa.K * (k.pa.src_cplx ? 16 : 8) + (double)k.NB * k.GM * k.Kpad * esz, tag);
         }
         if (!k.b_const) {
           pr.start(stream_);
           launch_pack(k.pb, stream_);
           pr.stop(stream_, KC_PACK, 0.0,
-                  (double)k.NB * k.pb.R * k.pb.K * (k.pb.src_cplx ? 16 : 8) + (double)k.NB * k.GN * k.Kpad * esz);
+                  (double)k.NB * k.pb.R * k.pb.K * (k.pb.src_cplx ? 16 : 8) + (double)k.NB * k.GN * k.Kpad * esz, tag);
         }
         // kernel-level algorithmic flops: the real multiply-adds of the packed product without padding
         const double kflops = 2.0 * k.NB * k.GM * k.GN * (double)(k.pa.nss * k.pa.ncs * k.pa.K);
@@ -568,11 +629,11 @@ void Engine::run(const Program& P) {
           launch_gemm_f64(static_cast<const double*>(k.pa.dst), static_cast<const double*>(k.pb.dst),
                           static_cast<double*>(wsC_), k.GM, k.GN, k.Kpad, k.NB, stream_);
         pr.stop(stream_, k.tc_kind >= 0 ? KC_TC_GEMM : KC_F64_GEMM, kflops,
-                (double)k.NB * (k.GM + k.GN) * k.Kpad * esz + (double)k.NB * k.GM * k.GN * (k.tc_kind >= 0 ? 4 : 8));
+                (double)k.NB * (k.GM + k.GN) * k.Kpad * esz + (double)k.NB * k.GM * k.GN * (k.tc_kind >= 0 ? 4 : 8), tag);
         pr.start(stream_);
         launch_unpack(k.up, stream_);
         pr.stop(stream_, KC_UNPACK, 0.0,
-                (double)k.NB * k.GM * k.GN * (k.tc_kind >= 0 ? 4 : 8) + 2.0 * k.NB * k.up.M * k.up.N * (k.up.c_cplx ? 16 : 8));
+                (double)k.NB * k.GM * k.GN * (k.tc_kind >= 0 ? 4 : 8) + 2.0 * k.NB * k.up.M * k.up.N * (k.up.c_cplx ? 16 : 8), tag);
       }
     }
   }

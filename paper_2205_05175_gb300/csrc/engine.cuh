@@ -52,6 +52,7 @@ struct Program {
   std::vector<int> zero_tensors;    // contiguous tensors cleared before the first op
   struct Zero2D { void* ptr; size_t pitch, width, height; };
   std::vector<Zero2D> zero2d;       // strided regions cleared before the first op
+  bool force_p64 = false;           // run this program's GEMM-path contractions in float64
   std::vector<std::shared_ptr<Compiled>> comp;
 };
 
@@ -66,12 +67,12 @@ class Profiler {
   void begin();
   bool on() const { return on_; }
   void start(cudaStream_t s);
-  void stop(cudaStream_t s, int cls, double flops, double bytes);
+  void stop(cudaStream_t s, int cls, double flops, double bytes, const char* tag = nullptr);
   // synchronises, accumulates per class and turns profiling off
   void end(long long launches[KC_N], double ms[KC_N], double flops[KC_N], double bytes[KC_N]);
   long long count[KC_N] = {0};   // launches per class, counted whether or not timing is on
  private:
-  struct Rec { int cls; int a, b; double flops, bytes; };
+  struct Rec { int cls; int a, b; double flops, bytes; std::string tag; };
   cudaEvent_t get();
   bool on_ = false;
   std::vector<cudaEvent_t> pool_;

@@ -13,6 +13,7 @@
 // that in-flight MMAs drain before TMEM is released.
 #include "common.cuh"
 #include <cudaTypedefs.h>
+#include <algorithm>
 
 namespace rtcc {
 namespace {
@@ -120,10 +121,12 @@ __device__ __forceinline__ uint32_t idesc_make() {
   return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
+constexpr int kGroupM = 8;   // M tiles per rasterisation group (a wave shares A and B panels in L2)
+
 template <int BN, int KIND, int STAGES>
 __global__ void __launch_bounds__(128, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   float* __restrict__ C, int M, int N, int nkb, int* __restrict__ err) {
+                   float* __restrict__ C, int M, int N, int nkb_total, int kb_per_split, int* __restrict__ err) {
   constexpr int A_BYTES = BM * 128;
   constexpr int B_BYTES = BN * 128;
   constexpr int KBLK = (KIND == 0) ? 32 : 64;
@@ -137,7 +140,18 @@ __global__ void __launch_bounds__(128, 1)
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(accf + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, bz = blockIdx.z;
+  // grouped rasterisation: GROUP_M consecutive M tiles sweep all N tiles before the next group
+  const int num_m = (M + BM - 1) / BM, num_n = (N + BN - 1) / BN;
+  const int pid = blockIdx.x;
+  const int group = pid / (kGroupM * num_n);
+  const int first_m = group * kGroupM;
+  const int gsize = min(num_m - first_m, kGroupM);
+  const int pig = pid - group * kGroupM * num_n;
+  const int m0 = (first_m + pig % gsize) * BM, n0 = (pig / gsize) * BN, bz = blockIdx.z;
+  // split-K range of this CTA
+  const int kb0 = blockIdx.y * kb_per_split;
+  const int nkb = min(nkb_total, kb0 + kb_per_split) - kb0;
+  const bool split = gridDim.y > 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -166,8 +180,8 @@ __global__ void __launch_bounds__(128, 1)
         break;
       }
       mbar_arrive_tx(&full[s], A_BYTES + B_BYTES);
-      tma_load3(su32(sA + s * A_BYTES), &tmA, su32(&full[s]), kb * KBLK, m0, bz);
-      tma_load3(su32(sB + s * B_BYTES), &tmB, su32(&full[s]), kb * KBLK, n0, bz);
+      tma_load3(su32(sA + s * A_BYTES), &tmA, su32(&full[s]), (kb0 + kb) * KBLK, m0, bz);
+      tma_load3(su32(sB + s * B_BYTES), &tmB, su32(&full[s]), (kb0 + kb) * KBLK, n0, bz);
     }
   } else if (warp == 1 && lane == 0) {
     const uint32_t idesc = idesc_make<KIND, BN>();
@@ -202,7 +216,11 @@ __global__ void __launch_bounds__(128, 1)
       uint32_t r[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
       const int col0 = n0 + c;
-      if (row < M && col0 < N) {
+      if (row < M && col0 < N && split) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+          if (col0 + q < N) atomicAdd(crow + col0 + q, __uint_as_float(r[q]));
+      } else if (row < M && col0 < N) {
         if (vec && col0 + 32 <= N) {
           float4* dst = reinterpret_cast<float4*>(crow + col0);
 #pragma unroll
@@ -270,8 +288,18 @@ void launch_inst(const TcGemmPlan& p, cudaStream_t s) {
     attr = true;
   }
   const int nkb = (int)(p.Kpad / (KIND == 0 ? 32 : 64));
-  dim3 grid((unsigned)((p.N + BN - 1) / BN), (unsigned)((p.M + BM - 1) / BM), (unsigned)p.NB);
-  kern<<<grid, 128, sm, s>>>(p.tmA, p.tmB, p.C, (int)p.M, (int)p.N, nkb, p.err);
+  const long long tiles = ((p.M + BM - 1) / BM) * ((p.N + BN - 1) / BN);
+  // split K when the output has less than one wave of tiles and K is long
+  int splits = 1;
+  if (tiles * p.NB < 152 && nkb >= 32) {
+    splits = (int)std::min<long long>((2 * 152 + tiles * p.NB - 1) / (tiles * p.NB), nkb / 16);
+    splits = std::max(1, std::min(splits, 64));
+  }
+  const int per = (nkb + splits - 1) / splits;
+  splits = (nkb + per - 1) / per;
+  if (splits > 1) RTCC_CUDA(cudaMemsetAsync(p.C, 0, sizeof(float) * p.M * p.N * p.NB, s));
+  dim3 grid((unsigned)tiles, (unsigned)splits, (unsigned)p.NB);
+  kern<<<grid, 128, sm, s>>>(p.tmA, p.tmB, p.C, (int)p.M, (int)p.N, nkb, per, p.err);
   RTCC_CUDA(cudaGetLastError());
 }
 

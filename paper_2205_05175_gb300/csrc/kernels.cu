@@ -8,6 +8,7 @@
 //   dgemm   : float64 SIMT GEMM for the float64 precision mode
 #include "common.cuh"
 #include <cuda_bf16.h>
+#include <algorithm>
 
 namespace rtcc {
 namespace {
@@ -27,147 +28,319 @@ __device__ __forceinline__ float tf32_rn(float x) {
   return __uint_as_float(r);
 }
 
-__global__ void pack_kernel(PackDesc d) {
-  const long long rows = (long long)d.nrb * d.R;
-  const long long total = d.NB * rows * d.Kpad;
-  const long long segK = (long long)d.ncs * d.K;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long kk = idx % d.Kpad;
-    const long long t = idx / d.Kpad;
-    const long long r = t % rows;
-    const long long bt = t / rows;
-    double x = 0.0;
-    int part = SP_FULL;
-    if (kk < d.nss * segK) {
-      const int ss = (int)(kk / segK);
-      const long long rem = kk - ss * segK;
-      const int cs = (int)(rem / d.K);
-      const long long k = rem - cs * d.K;
-      const int rb = (int)(r / d.R);
-      const long long m = r - rb * d.R;
-      const long long off = imap_offset(d.bat, bt) + imap_offset(d.rows, m) + imap_offset(d.cols, k);
-      const int comp = d.comp[rb][cs];
-      if (d.src_cplx) x = d.src[2 * off + comp];
-      else x = (comp == 0) ? d.src[off] : 0.0;
-      x *= (double)d.sign[rb][cs];
-      part = d.part[ss];
+// 32-bit mixed-radix decode of one index group (extents < 2^31 per group).
+__device__ __forceinline__ long long imap32(const IndexMap& m, unsigned idx) {
+  long long off = 0;
+  for (int d = m.n - 1; d >= 0; --d) {
+    const unsigned dim = (unsigned)m.dims[d];
+    const unsigned q = idx / dim;
+    off += (long long)(idx - q * dim) * m.strides[d];
+    idx = q;
+  }
+  return off;
+}
+
+template <int ELEM>
+__device__ __forceinline__ void put(void* dst, size_t i, double x, int part, int round_tf32) {
+  if constexpr (ELEM == PE_F64) {
+    static_cast<double*>(dst)[i] = x;
+  } else if constexpr (ELEM == PE_F32) {
+    float v;
+    if (part == SP_FULL) v = round_tf32 ? tf32_rn((float)x) : (float)x;
+    else {
+      const float hi = tf32_rn((float)x);
+      v = (part == SP_HI) ? hi : tf32_rn((float)(x - (double)hi));
     }
-    if (d.elem == PE_F64) {
-      static_cast<double*>(d.dst)[idx] = x;
-    } else if (d.elem == PE_F32) {
-      float v;
-      if (part == SP_FULL) v = d.round_tf32 ? tf32_rn((float)x) : (float)x;
-      else {
-        const float hi = tf32_rn((float)x);
-        v = (part == SP_HI) ? hi : tf32_rn((float)(x - (double)hi));
-      }
-      static_cast<float*>(d.dst)[idx] = v;
-    } else {
-      __nv_bfloat16 v;
-      if (part == SP_FULL) v = __float2bfloat16_rn((float)x);
-      else {
-        const __nv_bfloat16 hi = __float2bfloat16_rn((float)x);
-        v = (part == SP_HI) ? hi : __float2bfloat16_rn((float)(x - (double)__bfloat162float(hi)));
-      }
-      static_cast<__nv_bfloat16*>(d.dst)[idx] = v;
+    static_cast<float*>(dst)[i] = v;
+  } else {
+    __nv_bfloat16 v;
+    if (part == SP_FULL) v = __float2bfloat16_rn((float)x);
+    else {
+      const __nv_bfloat16 hi = __float2bfloat16_rn((float)x);
+      v = (part == SP_HI) ? hi : __float2bfloat16_rn((float)(x - (double)__bfloat162float(hi)));
+    }
+    static_cast<__nv_bfloat16*>(dst)[i] = v;
+  }
+}
+
+// Write one source element (xr, xi) to every destination it feeds: row blocks rb (re/im
+// stacking or the [[Ar,-Ai],[Ai,Ar]] embedding), column segments cs, precision parts ss.
+template <int ELEM>
+__device__ __forceinline__ void pack_store(const PackDesc& d, unsigned bt, unsigned m, unsigned k, double xr,
+                                           double xi) {
+  const size_t GR = (size_t)d.nrb * d.R;
+  const size_t K = (size_t)d.K;
+#pragma unroll 1
+  for (int rb = 0; rb < d.nrb; ++rb) {
+    const size_t rowbase = ((size_t)bt * GR + (size_t)rb * d.R + m) * (size_t)d.Kpad;
+#pragma unroll 1
+    for (int cs = 0; cs < d.ncs; ++cs) {
+      const double x = (d.comp[rb][cs] ? xi : xr) * (double)d.sign[rb][cs];
+#pragma unroll 1
+      for (int ss = 0; ss < d.nss; ++ss)
+        put<ELEM>(d.dst, rowbase + ((size_t)ss * d.ncs + cs) * K + k, x, d.part[ss], d.round_tf32);
     }
   }
 }
 
-__global__ void unpack_kernel(UnpackDesc d) {
-  const long long total = d.NB * d.M * d.N;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long n = idx % d.N;
-    const long long t = idx / d.N;
-    const long long m = t % d.M;
-    const long long bt = t / d.M;
-    const long long gb = bt * d.rows_g * d.ldg;
-    long long ire = gb + m * d.ldg + n, iim = -1;
-    if (d.mode == OM_STACK_M) iim = gb + (m + d.M) * d.ldg + n;
-    else if (d.mode == OM_STACK_N) iim = gb + m * d.ldg + n + d.N;
-    double re, im = 0.0;
-    if (d.gout_f64) {
-      const double* g = static_cast<const double*>(d.gout);
-      re = g[ire];
-      if (iim >= 0) im = g[iim];
-    } else {
-      const float* g = static_cast<const float*>(d.gout);
-      re = (double)g[ire];
-      if (iim >= 0) im = (double)g[iim];
-    }
-    const long long off = imap_offset(d.cb, bt) + imap_offset(d.cm, m) + imap_offset(d.cn, n);
-    const double vr = d.ar * re - d.ai * im;
-    const double vi = d.ar * im + d.ai * re;
-    if (d.c_cplx) {
-      d.C[2 * off] += vr;
-      d.C[2 * off + 1] += vi;
-    } else {
-      d.C[off] += vr;
+template <int ELEM>
+__device__ __forceinline__ void pack_pad(const PackDesc& d, unsigned bt, unsigned m, unsigned p) {
+  const size_t GR = (size_t)d.nrb * d.R;
+  const size_t c0 = (size_t)d.nss * d.ncs * d.K;
+  for (int rb = 0; rb < d.nrb; ++rb)
+    put<ELEM>(d.dst, ((size_t)bt * GR + (size_t)rb * d.R + m) * (size_t)d.Kpad + c0 + p, 0.0, SP_FULL, 0);
+}
+
+// Source unit stride along K: a row per thread-row, consecutive k per thread.
+template <int ELEM>
+__global__ void pack_direct_kernel(PackDesc d, unsigned kext, unsigned padw) {
+  const unsigned R = (unsigned)d.R, K = (unsigned)d.K;
+  const unsigned NR = (unsigned)(d.NB * d.R);
+  for (unsigned row = blockIdx.y * blockDim.y + threadIdx.y; row < NR; row += gridDim.y * blockDim.y) {
+    const unsigned bt = row / R, m = row - bt * R;
+    const long long base = imap32(d.bat, bt) + imap32(d.rows, m);
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < kext; k += gridDim.x * blockDim.x) {
+      if (k < K) {
+        const long long off = base + imap32(d.cols, k);
+        double xr, xi = 0.0;
+        if (d.src_cplx) {
+          const double2 v = reinterpret_cast<const double2*>(d.src)[off];
+          xr = v.x;
+          xi = v.y;
+        } else {
+          xr = d.src[off];
+        }
+        pack_store<ELEM>(d, bt, m, k, xr, xi);
+      } else if (k - K < padw) {
+        pack_pad<ELEM>(d, bt, m, k - K);
+      }
     }
   }
 }
 
+// Source unit stride along a row index: 32 x 32 tiles through shared memory (coalesced both ways).
+template <int ELEM>
+__global__ void __launch_bounds__(256) pack_transpose_kernel(PackDesc d, unsigned padw) {
+  __shared__ double tre[32][33], tim[32][33];
+  const unsigned R = (unsigned)d.R, K = (unsigned)d.K;
+  const unsigned NR = (unsigned)(d.NB * d.R);
+  const unsigned nkt = (K + 31) / 32, nrt = (NR + 31) / 32;
+  const unsigned tx = threadIdx.x, ty = threadIdx.y;
+  for (unsigned rt = blockIdx.y; rt < nrt; rt += gridDim.y) {
+    for (unsigned kt = blockIdx.x; kt < nkt + (padw ? 1u : 0u); kt += gridDim.x) {
+      const unsigned r0 = rt * 32, k0 = kt * 32;
+      if (kt == nkt) {
+        for (int i = 0; i < 4; ++i) {
+          const unsigned row = r0 + ty + 8 * i;
+          if (row >= NR) continue;
+          const unsigned bt = row / R, m = row - bt * R;
+          for (unsigned p = tx; p < padw; p += 32) pack_pad<ELEM>(d, bt, m, p);
+        }
+        continue;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const unsigned k = k0 + ty + 8 * i, row = r0 + tx;
+        double xr = 0.0, xi = 0.0;
+        if (row < NR && k < K) {
+          const unsigned bt = row / R, m = row - bt * R;
+          const long long off = imap32(d.bat, bt) + imap32(d.rows, m) + imap32(d.cols, k);
+          if (d.src_cplx) {
+            const double2 v = reinterpret_cast<const double2*>(d.src)[off];
+            xr = v.x;
+            xi = v.y;
+          } else {
+            xr = d.src[off];
+          }
+        }
+        tre[ty + 8 * i][tx] = xr;
+        tim[ty + 8 * i][tx] = xi;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const unsigned row = r0 + ty + 8 * i, k = k0 + tx;
+        if (row < NR && k < K) {
+          const unsigned bt = row / R, m = row - bt * R;
+          pack_store<ELEM>(d, bt, m, k, tre[tx][ty + 8 * i], tim[tx][ty + 8 * i]);
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <typename G>
+__device__ __forceinline__ void unpack_one(const UnpackDesc& d, const G* g, unsigned bt, unsigned m, unsigned n,
+                                           long long off) {
+  const size_t gb = (size_t)bt * (size_t)d.rows_g * (size_t)d.ldg;
+  double re = (double)g[gb + (size_t)m * d.ldg + n], im = 0.0;
+  if (d.mode == OM_STACK_M) im = (double)g[gb + ((size_t)m + d.M) * d.ldg + n];
+  else if (d.mode == OM_STACK_N) im = (double)g[gb + (size_t)m * d.ldg + n + d.N];
+  const double vr = d.ar * re - d.ai * im, vi = d.ar * im + d.ai * re;
+  if (d.c_cplx) {
+    double2* c = reinterpret_cast<double2*>(d.C) + off;
+    double2 x = *c;
+    x.x += vr;
+    x.y += vi;
+    *c = x;
+  } else {
+    d.C[off] += vr;
+  }
+}
+
+template <typename G>
+__global__ void unpack_direct_kernel(UnpackDesc d) {
+  const G* g = static_cast<const G*>(d.gout);
+  const unsigned M = (unsigned)d.M, N = (unsigned)d.N;
+  const unsigned NR = (unsigned)(d.NB * d.M);
+  for (unsigned row = blockIdx.y * blockDim.y + threadIdx.y; row < NR; row += gridDim.y * blockDim.y) {
+    const unsigned bt = row / M, m = row - bt * M;
+    const long long base = imap32(d.cb, bt) + imap32(d.cm, m);
+    for (unsigned n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x)
+      unpack_one<G>(d, g, bt, m, n, base + imap32(d.cn, n));
+  }
+}
+
+// Output unit stride along an M index: read GEMM tiles along n, write along m.
+template <typename G>
+__global__ void __launch_bounds__(256) unpack_transpose_kernel(UnpackDesc d) {
+  __shared__ double tre[32][33], tim[32][33];
+  const G* g = static_cast<const G*>(d.gout);
+  const unsigned M = (unsigned)d.M, N = (unsigned)d.N;
+  const unsigned NR = (unsigned)(d.NB * d.M);
+  const unsigned nnt = (N + 31) / 32, nrt = (NR + 31) / 32;
+  const unsigned tx = threadIdx.x, ty = threadIdx.y;
+  for (unsigned rt = blockIdx.y; rt < nrt; rt += gridDim.y) {
+    for (unsigned nt = blockIdx.x; nt < nnt; nt += gridDim.x) {
+      const unsigned r0 = rt * 32, n0 = nt * 32;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const unsigned row = r0 + ty + 8 * i, n = n0 + tx;
+        double re = 0.0, im = 0.0;
+        if (row < NR && n < N) {
+          const unsigned bt = row / M, m = row - bt * M;
+          const size_t gb = (size_t)bt * (size_t)d.rows_g * (size_t)d.ldg;
+          re = (double)g[gb + (size_t)m * d.ldg + n];
+          if (d.mode == OM_STACK_M) im = (double)g[gb + ((size_t)m + M) * d.ldg + n];
+          else if (d.mode == OM_STACK_N) im = (double)g[gb + (size_t)m * d.ldg + n + N];
+        }
+        tre[ty + 8 * i][tx] = re;
+        tim[ty + 8 * i][tx] = im;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const unsigned n = n0 + ty + 8 * i, row = r0 + tx;
+        if (row < NR && n < N) {
+          const unsigned bt = row / M, m = row - bt * M;
+          const long long off = imap32(d.cb, bt) + imap32(d.cm, m) + imap32(d.cn, n);
+          const double re = tre[tx][ty + 8 * i], im = tim[tx][ty + 8 * i];
+          const double vr = d.ar * re - d.ai * im, vi = d.ar * im + d.ai * re;
+          if (d.c_cplx) {
+            double2* c = reinterpret_cast<double2*>(d.C) + off;
+            double2 x = *c;
+            x.x += vr;
+            x.y += vi;
+            *c = x;
+          } else {
+            d.C[off] += vr;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// rows (bt, m) over blockIdx.y/threadIdx.y, n over x; K walked with an odometer (no divisions)
 __global__ void direct_kernel(DirectDesc d) {
-  const long long total = d.NB * d.M * d.N;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long n = idx % d.N;
-    const long long t = idx / d.N;
-    const long long m = t % d.M;
-    const long long bt = t / d.M;
-    const long long a0 = imap_offset(d.ab, bt) + imap_offset(d.am, m);
-    const long long b0 = imap_offset(d.bb, bt) + imap_offset(d.bn, n);
-    int ctr[kMaxLab];
-    for (int q = 0; q < kMaxLab; ++q) ctr[q] = 0;
-    long long ao = 0, bo = 0;
-    double sr = 0.0, si = 0.0;
-    for (long long k = 0; k < d.K; ++k) {
-      double ar_, ai_ = 0.0, br_, bi_ = 0.0;
-      if (d.a_cplx) { ar_ = d.A[2 * (a0 + ao)]; ai_ = d.A[2 * (a0 + ao) + 1]; }
-      else ar_ = d.A[a0 + ao];
-      if (d.b_cplx) { br_ = d.B[2 * (b0 + bo)]; bi_ = d.B[2 * (b0 + bo) + 1]; }
-      else br_ = d.B[b0 + bo];
-      sr += ar_ * br_ - ai_ * bi_;
-      si += ar_ * bi_ + ai_ * br_;
-      for (int q = d.ak.n - 1; q >= 0; --q) {
-        ++ctr[q];
-        ao += d.ak.strides[q];
-        bo += d.bk.strides[q];
-        if (ctr[q] < d.ak.dims[q]) break;
-        ao -= (long long)d.ak.dims[q] * d.ak.strides[q];
-        bo -= (long long)d.bk.dims[q] * d.bk.strides[q];
-        ctr[q] = 0;
+  const unsigned M = (unsigned)d.M, N = (unsigned)d.N;
+  const unsigned NR = (unsigned)(d.NB * d.M);
+  for (unsigned row = blockIdx.y * blockDim.y + threadIdx.y; row < NR; row += gridDim.y * blockDim.y) {
+    const unsigned bt = row / M, m = row - bt * M;
+    const long long a0 = imap32(d.ab, bt) + imap32(d.am, m);
+    const long long bb0 = imap32(d.bb, bt);
+    const long long cb0 = imap32(d.cb, bt) + imap32(d.cm, m);
+    for (unsigned n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+      const long long b0 = bb0 + imap32(d.bn, n);
+      int ctr[kMaxLab];
+      for (int q = 0; q < kMaxLab; ++q) ctr[q] = 0;
+      long long ao = 0, bo = 0;
+      double sr = 0.0, si = 0.0;
+      for (long long k = 0; k < d.K; ++k) {
+        double ar_, ai_ = 0.0, br_, bi_ = 0.0;
+        if (d.a_cplx) {
+          const double2 x = reinterpret_cast<const double2*>(d.A)[a0 + ao];
+          ar_ = x.x;
+          ai_ = x.y;
+        } else {
+          ar_ = d.A[a0 + ao];
+        }
+        if (d.b_cplx) {
+          const double2 x = reinterpret_cast<const double2*>(d.B)[b0 + bo];
+          br_ = x.x;
+          bi_ = x.y;
+        } else {
+          br_ = d.B[b0 + bo];
+        }
+        sr += ar_ * br_ - ai_ * bi_;
+        si += ar_ * bi_ + ai_ * br_;
+        for (int q = d.ak.n - 1; q >= 0; --q) {
+          ++ctr[q];
+          ao += d.ak.strides[q];
+          bo += d.bk.strides[q];
+          if (ctr[q] < d.ak.dims[q]) break;
+          ao -= (long long)d.ak.dims[q] * d.ak.strides[q];
+          bo -= (long long)d.bk.dims[q] * d.bk.strides[q];
+          ctr[q] = 0;
+        }
       }
-    }
-    const long long off = imap_offset(d.cb, bt) + imap_offset(d.cm, m) + imap_offset(d.cn, n);
-    const double vr = d.ar * sr - d.ai * si;
-    const double vi = d.ar * si + d.ai * sr;
-    if (d.c_cplx) {
-      d.C[2 * off] += vr;
-      d.C[2 * off + 1] += vi;
-    } else {
-      d.C[off] += vr;
+      const long long off = cb0 + imap32(d.cn, n);
+      const double vr = d.ar * sr - d.ai * si;
+      const double vi = d.ar * si + d.ai * sr;
+      if (d.c_cplx) {
+        double2* c = reinterpret_cast<double2*>(d.C) + off;
+        double2 x = *c;
+        x.x += vr;
+        x.y += vi;
+        *c = x;
+      } else {
+        d.C[off] += vr;
+      }
     }
   }
 }
 
-__global__ void add_kernel(AddDesc d) {
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < d.n;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long co = imap_offset(d.c_all, idx);
-    const long long ao = imap_offset(d.a_all, idx);
-    double xr, xi = 0.0;
-    if (d.a_cplx) { xr = d.A[2 * ao]; xi = d.A[2 * ao + 1]; }
-    else xr = d.A[ao];
-    const double vr = d.ar * xr - d.ai * xi;
-    const double vi = d.ar * xi + d.ai * xr;
-    if (d.c_cplx) {
-      d.C[2 * co] += vr;
-      d.C[2 * co + 1] += vi;
-    } else {
-      d.C[co] += vr;
+// C[all labels] += alpha * A: the innermost label over threadIdx.x, the rest over rows
+__global__ void add_kernel(AddDesc d, unsigned inner) {
+  const unsigned rows = (unsigned)(d.n / inner);
+  IndexMap co = d.c_all, ao = d.a_all;   // outer labels (all but the innermost)
+  co.n -= 1;
+  ao.n -= 1;
+  const long long cs = d.c_all.strides[d.c_all.n - 1], as = d.a_all.strides[d.a_all.n - 1];
+  for (unsigned r = blockIdx.y * blockDim.y + threadIdx.y; r < rows; r += gridDim.y * blockDim.y) {
+    const long long cb = imap32(co, r), ab = imap32(ao, r);
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < inner; i += gridDim.x * blockDim.x) {
+      const long long c_off = cb + (long long)i * cs, a_off = ab + (long long)i * as;
+      double xr, xi = 0.0;
+      if (d.a_cplx) {
+        const double2 x = reinterpret_cast<const double2*>(d.A)[a_off];
+        xr = x.x;
+        xi = x.y;
+      } else {
+        xr = d.A[a_off];
+      }
+      const double vr = d.ar * xr - d.ai * xi, vi = d.ar * xi + d.ai * xr;
+      if (d.c_cplx) {
+        double2* c = reinterpret_cast<double2*>(d.C) + c_off;
+        double2 x = *c;
+        x.x += vr;
+        x.y += vi;
+        *c = x;
+      } else {
+        d.C[c_off] += vr;
+      }
     }
   }
 }
@@ -263,21 +436,60 @@ __global__ void __launch_bounds__(256) dgemm_kernel(const double* __restrict__ A
 }  // namespace
 
 void launch_pack(const PackDesc& d, cudaStream_t s) {
-  const long long total = d.NB * (long long)d.nrb * d.R * d.Kpad;
-  if (total == 0) return;
-  pack_kernel<<<grid_for(total), kThreads, 0, s>>>(d);
+  const long long NR = d.NB * d.R;
+  if (NR == 0) return;
+  RTCC_REQUIRE(NR < (1ll << 31) && d.K < (1ll << 31), "pack extents exceed 32-bit indexing");
+  const unsigned padw = (unsigned)(d.Kpad - (long long)d.nss * d.ncs * d.K);
+  if (d.transpose) {
+    const unsigned nkt = (unsigned)((d.K + 31) / 32) + (padw ? 1 : 0);
+    const unsigned nrt = (unsigned)((NR + 31) / 32);
+    dim3 grid(std::min(nkt, 4096u), std::min(nrt, 65535u));
+    dim3 blk(32, 8);
+    if (d.elem == PE_F64) pack_transpose_kernel<PE_F64><<<grid, blk, 0, s>>>(d, padw);
+    else if (d.elem == PE_F32) pack_transpose_kernel<PE_F32><<<grid, blk, 0, s>>>(d, padw);
+    else pack_transpose_kernel<PE_BF16><<<grid, blk, 0, s>>>(d, padw);
+  } else {
+    const unsigned kext = (unsigned)d.K + padw;
+    const unsigned bx = kext >= 256 ? 256u : std::max(32u, (kext + 31) / 32 * 32);
+    const unsigned by = 256 / bx;
+    dim3 blk(bx, by);
+    dim3 grid(std::min((kext + bx - 1) / bx, 4096u), (unsigned)std::min((NR + by - 1) / by, 65535ll));
+    if (d.elem == PE_F64) pack_direct_kernel<PE_F64><<<grid, blk, 0, s>>>(d, kext, padw);
+    else if (d.elem == PE_F32) pack_direct_kernel<PE_F32><<<grid, blk, 0, s>>>(d, kext, padw);
+    else pack_direct_kernel<PE_BF16><<<grid, blk, 0, s>>>(d, kext, padw);
+  }
   RTCC_CUDA(cudaGetLastError());
 }
 void launch_unpack(const UnpackDesc& d, cudaStream_t s) {
-  const long long total = d.NB * d.M * d.N;
-  if (total == 0) return;
-  unpack_kernel<<<grid_for(total), kThreads, 0, s>>>(d);
+  const long long NR = d.NB * d.M;
+  if (NR == 0 || d.N == 0) return;
+  RTCC_REQUIRE(NR < (1ll << 31) && d.N < (1ll << 31), "unpack extents exceed 32-bit indexing");
+  if (d.transpose) {
+    dim3 grid((unsigned)std::min((d.N + 31) / 32, 4096ll), (unsigned)std::min((NR + 31) / 32, 65535ll));
+    dim3 blk(32, 8);
+    if (d.gout_f64) unpack_transpose_kernel<double><<<grid, blk, 0, s>>>(d);
+    else unpack_transpose_kernel<float><<<grid, blk, 0, s>>>(d);
+  } else {
+    const unsigned N = (unsigned)d.N;
+    const unsigned bx = N >= 256 ? 256u : std::max(32u, (N + 31) / 32 * 32);
+    const unsigned by = 256 / bx;
+    dim3 blk(bx, by);
+    dim3 grid(std::min((N + bx - 1) / bx, 4096u), (unsigned)std::min((NR + by - 1) / by, 65535ll));
+    if (d.gout_f64) unpack_direct_kernel<double><<<grid, blk, 0, s>>>(d);
+    else unpack_direct_kernel<float><<<grid, blk, 0, s>>>(d);
+  }
   RTCC_CUDA(cudaGetLastError());
 }
 void launch_direct(const DirectDesc& d, cudaStream_t s) {
-  const long long total = d.NB * d.M * d.N;
-  if (total == 0) return;
-  direct_kernel<<<grid_for(total, 128), 128, 0, s>>>(d);
+  const long long NR = d.NB * d.M;
+  if (NR == 0 || d.N == 0) return;
+  RTCC_REQUIRE(NR < (1ll << 31) && d.N < (1ll << 31), "direct extents exceed 32-bit indexing");
+  const unsigned N = (unsigned)d.N;
+  const unsigned bx = N >= 128 ? 128u : std::max(32u, (N + 31) / 32 * 32);
+  const unsigned by = 128 / bx;
+  dim3 blk(bx, by);
+  dim3 grid(std::min((N + bx - 1) / bx, 4096u), (unsigned)std::min((NR + by - 1) / by, 65535ll));
+  direct_kernel<<<grid, blk, 0, s>>>(d);
   RTCC_CUDA(cudaGetLastError());
 }
 void launch_reduce(const DirectDesc& d, long long splits, cudaStream_t s) {
@@ -290,7 +502,14 @@ void launch_reduce(const DirectDesc& d, long long splits, cudaStream_t s) {
 }
 void launch_add(const AddDesc& d, cudaStream_t s) {
   if (d.n == 0) return;
-  add_kernel<<<grid_for(d.n), kThreads, 0, s>>>(d);
+  RTCC_REQUIRE(d.n < (1ll << 32) && d.c_all.n >= 1, "add extents exceed 32-bit indexing");
+  const unsigned inner = (unsigned)d.c_all.dims[d.c_all.n - 1];
+  const unsigned rows = (unsigned)(d.n / inner);
+  const unsigned bx = inner >= 256 ? 256u : std::max(32u, (inner + 31) / 32 * 32);
+  const unsigned by = 256 / bx;
+  dim3 blk(bx, by);
+  dim3 grid(std::min((inner + bx - 1) / bx, 4096u), std::min((rows + by - 1) / by, 65535u));
+  add_kernel<<<grid, blk, 0, s>>>(d, inner);
   RTCC_CUDA(cudaGetLastError());
 }
 void launch_gemm_f64(const double* A, const double* B, double* C, long long M, long long N, long long Kpad,

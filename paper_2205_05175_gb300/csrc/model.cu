@@ -10,6 +10,7 @@
 // Index letters: z trajectory, x dipole component, P auxiliary, i j m n occupied,
 // a b e f virtual.
 #include "model.cuh"
+#include <set>
 
 namespace rtcc {
 
@@ -137,8 +138,16 @@ struct Builder {
   Program& P;
   int arena;
   int nz, o, v;
+  int nx;   // extent of the operator label of Fock-dependent intermediates (0: none)
+  // amplitude-only intermediates carry the trajectory label z
   int tmp(const std::string& nm, std::vector<int> dims) {
     dims.insert(dims.begin(), nz);
+    return E.temp(arena, nm, dims, true);
+  }
+  // intermediates that depend on the one-body operator carry its label too ("xz" or "z")
+  int tmpf(const std::string& nm, std::vector<int> dims) {
+    dims.insert(dims.begin(), nz);
+    if (nx) dims.insert(dims.begin(), nx);
     return E.temp(arena, nm, dims, true);
   }
   void ein(int c, const std::string& lc, int a, const std::string& la, int b, const std::string& lb,
@@ -155,6 +164,7 @@ struct Builder {
 int residual_ops(Builder& b, const IntIds* I, int t1, int t2, const OneBody& f, int r1, int r2) {
   const int o = b.o, v = b.v;
   const std::string F = f.pre;
+  const std::string Q = b.nx ? "xz" : "z";   // labels of Fock-dependent intermediates
   using B = IntegralStore;
   auto V = [&](int k) { return I->b[k]; };
   const bool two = (I != nullptr);
@@ -169,61 +179,61 @@ int residual_ops(Builder& b, const IntIds* I, int t1, int t2, const OneBody& f, 
   b.add(taut, "zijab", tt, "zijab", 0.5);
 
   // one-body intermediates
-  const int Fae = b.tmp("Fae", {v, v});
-  b.add(Fae, "zae", f.vv, F + "ae");
-  b.ein(Fae, "zae", f.ov, F + "me", t1, "zma", -0.5);
-  const int Fmi = b.tmp("Fmi", {o, o});
-  b.add(Fmi, "zmi", f.oo, F + "mi");
-  b.ein(Fmi, "zmi", t1, "zie", f.ov, F + "me", 0.5);
-  const int Fme = b.tmp("Fme", {o, v});
-  b.add(Fme, "zme", f.ov, F + "me");
+  const int Fae = b.tmpf("Fae", {v, v});
+  b.add(Fae, Q + "ae", f.vv, F + "ae");
+  b.ein(Fae, Q + "ae", f.ov, F + "me", t1, "zma", -0.5);
+  const int Fmi = b.tmpf("Fmi", {o, o});
+  b.add(Fmi, Q + "mi", f.oo, F + "mi");
+  b.ein(Fmi, Q + "mi", t1, "zie", f.ov, F + "me", 0.5);
+  const int Fme = b.tmpf("Fme", {o, v});
+  b.add(Fme, Q + "me", f.ov, F + "me");
   if (two) {
-    b.ein(Fae, "zae", t1, "zmf", V(B::LOVVV), "mafe");
-    b.ein(Fae, "zae", taut, "zmnaf", V(B::LOOVV), "mnef", -1.0);
-    b.ein(Fmi, "zmi", t1, "zne", V(B::LOOOV), "mnie");
-    b.ein(Fmi, "zmi", taut, "zinef", V(B::LOOVV), "mnef");
-    b.ein(Fme, "zme", t1, "znf", V(B::LOOVV), "mnef");
+    b.ein(Fae, Q + "ae", t1, "zmf", V(B::LOVVV), "mafe");
+    b.ein(Fae, Q + "ae", taut, "zmnaf", V(B::LOOVV), "mnef", -1.0);
+    b.ein(Fmi, Q + "mi", t1, "zne", V(B::LOOOV), "mnie");
+    b.ein(Fmi, Q + "mi", taut, "zinef", V(B::LOOVV), "mnef");
+    b.ein(Fme, Q + "me", t1, "znf", V(B::LOOVV), "mnef");
   }
 
   // singles
   const int t2t = b.tmp("t2t", {o, o, v, v});   // 2 t_imae - t_imea
   b.add(t2t, "zimae", t2, "zimae", 2.0);
   b.add(t2t, "zimae", t2, "zimea", -1.0);
-  b.add(r1, "zia", f.ov, F + "ia");
-  b.ein(r1, "zia", t1, "zie", Fae, "zae");
-  b.ein(r1, "zia", t1, "zma", Fmi, "zmi", -1.0);
-  b.ein(r1, "zia", t2t, "zimae", Fme, "zme");
+  b.add(r1, Q + "ia", f.ov, F + "ia");
+  b.ein(r1, Q + "ia", t1, "zie", Fae, Q + "ae");
+  b.ein(r1, Q + "ia", t1, "zma", Fmi, Q + "mi", -1.0);
+  b.ein(r1, Q + "ia", t2t, "zimae", Fme, Q + "me");
   if (two) {
-    b.ein(r1, "zia", t1, "znf", V(B::LOVVO), "nafi");
-    b.ein(r1, "zia", t2, "zimef", V(B::LOVVV), "mafe");
-    b.ein(r1, "zia", t2, "zmnae", V(B::LOOVO), "nmei", -1.0);
+    b.ein(r1, Q + "ia", t1, "znf", V(B::LOVVO), "nafi");
+    b.ein(r1, Q + "ia", t2, "zimef", V(B::LOVVV), "mafe");
+    b.ein(r1, Q + "ia", t2, "zmnae", V(B::LOOVO), "nmei", -1.0);
   }
 
   // doubles: Omega2 = S + S^(i<->j, a<->b)
-  const int Xbe = b.tmp("Xbe", {v, v});
-  b.add(Xbe, "zbe", Fae, "zbe");
-  b.ein(Xbe, "zbe", t1, "zmb", Fme, "zme", -0.5);
-  const int Zmj = b.tmp("Zmj", {o, o});
-  b.add(Zmj, "zmj", Fmi, "zmj");
-  b.ein(Zmj, "zmj", t1, "zje", Fme, "zme", 0.5);
-  const int S = b.tmp("S", {o, o, v, v});
-  b.ein(S, "zijab", t2, "zijae", Xbe, "zbe");
-  b.ein(S, "zijab", t2, "zimab", Zmj, "zmj", -1.0);
+  const int Xbe = b.tmpf("Xbe", {v, v});
+  b.add(Xbe, Q + "be", Fae, Q + "be");
+  b.ein(Xbe, Q + "be", t1, "zmb", Fme, Q + "me", -0.5);
+  const int Zmj = b.tmpf("Zmj", {o, o});
+  b.add(Zmj, Q + "mj", Fmi, Q + "mj");
+  b.ein(Zmj, Q + "mj", t1, "zje", Fme, Q + "me", 0.5);
+  const int S = b.tmpf("S", {o, o, v, v});
+  b.ein(S, Q + "ijab", t2, "zijae", Xbe, Q + "be");
+  b.ein(S, Q + "ijab", t2, "zimab", Zmj, Q + "mj", -1.0);
   if (two) {
-    b.add(S, "zijab", V(B::OOVV), "ijab", 0.5);
+    b.add(S, Q + "ijab", V(B::OOVV), "ijab", 0.5);
     // particle-particle ladder (half: the symmetrisation doubles it)
-    b.ein(S, "zijab", tau, "zijef", V(B::VVVV), "abef", 0.5);
+    b.ein(S, Q + "ijab", tau, "zijef", V(B::VVVV), "abef", 0.5);
     // hole-hole ladder with W_mnij = <mn|ij> + P t1 terms + tau <mn|ef>
     const int Wmnij = b.tmp("Wmnij", {o, o, o, o});
     b.add(Wmnij, "zmnij", V(B::OOOO), "mnij");
     b.ein(Wmnij, "zmnij", t1, "zje", V(B::OOOV), "mnie");
     b.ein(Wmnij, "zmnij", t1, "zie", V(B::OOVO), "mnej");
     b.ein(Wmnij, "zmnij", tau, "zijef", V(B::OOVV), "mnef");
-    b.ein(S, "zijab", tau, "zmnab", Wmnij, "zmnij", 0.5);
+    b.ein(S, Q + "ijab", tau, "zmnab", Wmnij, "zmnij", 0.5);
     // t1 pieces of the particle-particle ladder
     const int Zijmb = b.tmp("Zijmb", {o, o, o, v});
     b.ein(Zijmb, "zijmb", tau, "zijef", V(B::OVVV), "mbef");
-    b.ein(S, "zijab", t1, "zma", Zijmb, "zijmb", -1.0);
+    b.ein(S, Q + "ijab", t1, "zma", Zijmb, "zijmb", -1.0);
     // ring intermediates: (m a, b b, e a, j b) and (m a, b b, e b, j a) spin blocks of W_mbej
     const int t1t1 = b.tmp("t1t1", {o, o, v, v});
     b.ein(t1t1, "zjnfb", t1, "zjf", t1, "znb");
@@ -242,21 +252,21 @@ int residual_ops(Builder& b, const IntIds* I, int t1, int t2, const OneBody& f, 
     b.ein(U, "zmbej", t1, "zjf", V(B::OVVV), "mbfe", -1.0);
     b.ein(U, "zmbej", t1, "znb", V(B::OOOV), "mnje");
     b.ein(U, "zmbej", Uh, "zjnfb", V(B::OOVV), "mnfe");
-    b.ein(S, "zijab", t2t, "zimae", Wa, "zmbej");
-    b.ein(S, "zijab", t2, "zimae", U, "zmbej");
-    b.ein(S, "zijab", t2, "zmjae", U, "zmbei");
+    b.ein(S, Q + "ijab", t2t, "zimae", Wa, "zmbej");
+    b.ein(S, Q + "ijab", t2, "zimae", U, "zmbej");
+    b.ein(S, Q + "ijab", t2, "zmjae", U, "zmbei");
     // t1 t1 <mb|ej> and t1 t1 <mb|ie> rings, t1 <ab|ej>, t1 <mb|ij>
     const int Q1 = b.tmp("Q1", {o, v, o, o});
     b.ein(Q1, "zmbij", t1, "zie", V(B::OVVO), "mbej");
-    b.ein(S, "zijab", t1, "zma", Q1, "zmbij", -1.0);
+    b.ein(S, Q + "ijab", t1, "zma", Q1, "zmbij", -1.0);
     const int Q2 = b.tmp("Q2", {o, v, o, o});
     b.ein(Q2, "zmbji", t1, "zje", V(B::OVOV), "mbie");
-    b.ein(S, "zijab", t1, "zma", Q2, "zmbji", -1.0);
-    b.ein(S, "zijab", t1, "zie", V(B::VVVO), "abej");
-    b.ein(S, "zijab", t1, "zma", V(B::OVOO), "mbij", -1.0);
+    b.ein(S, Q + "ijab", t1, "zma", Q2, "zmbji", -1.0);
+    b.ein(S, Q + "ijab", t1, "zie", V(B::VVVO), "abej");
+    b.ein(S, Q + "ijab", t1, "zma", V(B::OVOO), "mbij", -1.0);
   }
-  b.add(r2, "zijab", S, "zijab");
-  b.add(r2, "zijab", S, "zjiba");
+  b.add(r2, Q + "ijab", S, Q + "ijab");
+  b.add(r2, Q + "ijab", S, Q + "jiba");
   return tau;
 }
 
@@ -279,7 +289,7 @@ RhsPrograms build_rhs(Engine& E, const IntIds& I, int nz, int o, int v, double* 
   R.fwd.zero_arenas = {fa};
   const long long ns = 2ll * o * v + 2ll * o * o * v * v, nT = (long long)o * v + (long long)o * o * v * v;
   R.fwd.zero2d = {{out, (size_t)ns * 16, (size_t)nT * 16, (size_t)nz}};
-  Builder b{E, R.fwd, fa, nz, o, v};
+  Builder b{E, R.fwd, fa, nz, o, v, 0};
   R.t1 = in.x1;
   R.t2 = in.x2;
   R.l1 = in.y1;
@@ -306,33 +316,58 @@ RhsPrograms build_rhs(Engine& E, const IntIds& I, int nz, int o, int v, double* 
 
 DipolePrograms build_dipole(Engine& E, int nz, int o, int v, double* state, const double* mu_dev,
                             double* dip_out) {
+  // The dipole is the one-body Lagrangian evaluated with f -> mu_x (Eq. dipole).  That Lagrangian is
+  // linear in the one-body operator, L1(f) = sum_pq rho_pq f_pq, so rho = dL1/df is the one-particle
+  // density: one reverse sweep of the one-body program with f as the active input gives rho for
+  // every trajectory, and mu_x = 2 sum_i mu_x,ii + sum_pq rho_pq mu_x,pq.
   DipolePrograms D;
   const int n = o + v;
   const StateViews in = state_views(E, "yd", state, nz, o, v);
-  const int arena = E.new_arena();
-  // per-component one-body residual buffers (shared by the three programs, run in turn)
-  const int om1 = E.temp(arena, "om1mu", {nz, o, v}, true);
-  const int om2 = E.temp(arena, "om2mu", {nz, o, o, v, v}, true);
-  const long long mark = E.arena_mark(arena);
-  for (int x = 0; x < 3; ++x) {
-    E.arena_reset(arena, mark);
-    Program& P = D.prog[x];
-    P.name = "dipole" + std::to_string(x);
-    P.zero_arenas = {arena};
-    const double* mx = mu_dev + (size_t)x * n * n;
-    OneBody f;
-    f.pre = "";
-    f.oo = E.external("mu.oo", {o, o}, false, const_cast<double*>(mx), {n, 1}, true);
-    f.ov = E.external("mu.ov", {o, v}, false, const_cast<double*>(mx) + o, {n, 1}, true);
-    f.vv = E.external("mu.vv", {v, v}, false, const_cast<double*>(mx) + (size_t)o * n + o, {n, 1}, true);
-    Builder b{E, P, arena, nz, o, v};
-    residual_ops(b, nullptr, in.x1, in.x2, f, om1, om2);
-    const int dx = E.external("dip" + std::to_string(x), {nz}, true, dip_out + 2 * (size_t)x * nz);
-    P.zero_tensors = {dx};
-    Engine::ein(P, dx, "z", f.ov, "ia", in.x1, "zia", 2.0);
-    Engine::ein(P, dx, "z", in.y1, "zia", om1, "zia");
-    Engine::ein(P, dx, "z", in.y2, "zijab", om2, "zijab");
+  const int fa = E.new_arena();
+  const int ra = E.new_arena();
+  Program fwd;
+  fwd.name = "dens_fwd";
+  // a placeholder operator buffer: the pruned forward never reads it and the reverse pass only needs
+  // the amplitude-only intermediates
+  const long long sf = (long long)n * n;
+  D.fdummy = static_cast<double*>(dev_alloc(sizeof(double) * (size_t)nz * n * n));
+  RTCC_CUDA(cudaMemset(D.fdummy, 0, sizeof(double) * (size_t)nz * n * n));
+  OneBody f;
+  f.pre = "z";
+  f.oo = E.external("fd.oo", {nz, o, o}, false, D.fdummy, {sf, n, 1});
+  f.ov = E.external("fd.ov", {nz, o, v}, false, D.fdummy + o, {sf, n, 1});
+  f.vv = E.external("fd.vv", {nz, v, v}, false, D.fdummy + (size_t)o * n + o, {sf, n, 1});
+  Builder b{E, fwd, fa, nz, o, v, 0};
+  const int om1 = b.tmp("om1mu", {o, v});
+  const int om2 = b.tmp("om2mu", {o, o, v, v});
+  residual_ops(b, nullptr, in.x1, in.x2, f, om1, om2);
+  std::map<int, int> adj;
+  Program rev = E.reverse(fwd, {f.oo, f.ov, f.vv}, ra, adj);
+  // keep only the forward ops that do not depend on the operator (amplitude-only intermediates)
+  std::set<int> dep = {f.oo, f.ov, f.vv};
+  Program& P = D.prog;
+  P.name = "dipole";
+  P.force_p64 = true;   // the recorded observable is evaluated in float64 in every precision mode
+  P.zero_arenas = {fa, ra};
+  for (const Op& op : fwd.ops) {
+    const bool d = dep.count(op.a) || (op.kind == OP_EIN && dep.count(op.b));
+    if (d) dep.insert(op.c);
+    else P.ops.push_back(op);
   }
+  // seeds: dL1/dOmega1 = l1, dL1/dOmega2 = l2, dE1/df_ov = 2 t1
+  P.ops.push_back(Op{OP_ADD, adj.at(om1), in.y1, -1, "zia", "zia", "", 1.0});
+  P.ops.push_back(Op{OP_ADD, adj.at(om2), in.y2, -1, "zijab", "zijab", "", 1.0});
+  P.ops.push_back(Op{OP_ADD, adj.at(f.ov), in.x1, -1, "zia", "zia", "", 2.0});
+  for (const Op& op : rev.ops) P.ops.push_back(op);
+  double* m = const_cast<double*>(mu_dev);
+  const int moo = E.external("mu.oo", {3, o, o}, false, m, {sf, n, 1}, true);
+  const int mov = E.external("mu.ov", {3, o, v}, false, m + o, {sf, n, 1}, true);
+  const int mvv = E.external("mu.vv", {3, v, v}, false, m + (size_t)o * n + o, {sf, n, 1}, true);
+  const int dx = E.external("dip", {3, nz}, true, dip_out);
+  P.zero_tensors = {dx};
+  Engine::ein(P, dx, "xz", moo, "xij", adj.at(f.oo), "zij");
+  Engine::ein(P, dx, "xz", mov, "xia", adj.at(f.ov), "zia");
+  Engine::ein(P, dx, "xz", mvv, "xab", adj.at(f.vv), "zab");
   return D;
 }
 

@@ -41,7 +41,8 @@ RhsPrograms build_rhs(Engine& E, const IntIds& I, int nz, int o, int v, double* 
 // Dipole of the state views: for each component x, mu_xz = E[mu_x] + l.Omega[mu_x]
 // (one-body programs; the reference term 2 sum_i mu_ii is added by the caller).
 struct DipolePrograms {
-  Program prog[3];
+  Program prog;
+  double* fdummy = nullptr;   // placeholder operator buffer (owned by the caller's allocation list)
 };
 DipolePrograms build_dipole(Engine& E, int nz, int o, int v, double* state, const double* mu_dev,
                             double* dip_out);

@@ -5,6 +5,8 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <cstdio>
+#include <cstdlib>
 
 namespace rtcc {
 namespace {
@@ -439,6 +441,8 @@ struct GroundEngine {
   Program energy;
   double *Y = nullptr, *R = nullptr, *F = nullptr, *Ec = nullptr;
   double *hx = nullptr, *he = nullptr, *dots = nullptr;   // DIIS history (one amplitude block)
+  double* DIP = nullptr;
+  DipolePrograms dip;
   unsigned long long* scratch = nullptr;
 };
 
@@ -505,7 +509,7 @@ void copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
 }
 
 void run_dipole(rtcc_ctx* h) {
-  for (int x = 0; x < 3; ++x) h->E->run(h->dip.prog[x]);
+  h->E->run(h->dip.prog);
 }
 
 // One Runge-Kutta attempt over all trajectories (stages, combination, controller, accept, dipole, record).
@@ -592,7 +596,14 @@ GroundEngine* ground_engine(rtcc_ctx* h, Prec p) {
   RTCC_CUDA(cudaMemcpyAsync(g->F, h->f0, sizeof(double) * h->nmo * h->nmo, cudaMemcpyDeviceToDevice, h->stream));
   g->rhs = build_rhs(E, I, 1, h->o, h->v, g->Y, g->F, g->R, true);
   g->energy = build_energy(E, I, g->rhs, 1, h->o, h->v, g->F, g->Ec);
-  E.finalize({&g->rhs.fwd, &g->rhs.rev, &g->energy});
+  g->DIP = h->alloc<double>(6);
+  if (p == Prec::P64) {
+    g->dip = build_dipole(E, 1, h->o, h->v, g->Y, h->mu, g->DIP);
+    h->allocs.push_back(g->dip.fdummy);
+    E.finalize({&g->rhs.fwd, &g->rhs.rev, &g->energy, &g->dip.prog});
+  } else {
+    E.finalize({&g->rhs.fwd, &g->rhs.rev, &g->energy});
+  }
   slot = std::move(g);
   return slot.get();
 }
@@ -624,6 +635,9 @@ double solve_block(rtcc_ctx* h, GroundEngine* g, bool lambda, double tol, int ma
     if (lambda) g->E->run(g->rhs.rev);
     else g->E->run(g->rhs.fwd);
     const double err = read_max(h, r, nT, g->scratch);
+    if (std::getenv("RTCC_VERBOSE"))
+      std::fprintf(stderr, "[rtcc] ground state %s prec=%d iter %d max|residual| %.3e\n", lambda ? "Lambda" : "T",
+                   (int)g->E->prec(), it, err);
     if (!std::isfinite(err)) throw Error(RTCC_ERR_DIVERGED, "ground-state residual is not finite");
     if (err < tol) return err;
     if (err < 0.999 * best) {
@@ -767,7 +781,8 @@ rtcc_status_t rtcc_create(const double* f, const double* B, int naux, const doub
     const IntIds I = register_integrals(*h->E, *h->ints);
     h->rhs = build_rhs(*h->E, I, h->nz, o, v, h->Ys, h->F, h->Rout, true);
     h->dip = build_dipole(*h->E, h->nz, o, v, h->Y, h->mu, h->DIP);
-    h->E->finalize({&h->rhs.fwd, &h->rhs.rev, &h->dip.prog[0], &h->dip.prog[1], &h->dip.prog[2]});
+    h->allocs.push_back(h->dip.fdummy);
+    h->E->finalize({&h->rhs.fwd, &h->rhs.rev, &h->dip.prog});
     h->E->set_profiler(&h->prof);
     RTCC_CUDA(cudaStreamSynchronize(h->stream));
   });
@@ -881,11 +896,11 @@ rtcc_status_t rtcc_ground_state(rtcc_handle_t h, double tol, int maxiter, double
     g->E->check_error();
     if (e_corr) *e_corr = ec[0];
     if (mu0) {
-      run_dipole(h);
-      std::vector<double> d((size_t)6 * h->nz);
-      RTCC_CUDA(cudaMemcpyAsync(d.data(), h->DIP, sizeof(double) * d.size(), cudaMemcpyDeviceToHost, h->stream));
+      g->E->run(g->dip.prog);
+      double d[6];
+      RTCC_CUDA(cudaMemcpyAsync(d, g->DIP, sizeof(d), cudaMemcpyDeviceToHost, h->stream));
       RTCC_CUDA(cudaStreamSynchronize(h->stream));
-      for (int x = 0; x < 3; ++x) mu0[x] = d[2 * x * h->nz] + h->mu_ref[x];
+      for (int x = 0; x < 3; ++x) mu0[x] = d[2 * x] + h->mu_ref[x];
     }
   });
 }
@@ -944,12 +959,16 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
       RTCC_CUDA(cudaGraphInstantiate(&exec, graph, 0));
       cudaGraphDestroy(graph);
     }
-    std::vector<int> stat(nz);
+    std::vector<int> stat(nz), stp(nz);
+    std::vector<double> tz(nz), hz(nz);
     long long attempts = 1;
     const long long max_attempts = (in.nsteps > 0) ? (long long)in.nsteps * 64 + 64 : (1ll << 40);
     int check_every = 4;
     while (true) {
       RTCC_CUDA(cudaMemcpyAsync(stat.data(), h->ctl.status, sizeof(int) * nz, cudaMemcpyDeviceToHost, s));
+      RTCC_CUDA(cudaMemcpyAsync(stp.data(), h->ctl.steps, sizeof(int) * nz, cudaMemcpyDeviceToHost, s));
+      RTCC_CUDA(cudaMemcpyAsync(tz.data(), h->ctl.t, sizeof(double) * nz, cudaMemcpyDeviceToHost, s));
+      RTCC_CUDA(cudaMemcpyAsync(hz.data(), h->ctl.h, sizeof(double) * nz, cudaMemcpyDeviceToHost, s));
       RTCC_CUDA(cudaStreamSynchronize(s));
       h->E->check_error();
       bool running = false;
@@ -961,8 +980,19 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
       }
       if (!running) break;
       if (attempts >= max_attempts) throw Error(RTCC_ERR_TIMEOUT, "attempt limit reached");
-      long long k = check_every;
-      if (in.nsteps > 0 && in.method != RTCC_CK) k = std::max(1ll, std::min<long long>(k, in.nsteps - attempts));
+      // every running trajectory needs at least `need` more attempts: replay that many before polling
+      long long need = 1ll << 40;
+      for (int z = 0; z < nz; ++z) {
+        if (stat[z] != TS_RUN) continue;
+        long long nz_need;
+        if (in.nsteps > 0) nz_need = in.nsteps - stp[z];
+        else {
+          const double hstep = (in.method == RTCC_CK) ? hz[z] * 5.0 : (in.method == RTCC_RK4 ? in.h : std::max(in.h1, in.h2));
+          nz_need = (long long)std::floor((in.t_end - tz[z]) / hstep);
+        }
+        need = std::min(need, nz_need);
+      }
+      const long long k = std::max(1ll, std::min<long long>(need, check_every));
       for (long long q = 0; q < k; ++q) {
         if (exec) RTCC_CUDA(cudaGraphLaunch(exec, s));
         else run_attempt(h, tb, in, tout, muout, max_out);

@@ -4,12 +4,13 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-# bound on max|C - C_ref| / (max|A| max|B| K) for each precision mode
+# bound on max|C - C_ref| / (max|A| max|B| K) for each precision mode; the shapes cover
+# ragged M/N/K tails, several tiles, split-K (long K, few tiles) and grouped rasterisation
 TOL = {0: 1e-15, 1: 2e-3, 2: 2e-6, 3: 3e-5}
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2, 3])
-@pytest.mark.parametrize("shape", [(1, 8, 8, 4), (2, 300, 200, 77), (1, 129, 257, 130), (3, 64, 40, 1000)])
+@pytest.mark.parametrize("shape", [(1, 8, 8, 4), (2, 300, 200, 77), (1, 129, 257, 130), (3, 64, 40, 1000), (2, 40, 30, 6000), (1, 1100, 700, 300)])
 def test_gemm_matches_float64(prec, shape):
     from paper_2205_05175_gb300 import rtcc
     nb, M, N, K = shape
