@@ -199,11 +199,12 @@ rtcc_status_t rtcc_spectrum(const double* t, const double* mu, int n, const rtcc
 const char* rtcc_last_error(void);
 
 /* Library self-test of the contraction core (not part of the method): computes
- * C[b][m][n] = sum_k A[b][m][k] * Bm[b][n][k] for float64 host or device inputs with
- * the handle-independent GEMM path of precision `prec` (TF32/3xTF32/BF16x3 run on
- * the tcgen05 tensor cores, P64 on the float64 path).  C is float64 host or device.
- * Errors: INVALID_ARG, CUDA, TIMEOUT. */
-rtcc_status_t rtcc_selftest_gemm(int prec, int batch, int M, int N, int K, const double* A,
+ * C[b][m][n] = sum_k A[b][m][k] * Bm[b][n][k] for host or device inputs with the
+ * handle-independent GEMM path of precision `prec` (TF32/3xTF32/BF16x3 run on the
+ * tcgen05 tensor cores, P64 on the float64 path).  cplx bit 0: A is complex
+ * (interleaved re, im), bit 1: Bm is complex; C (host or device) is complex when either
+ * operand is.  Errors: INVALID_ARG, CUDA, TIMEOUT. */
+rtcc_status_t rtcc_selftest_gemm(int prec, int cplx, int batch, int M, int N, int K, const double* A,
                                  const double* Bm, double* C);
 
 #ifdef __cplusplus

@@ -64,6 +64,7 @@ inline long long imap_size(const IndexMap& m) {
 //  value = sign[rb][cs] * component(src(m,k), comp[rb][cs]) then split part[ss].
 enum PackElem : int { PE_F32 = 0, PE_BF16 = 1, PE_F64 = 2 };
 enum SplitPart : int { SP_FULL = 0, SP_HI = 1, SP_LO = 2 };
+constexpr int kMaxRb = 4;
 struct PackDesc {
   const double* src;
   int src_cplx;
@@ -72,13 +73,17 @@ struct PackDesc {
   IndexMap bat;     // batch labels
   long long R, K, NB;
   int nrb, ncs, nss;
-  int comp[2][2];   // 0 = re, 1 = im
-  int sign[2][2];
-  int part[3];
+  int comp[kMaxRb][2];   // 0 = re, 1 = im
+  int sign[kMaxRb][2];
+  int part[3];           // split part per column segment (when nss > 1)
+  int rb_part[kMaxRb];   // split part per row block (when nss == 1): planes of a tensor-core operand
   long long Kpad;   // padded row length of the packed matrix
   int elem;         // PackElem
   int round_tf32;   // round float32 values to TF32 (round-to-nearest) when packing
   int transpose;    // 1: the source's unit-stride index is a row index (shared-memory tile transpose)
+  // transpose mode: rows are enumerated in "read order" (the source's unit-stride label last);
+  // rd_src gives the source offset and rd_dst the packed row index of a read-order row
+  IndexMap rd_src, rd_dst;
   void* dst;
 };
 
@@ -126,19 +131,55 @@ void launch_add(const AddDesc& d, cudaStream_t s);
 void launch_gemm_f64(const double* A, const double* B, double* C, long long M, long long N,
                      long long Kpad, long long NB, cudaStream_t s);
 
-// tcgen05 GEMM: C[b][m][n] = sum_k A[b][m][k] B[b][n][k], A/B packed (float32 as TF32 or bf16),
-// rows padded to Kpad (multiple of the 128-byte K block).  C float32 row-major [NB][M][N].
-struct TcGemmPlan {
-  CUtensorMap tmA, tmB;
-  int kind;        // 0 tf32, 1 bf16
-  int bn;          // N tile (64, 128 or 256)
-  long long M, N, Kpad, NB;
-  float* C;
-  int* err;        // device error word
+// tcgen05 GEMM over operand planes.  The packed A holds planes (re/im x hi/lo) of M rows each,
+// B planes of N rows; every row is Kpad elements (whole 128-byte K blocks).  Output plane rb
+// (0 = real part, 1 = imaginary part) is  sum_s (-1)^neg_s A[planeA_s] B[planeB_s]^T, accumulated
+// in TMEM and added (times a real alpha) straight into the strided float64 output tensor.
+constexpr int kMaxSeg = 8;
+struct TcSeg {
+  int pa, pb, neg;
 };
-void tc_gemm_plan(TcGemmPlan& p, int kind, const void* A, const void* B, float* C, long long M,
+struct TcEpilogue {
+  double* C;
+  int c_cplx;
+  double alpha;
+  IndexMap cm, cn, cb;
+  int flat_n;          // 1: C offset of column n is rowoff + n * sn
+  long long sn;
+  int unit_n;          // 1: the output's unit stride runs along n (write through a shared-memory transpose)
+};
+struct TcGemmParams {
+  CUtensorMap tmA, tmB;
+  int M, N, nkb;       // rows of one A plane, rows of one B plane, K blocks per plane
+  int nrb;             // output planes
+  int nseg[2];
+  TcSeg seg[2][kMaxSeg];
+  int vper;            // virtual K blocks (segments x nkb) per split
+  TcEpilogue epi;
+  int* err;            // device error word
+};
+struct TcGemmPlan {
+  TcGemmParams p;
+  int kind;            // 0 tf32, 1 bf16
+  int bn;              // N tile (64, 128 or 256)
+  int splits;
+  long long NB;
+};
+void tc_gemm_plan(TcGemmPlan& pl, int kind, const void* A, int planesA, const void* B, int planesB, long long M,
                   long long N, long long Kpad, long long NB, int* err);
 void launch_tc_gemm(const TcGemmPlan& p, cudaStream_t s);
 int tc_kblock_elems(int kind);   // K elements per 128-byte block: 32 (tf32) or 64 (bf16)
+
+// 32-bit mixed-radix decode of one index group (extents < 2^31 per group).
+__device__ __forceinline__ long long imap32(const IndexMap& m, unsigned idx) {
+  long long off = 0;
+  for (int d = m.n - 1; d >= 0; --d) {
+    const unsigned dim = (unsigned)m.dims[d];
+    const unsigned q = idx / dim;
+    off += (long long)(idx - q * dim) * m.strides[d];
+    idx = q;
+  }
+  return off;
+}
 
 }  // namespace rtcc

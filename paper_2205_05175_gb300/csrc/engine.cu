@@ -45,6 +45,36 @@ std::string by_stride(const std::string& labs, const Tensor& t, const std::strin
   return out;
 }
 
+// Chooses how a pack reads its source: directly along K when the source's unit-stride label is the
+// last K label, else through shared-memory tiles enumerated with the unit-stride row label last.
+void choose_pack_mode(PackDesc& pd, const Tensor& t, const std::string& tl, const std::string& rows,
+                      const std::string& cols) {
+  pd.transpose = 0;
+  char u = 0;
+  long long bs = -1;
+  for (char l : rows + cols) {
+    const long long st = std::llabs(t.strides[tl.find(l)]);
+    if (bs < 0 || st < bs) {
+      bs = st;
+      u = l;
+    }
+  }
+  if (u == 0 || rows.find(u) == std::string::npos) return;
+  std::string rd = rows;
+  rd.erase(rd.find(u), 1);
+  rd.push_back(u);
+  std::map<char, long long> P;
+  long long acc = 1;
+  for (int i = (int)rows.size() - 1; i >= 0; --i) {
+    P[rows[i]] = acc;
+    acc *= t.dims[tl.find(rows[i])];
+  }
+  pd.rd_src = map_for(t, tl, rd);
+  pd.rd_dst = pd.rd_src;
+  for (int i = 0; i < pd.rd_dst.n; ++i) pd.rd_dst.strides[i] = P[rd[i]];
+  pd.transpose = 1;
+}
+
 // True when the smallest-stride label of t among (rows + cols) is the last row label.
 bool row_is_unit(const Tensor& t, const std::string& tl, const std::string& rows, const std::string& cols) {
   if (rows.empty()) return false;
@@ -147,6 +177,8 @@ void Profiler::end(long long launches[KC_N], double ms[KC_N], double flops[KC_N]
   recs_.clear();
   used_ = 0;
 }
+
+static bool C_cplx_of(const Compiled& k) { return k.tcp.p.epi.c_cplx != 0; }
 
 void* dev_alloc(size_t bytes) {
   void* p = nullptr;
@@ -279,7 +311,7 @@ Program Engine::reverse(const Program& fwd, const std::vector<int>& active_input
 
 void Engine::plan(Program& P) {
   P.comp.clear();
-  const Prec prec = P.force_p64 ? Prec::P64 : prec_;
+  const Prec prec = P.prec_override >= 0 ? (Prec)P.prec_override : prec_;
   for (const Op& op : P.ops) {
     auto cp = std::make_shared<Compiled>();
     Compiled& k = *cp;
@@ -332,10 +364,15 @@ void Engine::plan(Program& P) {
     for (char l : op.lb)
       if (op.lc.find(l) == std::string::npos)
         RTCC_REQUIRE(op.la.find(l) != std::string::npos, std::string("dangling label ") + l + " in " + P.name);
-    // label orders: unit-stride labels last for the operands that are packed every run
-    Lm = A.constant ? by_stride(Lm, C, op.lc) : by_stride(Lm, A, op.la);
-    Ln = B.constant ? by_stride(Ln, C, op.lc) : by_stride(Ln, B, op.lb);
-    Lk = !A.constant ? by_stride(Lk, A, op.la) : (!B.constant ? by_stride(Lk, B, op.lb) : Lk);
+    // label orders: M and N follow the output (the GEMM epilogue writes it in place), K follows the
+    // larger operand that is packed every run; packs transpose through shared memory as needed
+    Lm = by_stride(Lm, C, op.lc);
+    Ln = by_stride(Ln, C, op.lc);
+    {
+      const bool use_a = !A.constant && (B.constant || A.numel() >= tensors_[op.b].numel());
+      if (use_a) Lk = by_stride(Lk, A, op.la);
+      else if (!tensors_[op.b].constant) Lk = by_stride(Lk, tensors_[op.b], op.lb);
+    }
     // extent consistency
     auto ext = [&](const Tensor& t, const std::string& tl, char l) { return t.dims[tl.find(l)]; };
     for (char l : op.lc) {
@@ -391,7 +428,99 @@ void Engine::plan(Program& P) {
     } else {
       k.kind = CK_GEMM;
     }
-    if (k.kind == CK_GEMM) {
+    if (k.kind == CK_GEMM && prec != Prec::P64) {
+      // tensor-core path: operands packed as planes (re/im x hi/lo), segment table per output plane
+      const bool x3 = (prec == Prec::TF32X3 || prec == Prec::BF16X3);
+      const int npart = x3 ? 2 : 1;
+      const int elem = (prec == Prec::BF16X3) ? PE_BF16 : PE_F32;
+      const int esz = (elem == PE_F32) ? 4 : 2;
+      k.tc_kind = (prec == Prec::BF16X3) ? 1 : 0;
+      const long long Kp = round_up(K, tc_kblock_elems(k.tc_kind));
+      auto planes = [&](PackDesc& pd, const Tensor& T, const IndexMap& rows, const IndexMap& cols,
+                        const IndexMap& bat, long long R) {
+        pd = PackDesc{};
+        pd.src = T.ptr;
+        pd.src_cplx = T.cplx;
+        pd.rows = rows;
+        pd.cols = cols;
+        pd.bat = bat;
+        pd.R = R;
+        pd.K = K;
+        pd.NB = NB;
+        const int nc = T.cplx ? 2 : 1;
+        pd.nrb = nc * npart;
+        pd.ncs = 1;
+        pd.nss = 1;
+        for (int c = 0; c < nc; ++c)
+          for (int q = 0; q < npart; ++q) {
+            const int rb = c * npart + q;
+            pd.comp[rb][0] = c;
+            pd.sign[rb][0] = 1;
+            pd.rb_part[rb] = (npart == 1) ? SP_FULL : (q == 0 ? SP_HI : SP_LO);
+          }
+        pd.Kpad = Kp;
+        pd.elem = elem;
+        pd.round_tf32 = 1;
+      };
+      planes(k.pa, A, d.am, d.ak, d.ab, M);
+      planes(k.pb, B, d.bn, d.bk, d.bb, N);
+      choose_pack_mode(k.pa, A, op.la, Lm, Lk);
+      choose_pack_mode(k.pb, B, op.lb, Ln, Lk);
+      TcGemmParams& g = k.tcp.p;
+      g = TcGemmParams{};
+      g.nrb = (A.cplx || B.cplx) ? 2 : 1;
+      auto pl = [&](int c, int q) { return c * npart + q; };
+      auto pair = [&](int rb, int ca, int cb, int neg) {
+        auto push = [&](int pa_, int pb_) {
+          RTCC_REQUIRE(g.nseg[rb] < kMaxSeg, "too many GEMM segments");
+          g.seg[rb][g.nseg[rb]++] = TcSeg{pa_, pb_, neg};
+        };
+        if (npart == 1) push(pl(ca, 0), pl(cb, 0));
+        else {
+          push(pl(ca, 0), pl(cb, 0));   // hi hi
+          push(pl(ca, 0), pl(cb, 1));   // hi lo
+          push(pl(ca, 1), pl(cb, 0));   // lo hi
+        }
+      };
+      if (!A.cplx && !B.cplx) {
+        pair(0, 0, 0, 0);
+      } else if (A.cplx && !B.cplx) {
+        pair(0, 0, 0, 0);
+        pair(1, 1, 0, 0);
+      } else if (!A.cplx && B.cplx) {
+        pair(0, 0, 0, 0);
+        pair(1, 0, 1, 0);
+      } else {   // (Ar + i Ai)(Br + i Bi): re = Ar Br - Ai Bi, im = Ar Bi + Ai Br
+        pair(0, 0, 0, 0);
+        pair(0, 1, 1, 1);
+        pair(1, 0, 1, 0);
+        pair(1, 1, 0, 0);
+      }
+      RTCC_REQUIRE(op.alpha.imag() == 0.0, "tensor-core contractions take a real scale factor");
+      TcEpilogue& ep = g.epi;
+      ep.c_cplx = C.cplx;
+      ep.alpha = op.alpha.real();
+      ep.cm = d.cm;
+      ep.cn = d.cn;
+      ep.cb = d.cb;
+      ep.flat_n = 1;
+      for (int i = 0; i + 1 < ep.cn.n; ++i)
+        if (ep.cn.strides[i] != ep.cn.strides[i + 1] * ep.cn.dims[i + 1]) ep.flat_n = 0;
+      ep.sn = ep.cn.n ? ep.cn.strides[ep.cn.n - 1] : 0;
+      ep.unit_n = (Ln.size() > 0 && !row_is_unit(C, op.lc, Lm, Ln)) ? 1 : 0;
+      k.Kpad = Kp;
+      k.NB = NB;
+      k.GM = (long long)k.pa.nrb * M;
+      k.GN = (long long)k.pb.nrb * N;
+      k.a_const = A.constant;
+      k.b_const = B.constant;
+      k.a_bytes = (size_t)(NB * k.GM * Kp * esz);
+      k.b_bytes = (size_t)(NB * k.GN * Kp * esz);
+      k.c_bytes = 0;
+      k.exec_flops = 2 * NB * M * N * K * (long long)(g.nseg[0] + g.nseg[1]);
+      if (!k.a_const) wsA_bytes_ = std::max(wsA_bytes_, k.a_bytes);
+      if (!k.b_const) wsB_bytes_ = std::max(wsB_bytes_, k.b_bytes);
+    } else if (k.kind == CK_GEMM) {
       const int nss = (prec == Prec::TF32X3 || prec == Prec::BF16X3) ? 3 : 1;
       const int elem = (prec == Prec::P64) ? PE_F64 : (prec == Prec::BF16X3 ? PE_BF16 : PE_F32);
       const int esz = (elem == PE_F64) ? 8 : (elem == PE_F32 ? 4 : 2);
@@ -463,8 +592,8 @@ void Engine::plan(Program& P) {
       pa.Kpad = pb.Kpad = Kp;
       pa.elem = pb.elem = elem;
       pa.round_tf32 = pb.round_tf32 = 1;
-      pa.transpose = row_is_unit(A, op.la, Lm, Lk) ? 1 : 0;
-      pb.transpose = row_is_unit(B, op.lb, Ln, Lk) ? 1 : 0;
+      choose_pack_mode(pa, A, op.la, Lm, Lk);
+      choose_pack_mode(pb, B, op.lb, Ln, Lk);
       k.GM = (long long)pa.nrb * M;
       k.GN = (long long)pb.nrb * N;
       k.Kpad = Kp;
@@ -538,9 +667,10 @@ void Engine::bind(Program& P) {
       k.pb.dst = wsB_;
     }
     k.up.gout = wsC_;
-    if (k.tc_kind >= 0)
-      tc_gemm_plan(k.tcp, k.tc_kind, k.pa.dst, k.pb.dst, static_cast<float*>(wsC_), k.GM, k.GN, k.Kpad, k.NB,
-                   dev_err_);
+    if (k.tc_kind >= 0) {
+      k.tcp.p.epi.C = C.ptr;
+      tc_gemm_plan(k.tcp, k.tc_kind, k.pa.dst, k.pa.nrb, k.pb.dst, k.pb.nrb, k.pa.R, k.pb.R, k.Kpad, k.NB, dev_err_);
+    }
   }
 }
 
@@ -621,15 +751,20 @@ void Engine::run(const Program& P) {
           pr.stop(stream_, KC_PACK, 0.0,
                   (double)k.NB * k.pb.R * k.pb.K * (k.pb.src_cplx ? 16 : 8) + (double)k.NB * k.GN * k.Kpad * esz, tag);
         }
-        // kernel-level algorithmic flops: the real multiply-adds of the packed product without padding
+        if (k.tc_kind >= 0) {
+          // kernel-level algorithmic flops: real multiply-adds of all segments, without padding
+          pr.start(stream_);
+          launch_tc_gemm(k.tcp, stream_);
+          pr.stop(stream_, KC_TC_GEMM, (double)k.exec_flops,
+                  (double)k.NB * (k.GM + k.GN) * k.Kpad * esz + 2.0 * k.NB * k.pa.R * k.pb.R * (C_cplx_of(k) ? 16 : 8), tag);
+          break;
+        }
         const double kflops = 2.0 * k.NB * k.GM * k.GN * (double)(k.pa.nss * k.pa.ncs * k.pa.K);
         pr.start(stream_);
-        if (k.tc_kind >= 0) launch_tc_gemm(k.tcp, stream_);
-        else
-          launch_gemm_f64(static_cast<const double*>(k.pa.dst), static_cast<const double*>(k.pb.dst),
-                          static_cast<double*>(wsC_), k.GM, k.GN, k.Kpad, k.NB, stream_);
-        pr.stop(stream_, k.tc_kind >= 0 ? KC_TC_GEMM : KC_F64_GEMM, kflops,
-                (double)k.NB * (k.GM + k.GN) * k.Kpad * esz + (double)k.NB * k.GM * k.GN * (k.tc_kind >= 0 ? 4 : 8), tag);
+        launch_gemm_f64(static_cast<const double*>(k.pa.dst), static_cast<const double*>(k.pb.dst),
+                        static_cast<double*>(wsC_), k.GM, k.GN, k.Kpad, k.NB, stream_);
+        pr.stop(stream_, KC_F64_GEMM, kflops,
+                (double)k.NB * (k.GM + k.GN) * k.Kpad * esz + (double)k.NB * k.GM * k.GN * 8, tag);
         pr.start(stream_);
         launch_unpack(k.up, stream_);
         pr.stop(stream_, KC_UNPACK, 0.0,

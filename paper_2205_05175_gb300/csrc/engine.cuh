@@ -52,7 +52,7 @@ struct Program {
   std::vector<int> zero_tensors;    // contiguous tensors cleared before the first op
   struct Zero2D { void* ptr; size_t pitch, width, height; };
   std::vector<Zero2D> zero2d;       // strided regions cleared before the first op
-  bool force_p64 = false;           // run this program's GEMM-path contractions in float64
+  int prec_override = -1;           // >= 0: run this program's GEMM-path contractions in this Prec
   std::vector<std::shared_ptr<Compiled>> comp;
 };
 

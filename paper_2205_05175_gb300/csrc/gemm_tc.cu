@@ -1,16 +1,22 @@
 // tcgen05 tensor-core GEMM for the residual contractions (sm_103a).
 //
-// C[b][m][n] = sum_k A[b][m][k] * B[b][n][k], both operands K-major in global memory
-// (packed by the pack kernel, rows padded to whole 128-byte K blocks), C float32.
+// Output plane rb of C (0 = real part, 1 = imaginary part) gets
+//     C[b][m][n] += alpha * sum_s (-1)^neg_s * sum_k A[planeA_s][b][m][k] * B[planeB_s][b][n][k]
+// with A and B packed K-major as planes (re/im x hi/lo split parts, 128-byte K blocks) and C a
+// strided float64 tensor addressed through index maps (no intermediate output buffer).
 //
-// One CTA computes a 128 x BN tile with 128 threads:
-//   warp 0 lane 0 : TMA producer (cp.async.bulk.tensor, 128-byte swizzle, mbarrier tx)
-//   warp 1 lane 0 : MMA issuer (tcgen05.mma kind::tf32 or kind::f16 with bf16 inputs,
-//                   accumulator in TMEM, tcgen05.commit releases smem stages)
-//   warps 0-3     : epilogue (tcgen05.ld 32x32b, lane quarter per warp) -> global
-// Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the thread records a
-// code in the device error word and leaves its loop, the MMA thread still commits so
-// that in-flight MMAs drain before TMEM is released.
+// Persistent, warp-specialised: one CTA per SM walks work items (batch, plane, split-K slice,
+// 128 x BN tile in grouped order) with 192 threads:
+//   warp 0 lane 0 : TMA producer (cp.async.bulk.tensor, 128-byte swizzle, mbarrier tx count)
+//   warp 1 lane 0 : MMA issuer (tcgen05.mma kind::tf32, or kind::f16 with bf16 inputs; the
+//                   instruction descriptor's negate-A bit gives -Ai Bi), tcgen05.commit
+//                   releases smem stages and hands a finished accumulator to the epilogue
+//   warps 2-5     : epilogue (tcgen05.ld 32x32b over the warp's TMEM lane quarter, batched
+//                   read-modify-write of C, shared-memory transpose when C is unit-stride in n)
+// Two TMEM accumulators (2 x BN columns) overlap the epilogue of one tile with the main loop
+// of the next.  Every mbarrier wait is bounded (2 s of %globaltimer): on expiry the thread
+// records a code in the device error word and leaves its loop; the MMA thread still commits
+// so that issued MMAs drain before TMEM is released.
 #include "common.cuh"
 #include <cudaTypedefs.h>
 #include <algorithm>
@@ -122,11 +128,45 @@ __device__ __forceinline__ uint32_t idesc_make() {
 }
 
 constexpr int kGroupM = 8;   // M tiles per rasterisation group (a wave shares A and B panels in L2)
+constexpr int kThreads = 192;  // warp 0 TMA, warp 1 MMA (+ TMEM allocation), warps 2-5 epilogue
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+
+struct Item {
+  int m0, n0, rb, bz, v0, nvl;
+};
+
+template <int BN>
+__device__ __forceinline__ Item decode_item(const TcGemmParams& p, int w, int splits) {
+  const int num_m = (p.M + BM - 1) / BM, num_n = (p.N + BN - 1) / BN;
+  const int tiles = num_m * num_n;
+  const int per_b = p.nrb * splits * tiles;
+  Item it;
+  it.bz = w / per_b;
+  int rem = w - it.bz * per_b;
+  const int rbs = rem / tiles;
+  const int tile = rem - rbs * tiles;
+  it.rb = rbs % p.nrb;
+  const int sp = rbs / p.nrb;
+  const int group = tile / (kGroupM * num_n);
+  const int first_m = group * kGroupM;
+  const int gsize = min(num_m - first_m, kGroupM);
+  const int pig = tile - group * kGroupM * num_n;
+  it.m0 = (first_m + pig % gsize) * BM;
+  it.n0 = (pig / gsize) * BN;
+  const int nv = p.nseg[it.rb] * p.nkb;
+  it.v0 = sp * p.vper;
+  it.nvl = max(0, min(nv, it.v0 + p.vper) - it.v0);
+  return it;
+}
+
+// Persistent warp-specialised GEMM: each CTA walks work items (batch, output plane, split, tile);
+// two TMEM accumulators let the epilogue of one tile overlap the main loop of the next.
 template <int BN, int KIND, int STAGES>
-__global__ void __launch_bounds__(128, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   float* __restrict__ C, int M, int N, int nkb_total, int kb_per_split, int* __restrict__ err) {
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ TcGemmParams p, int splits, int total_items) {
   constexpr int A_BYTES = BM * 128;
   constexpr int B_BYTES = BN * 128;
   constexpr int KBLK = (KIND == 0) ? 32 : 64;
@@ -134,36 +174,31 @@ __global__ void __launch_bounds__(128, 1)
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = base;
   uint8_t* sB = base + STAGES * A_BYTES;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * B_BYTES);
+  float* etile = reinterpret_cast<float*>(sB + STAGES * B_BYTES);        // 4 x 32 x 33 floats
+  long long* coloff_all = reinterpret_cast<long long*>(etile + 4 * 32 * 33);   // 4 warps x BN entries
+  uint64_t* full = reinterpret_cast<uint64_t*>(coloff_all + 4 * BN);
   uint64_t* empty = full + STAGES;
-  uint64_t* accf = empty + STAGES;
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(accf + 1);
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tempty + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // grouped rasterisation: GROUP_M consecutive M tiles sweep all N tiles before the next group
-  const int num_m = (M + BM - 1) / BM, num_n = (N + BN - 1) / BN;
-  const int pid = blockIdx.x;
-  const int group = pid / (kGroupM * num_n);
-  const int first_m = group * kGroupM;
-  const int gsize = min(num_m - first_m, kGroupM);
-  const int pig = pid - group * kGroupM * num_n;
-  const int m0 = (first_m + pig % gsize) * BM, n0 = (pig / gsize) * BN, bz = blockIdx.z;
-  // split-K range of this CTA
-  const int kb0 = blockIdx.y * kb_per_split;
-  const int nkb = min(nkb_total, kb0 + kb_per_split) - kb0;
-  const bool split = gridDim.y > 1;
+  const bool split = splits > 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accf, 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 128);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_holder)),
-                 "r"((uint32_t)BN)
+                 "r"((uint32_t)(2 * BN))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -172,81 +207,169 @@ __global__ void __launch_bounds__(128, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
 
-  if (warp == 0 && lane == 0) {
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES;
-      if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1)) {
-        atomicExch(err, DEV_TIMEOUT_PRODUCER);
-        break;
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool alive = true;
+      for (int w = blockIdx.x; w < total_items && alive; w += gridDim.x) {
+        const Item it = decode_item<BN>(p, w, splits);
+        for (int i = 0; i < it.nvl; ++i, ++g) {
+          const int v = it.v0 + i;
+          const int sg = v / p.nkb, kb = v - sg * p.nkb;
+          const uint32_t s = g % STAGES;
+          if (g >= STAGES && !mbar_wait(&empty[s], ((g / STAGES) - 1) & 1)) {
+            atomicExch(p.err, DEV_TIMEOUT_PRODUCER);
+            alive = false;
+            break;
+          }
+          mbar_arrive_tx(&full[s], A_BYTES + B_BYTES);
+          tma_load3(su32(sA + s * A_BYTES), &p.tmA, su32(&full[s]), kb * KBLK, p.seg[it.rb][sg].pa * p.M + it.m0,
+                    it.bz);
+          tma_load3(su32(sB + s * B_BYTES), &p.tmB, su32(&full[s]), kb * KBLK, p.seg[it.rb][sg].pb * p.N + it.n0,
+                    it.bz);
+        }
       }
-      mbar_arrive_tx(&full[s], A_BYTES + B_BYTES);
-      tma_load3(su32(sA + s * A_BYTES), &tmA, su32(&full[s]), (kb0 + kb) * KBLK, m0, bz);
-      tma_load3(su32(sB + s * B_BYTES), &tmB, su32(&full[s]), (kb0 + kb) * KBLK, n0, bz);
     }
-  } else if (warp == 1 && lane == 0) {
-    const uint32_t idesc = idesc_make<KIND, BN>();
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES;
-      if (!mbar_wait(&full[s], (kb / STAGES) & 1)) {
-        atomicExch(err, DEV_TIMEOUT_MMA);
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_make<KIND, BN>();
+      uint32_t g = 0;
+      int local = 0;
+      bool alive = true;
+      for (int w = blockIdx.x; w < total_items && alive; w += gridDim.x, ++local) {
+        const Item it = decode_item<BN>(p, w, splits);
+        const int a = local & 1, u = local >> 1;
+        if (u > 0 && !mbar_wait(&tempty[a], (u - 1) & 1)) {
+          atomicExch(p.err, DEV_TIMEOUT_MMA);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t acc = tmem + (uint32_t)(a * BN);
+        for (int i = 0; i < it.nvl; ++i, ++g) {
+          const int sg = (it.v0 + i) / p.nkb;
+          const uint32_t s = g % STAGES;
+          if (!mbar_wait(&full[s], (g / STAGES) & 1)) {
+            atomicExch(p.err, DEV_TIMEOUT_MMA);
+            alive = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t ad = sdesc_sw128(su32(sA + s * A_BYTES));
+          const uint64_t bd = sdesc_sw128(su32(sB + s * B_BYTES));
+          const uint32_t id = idesc | ((uint32_t)p.seg[it.rb][sg].neg << 13);   // negate A for -Ai Bi
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)   // 4 MMAs of 32 bytes of K per 128-byte block
+            tc_mma<KIND>(acc, ad + 2ull * kk, bd + 2ull * kk, id, (i | kk) ? 1u : 0u);
+          tc_commit(su32(&empty[s]));
+        }
+        tc_commit(su32(&tfull[a]));   // arrives when this tile's MMAs have completed
+      }
+    }
+    __syncwarp();
+  } else {
+    // epilogue warps 2..5: TMEM lane quarter q = warp % 4
+    const int q = warp & 3, ew = warp - 2;
+    const TcEpilogue& e = p.epi;
+    float* tile = etile + ew * (32 * 33);
+    long long* coloff = coloff_all + ew * BN;   // warp-private: no cross-warp barrier in the epilogue
+    int local = 0;
+    for (int w = blockIdx.x; w < total_items; w += gridDim.x, ++local) {
+      const Item it = decode_item<BN>(p, w, splits);
+      const int a = local & 1, u = local >> 1;
+      bool ok = mbar_wait(&tfull[a], u & 1);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0) atomicExch(p.err, DEV_TIMEOUT_EPI);
         break;
       }
       tc_fence_after();
-      const uint64_t ad = sdesc_sw128(su32(sA + s * A_BYTES));
-      const uint64_t bd = sdesc_sw128(su32(sB + s * B_BYTES));
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk)  // 4 MMAs of 32 bytes of K per 128-byte block
-        tc_mma<KIND>(tmem, ad + 2ull * kk, bd + 2ull * kk, idesc, (kb | kk) ? 1u : 0u);
-      tc_commit(su32(&empty[s]));
-    }
-    tc_commit(su32(accf));
-  }
-  __syncwarp();
-
-  bool ok = mbar_wait(accf, 0);
-  ok = __all_sync(0xffffffffu, ok);
-  if (!ok && lane == 0) atomicExch(err, DEV_TIMEOUT_EPI);
-  tc_fence_after();
-  if (ok) {
-    const int row = m0 + warp * 32 + lane;
-    float* crow = C + ((size_t)bz * (size_t)M + (size_t)row) * (size_t)N;
-    const bool vec = (N % 4) == 0;
+      // column offsets of this tile (each epilogue warp keeps its own copy)
+      __syncwarp();
+      for (int c = lane; c < BN; c += 32) {
+        const int n = it.n0 + c;
+        coloff[c] = (n < p.N) ? (e.flat_n ? (long long)n * e.sn : imap32(e.cn, (unsigned)n)) : -1;
+      }
+      __syncwarp();
+      const int row = it.m0 + q * 32 + lane;
+      long long rowoff = 0;
+      if (row < p.M) rowoff = imap32(e.cb, (unsigned)it.bz) + imap32(e.cm, (unsigned)row);
+      const uint32_t acc = tmem + (uint32_t)(a * BN) + ((uint32_t)(q * 32) << 16);
 #pragma unroll 1
-    for (int c = 0; c < BN; c += 32) {
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
-      const int col0 = n0 + c;
-      if (row < M && col0 < N && split) {
+      for (int c = 0; c < BN; c += 32) {
+        uint32_t r[32];
+        tmem_ld32(acc + (uint32_t)c, r);
+        if (it.nvl == 0) continue;
+        if (e.unit_n) {
 #pragma unroll
-        for (int q = 0; q < 32; ++q)
-          if (col0 + q < N) atomicAdd(crow + col0 + q, __uint_as_float(r[q]));
-      } else if (row < M && col0 < N) {
-        if (vec && col0 + 32 <= N) {
-          float4* dst = reinterpret_cast<float4*>(crow + col0);
+          for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = __uint_as_float(r[j]);
+          __syncwarp();
+          const long long noff = coloff[c + lane];
 #pragma unroll
-          for (int q = 0; q < 8; ++q)
-            dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
-                                 __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
-        } else {
+          for (int h = 0; h < 2; ++h) {
+            double* dst[16];
+            double old[16];
 #pragma unroll
-          for (int q = 0; q < 32; ++q)
-            if (col0 + q < N) crow[col0 + q] = __uint_as_float(r[q]);
+            for (int j = 0; j < 16; ++j) {
+              const int rr = h * 16 + j;
+              const long long ro = __shfl_sync(0xffffffffu, rowoff, rr);
+              const bool valid = (it.m0 + q * 32 + rr < p.M) && (noff >= 0);
+              const long long off = ro + noff;
+              dst[j] = valid ? e.C + (e.c_cplx ? 2 * off + it.rb : off) : nullptr;
+            }
+            if (!split) {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) old[j] = dst[j] ? *dst[j] : 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              if (!dst[j]) continue;
+              const double val = e.alpha * (double)tile[(h * 16 + j) * 33 + lane];
+              if (split) atomicAdd(dst[j], val);
+              else *dst[j] = old[j] + val;
+            }
+          }
+          __syncwarp();
+        } else if (row < p.M) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            double* dst[16];
+            double old[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const long long no = coloff[c + h * 16 + j];
+              const long long off = rowoff + no;
+              dst[j] = (no >= 0) ? e.C + (e.c_cplx ? 2 * off + it.rb : off) : nullptr;
+            }
+            if (!split) {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) old[j] = dst[j] ? *dst[j] : 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              if (!dst[j]) continue;
+              const double val = e.alpha * (double)__uint_as_float(r[h * 16 + j]);
+              if (split) atomicAdd(dst[j], val);
+              else *dst[j] = old[j] + val;
+            }
+          }
         }
       }
+      tc_fence_before();
+      mbar_arrive(&tempty[a]);
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN))
                  : "memory");
   }
 }
 
 template <int BN, int KIND, int STAGES>
 constexpr size_t smem_bytes() {
-  return 1024 + (size_t)STAGES * (BM * 128 + BN * 128) + (2 * STAGES + 1) * 8 + 16;
+  return 1024 + (size_t)STAGES * (BM * 128 + BN * 128) + 4 * 32 * 33 * 4 + 4 * BN * 8 + (2 * STAGES + 4) * 8 + 16;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -279,27 +402,24 @@ void make_map(CUtensorMap* tm, int kind, const void* ptr, long long rows, long l
 }
 
 template <int BN, int KIND, int STAGES>
-void launch_inst(const TcGemmPlan& p, cudaStream_t s) {
+void launch_inst(const TcGemmPlan& pl, cudaStream_t s) {
   auto kern = tc_gemm_kernel<BN, KIND, STAGES>;
   constexpr size_t sm = smem_bytes<BN, KIND, STAGES>();
+  static_assert(sm <= 227 * 1024, "shared memory budget");
   static bool attr = false;
+  static int nsm = 0;
   if (!attr) {
     RTCC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int dev = 0;
+    RTCC_CUDA(cudaGetDevice(&dev));
+    RTCC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     attr = true;
   }
-  const int nkb = (int)(p.Kpad / (KIND == 0 ? 32 : 64));
-  const long long tiles = ((p.M + BM - 1) / BM) * ((p.N + BN - 1) / BN);
-  // split K when the output has less than one wave of tiles and K is long
-  int splits = 1;
-  if (tiles * p.NB < 152 && nkb >= 32) {
-    splits = (int)std::min<long long>((2 * 152 + tiles * p.NB - 1) / (tiles * p.NB), nkb / 16);
-    splits = std::max(1, std::min(splits, 64));
-  }
-  const int per = (nkb + splits - 1) / splits;
-  splits = (nkb + per - 1) / per;
-  if (splits > 1) RTCC_CUDA(cudaMemsetAsync(p.C, 0, sizeof(float) * p.M * p.N * p.NB, s));
-  dim3 grid((unsigned)tiles, (unsigned)splits, (unsigned)p.NB);
-  kern<<<grid, 128, sm, s>>>(p.tmA, p.tmB, p.C, (int)p.M, (int)p.N, nkb, per, p.err);
+  const long long tiles = (long long)((pl.p.M + BM - 1) / BM) * ((pl.p.N + BN - 1) / BN);
+  const long long items = tiles * pl.p.nrb * pl.splits * pl.NB;
+  RTCC_REQUIRE(items < (1ll << 31), "too many GEMM tiles");
+  const unsigned grid = (unsigned)std::min<long long>(items, nsm);
+  kern<<<grid, kThreads, sm, s>>>(pl.p, pl.splits, (int)items);
   RTCC_CUDA(cudaGetLastError());
 }
 
@@ -307,20 +427,27 @@ void launch_inst(const TcGemmPlan& p, cudaStream_t s) {
 
 int tc_kblock_elems(int kind) { return kind == 0 ? 32 : 64; }
 
-void tc_gemm_plan(TcGemmPlan& p, int kind, const void* A, const void* B, float* C, long long M, long long N,
-                  long long Kpad, long long NB, int* err) {
+void tc_gemm_plan(TcGemmPlan& pl, int kind, const void* A, int planesA, const void* B, int planesB, long long M,
+                  long long N, long long Kpad, long long NB, int* err) {
   RTCC_REQUIRE(M > 0 && N > 0 && Kpad > 0 && NB > 0, "empty GEMM");
-  RTCC_REQUIRE(M < (1ll << 31) && N < (1ll << 31) && NB < 65536, "GEMM extents too large");
-  p.kind = kind;
-  p.bn = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
-  p.M = M;
-  p.N = N;
-  p.Kpad = Kpad;
-  p.NB = NB;
-  p.C = C;
-  p.err = err;
-  make_map(&p.tmA, kind, A, M, Kpad, NB, BM);
-  make_map(&p.tmB, kind, B, N, Kpad, NB, p.bn);
+  RTCC_REQUIRE(M * planesA < (1ll << 31) && N * planesB < (1ll << 31) && NB < 65536, "GEMM extents too large");
+  pl.kind = kind;
+  pl.bn = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
+  pl.NB = NB;
+  pl.p.M = (int)M;
+  pl.p.N = (int)N;
+  pl.p.nkb = (int)(Kpad / tc_kblock_elems(kind));
+  pl.p.err = err;
+  make_map(&pl.p.tmA, kind, A, M * planesA, Kpad, NB, BM);
+  make_map(&pl.p.tmB, kind, B, N * planesB, Kpad, NB, pl.bn);
+  // split K when the output has less than one wave of tiles and the K loop is long
+  const long long tiles = ((M + BM - 1) / BM) * ((N + pl.bn - 1) / pl.bn) * NB * pl.p.nrb;
+  const int nv = pl.p.nseg[0] * pl.p.nkb;
+  int splits = 1;
+  if (tiles < 152 && nv >= 32) splits = (int)std::max(1ll, std::min<long long>((2 * 152 + tiles - 1) / tiles, nv / 16));
+  splits = std::min(splits, 64);
+  pl.p.vper = (nv + splits - 1) / splits;
+  pl.splits = (nv + pl.p.vper - 1) / pl.p.vper;
 }
 
 void launch_tc_gemm(const TcGemmPlan& p, cudaStream_t s) {

@@ -28,18 +28,6 @@ __device__ __forceinline__ float tf32_rn(float x) {
   return __uint_as_float(r);
 }
 
-// 32-bit mixed-radix decode of one index group (extents < 2^31 per group).
-__device__ __forceinline__ long long imap32(const IndexMap& m, unsigned idx) {
-  long long off = 0;
-  for (int d = m.n - 1; d >= 0; --d) {
-    const unsigned dim = (unsigned)m.dims[d];
-    const unsigned q = idx / dim;
-    off += (long long)(idx - q * dim) * m.strides[d];
-    idx = q;
-  }
-  return off;
-}
-
 template <int ELEM>
 __device__ __forceinline__ void put(void* dst, size_t i, double x, int part, int round_tf32) {
   if constexpr (ELEM == PE_F64) {
@@ -78,7 +66,8 @@ __device__ __forceinline__ void pack_store(const PackDesc& d, unsigned bt, unsig
       const double x = (d.comp[rb][cs] ? xi : xr) * (double)d.sign[rb][cs];
 #pragma unroll 1
       for (int ss = 0; ss < d.nss; ++ss)
-        put<ELEM>(d.dst, rowbase + ((size_t)ss * d.ncs + cs) * K + k, x, d.part[ss], d.round_tf32);
+        put<ELEM>(d.dst, rowbase + ((size_t)ss * d.ncs + cs) * K + k, x, d.nss > 1 ? d.part[ss] : d.rb_part[rb],
+                  d.round_tf32);
     }
   }
 }
@@ -133,7 +122,7 @@ __global__ void __launch_bounds__(256) pack_transpose_kernel(PackDesc d, unsigne
         for (int i = 0; i < 4; ++i) {
           const unsigned row = r0 + ty + 8 * i;
           if (row >= NR) continue;
-          const unsigned bt = row / R, m = row - bt * R;
+          const unsigned bt = row / R, m = (unsigned)imap32(d.rd_dst, row - bt * R);
           for (unsigned p = tx; p < padw; p += 32) pack_pad<ELEM>(d, bt, m, p);
         }
         continue;
@@ -143,8 +132,8 @@ __global__ void __launch_bounds__(256) pack_transpose_kernel(PackDesc d, unsigne
         const unsigned k = k0 + ty + 8 * i, row = r0 + tx;
         double xr = 0.0, xi = 0.0;
         if (row < NR && k < K) {
-          const unsigned bt = row / R, m = row - bt * R;
-          const long long off = imap32(d.bat, bt) + imap32(d.rows, m) + imap32(d.cols, k);
+          const unsigned bt = row / R, mr = row - bt * R;
+          const long long off = imap32(d.bat, bt) + imap32(d.rd_src, mr) + imap32(d.cols, k);
           if (d.src_cplx) {
             const double2 v = reinterpret_cast<const double2*>(d.src)[off];
             xr = v.x;
@@ -161,7 +150,8 @@ __global__ void __launch_bounds__(256) pack_transpose_kernel(PackDesc d, unsigne
       for (int i = 0; i < 4; ++i) {
         const unsigned row = r0 + ty + 8 * i, k = k0 + tx;
         if (row < NR && k < K) {
-          const unsigned bt = row / R, m = row - bt * R;
+          const unsigned bt = row / R, mr = row - bt * R;
+          const unsigned m = (unsigned)imap32(d.rd_dst, mr);
           pack_store<ELEM>(d, bt, m, k, tre[tx][ty + 8 * i], tim[tx][ty + 8 * i]);
         }
       }
@@ -388,23 +378,26 @@ __global__ void reduce_kernel(DirectDesc d, long long chunk) {
 
 // float64 SIMT GEMM: 64x64 tile, 16-deep K slices, 256 threads with 4x4 outputs each.
 __global__ void __launch_bounds__(256) dgemm_kernel(const double* __restrict__ A, const double* __restrict__ B,
-                                                    double* __restrict__ C, int M, int N, int K) {
+                                                    double* __restrict__ C, int M, int N, int K, int splits,
+                                                    int kper) {
   __shared__ double As[16][64 + 1];
   __shared__ double Bs[16][64 + 1];
-  const size_t bz = blockIdx.z;
+  const size_t bz = blockIdx.z / splits;
+  const int sp = blockIdx.z - (int)bz * splits;
+  const int kbeg = sp * kper, kend = min(K, kbeg + kper);
   A += bz * (size_t)M * K;
   B += bz * (size_t)N * K;
   C += bz * (size_t)M * N;
   const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   double acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += 16) {
+  for (int k0 = kbeg; k0 < kend; k0 += 16) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int e = threadIdx.x + q * 256;
       const int r = e >> 4, c = e & 15;
-      As[c][r] = (m0 + r < M && k0 + c < K) ? A[(size_t)(m0 + r) * K + k0 + c] : 0.0;
-      Bs[c][r] = (n0 + r < N && k0 + c < K) ? B[(size_t)(n0 + r) * K + k0 + c] : 0.0;
+      As[c][r] = (m0 + r < M && k0 + c < kend) ? A[(size_t)(m0 + r) * K + k0 + c] : 0.0;
+      Bs[c][r] = (n0 + r < N && k0 + c < kend) ? B[(size_t)(n0 + r) * K + k0 + c] : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -428,7 +421,10 @@ __global__ void __launch_bounds__(256) dgemm_kernel(const double* __restrict__ A
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int n = n0 + tx * 4 + j;
-      if (n < N) C[(size_t)m * N + n] = acc[i][j];
+      if (n < N) {
+        if (splits > 1) atomicAdd(&C[(size_t)m * N + n], acc[i][j]);
+        else C[(size_t)m * N + n] = acc[i][j];
+      }
     }
   }
 }
@@ -515,8 +511,16 @@ void launch_add(const AddDesc& d, cudaStream_t s) {
 void launch_gemm_f64(const double* A, const double* B, double* C, long long M, long long N, long long Kpad,
                      long long NB, cudaStream_t s) {
   RTCC_REQUIRE(M < (1ll << 31) && N < (1ll << 31) && Kpad < (1ll << 31) && NB < 65536, "GEMM extents too large");
-  dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64), (unsigned)NB);
-  dgemm_kernel<<<grid, 256, 0, s>>>(A, B, C, (int)M, (int)N, (int)Kpad);
+  const long long tiles = ((N + 63) / 64) * ((M + 63) / 64) * NB;
+  int splits = 1;
+  if (tiles < 2 * 152 && Kpad >= 512)
+    splits = (int)std::max(1ll, std::min<long long>((4 * 152 + tiles - 1) / tiles, Kpad / 256));
+  splits = (int)std::min<long long>(splits, 65535 / NB);
+  const int kper = (int)(((Kpad + splits - 1) / splits + 15) / 16 * 16);
+  splits = (int)((Kpad + kper - 1) / kper);
+  if (splits > 1) RTCC_CUDA(cudaMemsetAsync(C, 0, sizeof(double) * M * N * NB, s));
+  dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64), (unsigned)(NB * splits));
+  dgemm_kernel<<<grid, 256, 0, s>>>(A, B, C, (int)M, (int)N, (int)Kpad, splits, kper);
   RTCC_CUDA(cudaGetLastError());
 }
 

@@ -347,7 +347,8 @@ DipolePrograms build_dipole(Engine& E, int nz, int o, int v, double* state, cons
   std::set<int> dep = {f.oo, f.ov, f.vv};
   Program& P = D.prog;
   P.name = "dipole";
-  P.force_p64 = true;   // the recorded observable is evaluated in float64 in every precision mode
+  // the recorded observable: float64 in the float64 mode, split-TF32 (float32-level accuracy) otherwise
+  P.prec_override = (E.prec() == Prec::P64) ? (int)Prec::P64 : (int)Prec::TF32X3;
   P.zero_arenas = {fa, ra};
   for (const Op& op : fwd.ops) {
     const bool d = dep.count(op.a) || (op.kind == OP_EIN && dep.count(op.b));

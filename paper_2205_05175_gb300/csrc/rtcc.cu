@@ -1109,8 +1109,9 @@ rtcc_status_t rtcc_spectrum(const double* t, const double* mu, int n, const rtcc
   });
 }
 
-rtcc_status_t rtcc_selftest_gemm(int prec, int batch, int M, int N, int K, const double* A, const double* Bm, double* C) {
-  if (prec < 0 || prec > 3 || batch < 1 || M < 1 || N < 1 || K < 1 || !A || !Bm || !C)
+rtcc_status_t rtcc_selftest_gemm(int prec, int cplx, int batch, int M, int N, int K, const double* A,
+                                 const double* Bm, double* C) {
+  if (prec < 0 || prec > 3 || cplx < 0 || cplx > 3 || batch < 1 || M < 1 || N < 1 || K < 1 || !A || !Bm || !C)
     return fail(RTCC_ERR_INVALID_ARG, "bad argument");
   return guarded([&] {
     cudaStream_t s;
@@ -1122,7 +1123,9 @@ rtcc_status_t rtcc_selftest_gemm(int prec, int batch, int M, int N, int K, const
         al.push_back(p);
         return static_cast<double*>(p);
       };
-      const size_t na = (size_t)batch * M * K, nb = (size_t)batch * N * K, nc = (size_t)batch * M * N;
+      const bool ac = cplx & 1, bc = (cplx >> 1) & 1, cc = ac || bc;
+      const size_t na = (size_t)batch * M * K * (ac ? 2 : 1), nb = (size_t)batch * N * K * (bc ? 2 : 1);
+      const size_t nc = (size_t)batch * M * N * (cc ? 2 : 1);
       double* dA = Al(na * 8);
       double* dB = Al(nb * 8);
       double* dC = Al(nc * 8);
@@ -1131,9 +1134,9 @@ rtcc_status_t rtcc_selftest_gemm(int prec, int batch, int M, int N, int K, const
       RTCC_CUDA(cudaMemsetAsync(dC, 0, nc * 8, s));
       Engine E((Prec)prec, s);
       E.set_force_gemm(true);
-      const int ta = E.external("A", {batch, M, K}, false, dA);
-      const int tb = E.external("B", {batch, N, K}, false, dB);
-      const int tc = E.external("C", {batch, M, N}, false, dC);
+      const int ta = E.external("A", {batch, M, K}, ac, dA);
+      const int tb = E.external("B", {batch, N, K}, bc, dB);
+      const int tc = E.external("C", {batch, M, N}, cc, dC);
       Program P;
       P.name = "selftest";
       Engine::ein(P, tc, "zmn", ta, "zmk", tb, "znk");

@@ -70,7 +70,7 @@ _sig = {
     "rtcc_profile": [_vp, C.c_int, C.POINTER(rtcc_profile_t)],
     "rtcc_spectrum": [_vp, _vp, C.c_int, C.POINTER(rtcc_field_t), C.c_double, C.c_double, C.c_double, _vp,
                       C.c_int, _vp],
-    "rtcc_selftest_gemm": [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp],
+    "rtcc_selftest_gemm": [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp],
 }
 for _name, _args in _sig.items():
     _fn = getattr(_lib, _name)
@@ -225,10 +225,13 @@ def rtcc_spectrum(t, mu_re, field, omegas, kappa=0.0, gamma=0.01, dt=0.0):
 
 
 def rtcc_selftest_gemm(prec, A, B):
-    """C[b] = A[b] @ B[b]^T through the library's GEMM path (A: batch x M x K, B: batch x N x K)."""
-    A, B = _as_c(A), _as_c(B)
+    """C[b] = A[b] @ B[b]^T through the library's GEMM path (A: batch x M x K, B: batch x N x K,
+    real or complex numpy arrays)."""
+    ac, bc = np.iscomplexobj(A), np.iscomplexobj(B)
+    A = np.ascontiguousarray(A, dtype=complex if ac else np.float64)
+    B = np.ascontiguousarray(B, dtype=complex if bc else np.float64)
     nb, M, K = A.shape
     N = B.shape[1]
-    Cm = np.zeros((nb, M, N))
-    _check(_lib.rtcc_selftest_gemm(int(prec), nb, M, N, K, _ptr(A), _ptr(B), _ptr(Cm)))
+    Cm = np.zeros((nb, M, N), dtype=complex if (ac or bc) else np.float64)
+    _check(_lib.rtcc_selftest_gemm(int(prec), int(ac) | (int(bc) << 1), nb, M, N, K, _ptr(A), _ptr(B), _ptr(Cm)))
     return Cm

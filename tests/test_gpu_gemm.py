@@ -24,3 +24,19 @@ def test_gemm_matches_float64(prec, shape):
     # the tensor-core modes must not be exact (they run in reduced precision on the tensor cores)
     if prec in (1, 3) and K > 8:
         assert np.abs(C - ref).max() > 0
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("kinds", ["cr", "rc", "cc"])
+@pytest.mark.parametrize("shape", [(2, 150, 70, 90), (1, 33, 300, 1200)])
+def test_complex_gemm_matches_float64(prec, kinds, shape):
+    """Complex operands: re/im planes and the segment table (Ar Br - Ai Bi, Ar Bi + Ai Br)."""
+    from paper_2205_05175_gb300 import rtcc
+    nb, M, N, K = shape
+    rng = np.random.default_rng(99 + N)
+    A = rng.standard_normal((nb, M, K)) + (1j * rng.standard_normal((nb, M, K)) if kinds[0] == "c" else 0)
+    B = rng.standard_normal((nb, N, K)) + (1j * rng.standard_normal((nb, N, K)) if kinds[1] == "c" else 0)
+    ref = np.einsum("bmk,bnk->bmn", A, B)
+    C = rtcc.rtcc_selftest_gemm(prec, A, B)
+    err = np.abs(C - ref).max() / (np.abs(A).max() * np.abs(B).max() * K)
+    assert err < 2 * TOL[prec], err
