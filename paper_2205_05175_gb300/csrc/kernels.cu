@@ -160,6 +160,152 @@ __global__ void __launch_bounds__(256) pack_transpose_kernel(PackDesc d, unsigne
   }
 }
 
+// ---- plane packs (tensor-core operands): planes = components (re, im) x split parts (hi, lo) ----
+template <int ELEM>
+struct Vec4;
+template <>
+struct Vec4<PE_F32> {
+  using T = float4;
+};
+template <>
+struct Vec4<PE_BF16> {
+  using T = uint2;
+};
+
+template <int ELEM>
+__device__ __forceinline__ float part_value(double x, int part) {
+  if constexpr (ELEM == PE_F32) {
+    if (part == SP_FULL) return tf32_rn((float)x);
+    const float hi = tf32_rn((float)x);
+    return part == SP_HI ? hi : tf32_rn((float)(x - (double)hi));
+  } else {
+    if (part == SP_FULL) return __bfloat162float(__float2bfloat16_rn((float)x));
+    const __nv_bfloat16 hi = __float2bfloat16_rn((float)x);
+    return part == SP_HI ? __bfloat162float(hi) : __bfloat162float(__float2bfloat16_rn((float)(x - (double)__bfloat162float(hi))));
+  }
+}
+
+template <int ELEM>
+__device__ __forceinline__ void store4(void* dst, size_t idx, float a, float b, float c, float d) {
+  if constexpr (ELEM == PE_F32) {
+    *reinterpret_cast<float4*>(static_cast<float*>(dst) + idx) = make_float4(a, b, c, d);
+  } else {
+    __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+    uint2 v;
+    v.x = *reinterpret_cast<uint32_t*>(&lo);
+    v.y = *reinterpret_cast<uint32_t*>(&hi);
+    *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(dst) + idx) = v;
+  }
+}
+
+template <int ELEM>
+__device__ __forceinline__ void store2(void* dst, size_t idx, float a, float b) {
+  if constexpr (ELEM == PE_F32) {
+    *reinterpret_cast<float2*>(static_cast<float*>(dst) + idx) = make_float2(a, b);
+  } else {
+    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(dst) + idx) = v;
+  }
+}
+
+// Source unit stride along K: 4 consecutive k per thread (offsets computed once), rows strided over y.
+template <int ELEM>
+__global__ void pack_planes_direct_kernel(PackDesc d) {
+  const unsigned R = (unsigned)d.R, K = (unsigned)d.K, Kp = (unsigned)d.Kpad;
+  const unsigned NR = (unsigned)(d.NB * d.R);
+  const unsigned k4 = 4u * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (k4 >= Kp) return;
+  long long coff[4];
+  bool kv[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    kv[j] = k4 + j < K;
+    coff[j] = kv[j] ? imap32(d.cols, k4 + j) : 0;
+  }
+  const int np = d.nrb;
+  for (unsigned row = blockIdx.y * blockDim.y + threadIdx.y; row < NR; row += gridDim.y * blockDim.y) {
+    const unsigned bt = row / R, m = row - bt * R;
+    const long long base = imap32(d.bat, bt) + imap32(d.rows, m);
+    double xr[4], xi[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      xr[j] = 0.0;
+      xi[j] = 0.0;
+      if (kv[j]) {
+        if (d.src_cplx) {
+          const double2 v = reinterpret_cast<const double2*>(d.src)[base + coff[j]];
+          xr[j] = v.x;
+          xi[j] = v.y;
+        } else {
+          xr[j] = d.src[base + coff[j]];
+        }
+      }
+    }
+    for (int pl = 0; pl < np; ++pl) {
+      const int part = d.rb_part[pl];
+      const bool im = d.comp[pl][0] != 0;
+      float o[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) o[j] = part_value<ELEM>(im ? xi[j] : xr[j], part);
+      const size_t idx = (((size_t)bt * np + pl) * R + m) * (size_t)Kp + k4;
+      store4<ELEM>(d.dst, idx, o[0], o[1], o[2], o[3]);
+    }
+  }
+}
+
+// Source unit stride along a row label: 32 read-order rows x 64 k per tile through shared memory;
+// the store phase writes 2 consecutive k per thread (a warp covers 64 k of one row).
+template <int ELEM>
+__global__ void __launch_bounds__(256) pack_planes_transpose_kernel(PackDesc d) {
+  __shared__ double2 tl[64][33];
+  const unsigned R = (unsigned)d.R, K = (unsigned)d.K, Kp = (unsigned)d.Kpad;
+  const unsigned NR = (unsigned)(d.NB * d.R);
+  const unsigned nkt = (Kp + 63) / 64, nrt = (NR + 31) / 32;
+  const unsigned tx = threadIdx.x, ty = threadIdx.y;
+  const int np = d.nrb;
+  for (unsigned rt = blockIdx.y; rt < nrt; rt += gridDim.y) {
+    for (unsigned kt = blockIdx.x; kt < nkt; kt += gridDim.x) {
+      const unsigned r0 = rt * 32, k0 = kt * 64;
+      {
+        const unsigned row = r0 + tx;
+        long long rbase = -1;
+        if (row < NR) {
+          const unsigned bt = row / R, mr = row - bt * R;
+          rbase = imap32(d.bat, bt) + imap32(d.rd_src, mr);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const unsigned k = k0 + ty + 8 * i;
+          double2 v = make_double2(0.0, 0.0);
+          if (rbase >= 0 && k < K) {
+            const long long off = rbase + imap32(d.cols, k);
+            if (d.src_cplx) v = reinterpret_cast<const double2*>(d.src)[off];
+            else v.x = d.src[off];
+          }
+          tl[ty + 8 * i][tx] = v;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const unsigned row = r0 + ty + 8 * i, kk = 2 * tx, k = k0 + kk;
+        if (row < NR && k < Kp) {
+          const unsigned bt = row / R, m = (unsigned)imap32(d.rd_dst, row - bt * R);
+          const double2 v0 = tl[kk][ty + 8 * i], v1 = tl[kk + 1][ty + 8 * i];
+          for (int pl = 0; pl < np; ++pl) {
+            const int part = d.rb_part[pl];
+            const bool im = d.comp[pl][0] != 0;
+            const float a = part_value<ELEM>(im ? v0.y : v0.x, part);
+            const float b = part_value<ELEM>(im ? v1.y : v1.x, part);
+            store2<ELEM>(d.dst, (((size_t)bt * np + pl) * R + m) * (size_t)Kp + k, a, b);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 template <typename G>
 __device__ __forceinline__ void unpack_one(const UnpackDesc& d, const G* g, unsigned bt, unsigned m, unsigned n,
                                            long long off) {
@@ -435,6 +581,25 @@ void launch_pack(const PackDesc& d, cudaStream_t s) {
   const long long NR = d.NB * d.R;
   if (NR == 0) return;
   RTCC_REQUIRE(NR < (1ll << 31) && d.K < (1ll << 31), "pack extents exceed 32-bit indexing");
+  if (d.ncs == 1 && d.nss == 1 && d.elem != PE_F64 && d.Kpad % 4 == 0) {
+    // tensor-core operand planes
+    if (d.transpose) {
+      dim3 grid((unsigned)std::min((d.Kpad + 63) / 64, 4096ll), (unsigned)std::min((NR + 31) / 32, 65535ll));
+      dim3 blk(32, 8);
+      if (d.elem == PE_F32) pack_planes_transpose_kernel<PE_F32><<<grid, blk, 0, s>>>(d);
+      else pack_planes_transpose_kernel<PE_BF16><<<grid, blk, 0, s>>>(d);
+    } else {
+      const unsigned nq = (unsigned)(d.Kpad / 4);
+      const unsigned bx = nq >= 128 ? 128u : std::max(32u, (nq + 31) / 32 * 32);
+      const unsigned by = 256 / bx;
+      dim3 blk(bx, by);
+      dim3 grid((nq + bx - 1) / bx, (unsigned)std::min((NR + by - 1) / by, 16384ll));
+      if (d.elem == PE_F32) pack_planes_direct_kernel<PE_F32><<<grid, blk, 0, s>>>(d);
+      else pack_planes_direct_kernel<PE_BF16><<<grid, blk, 0, s>>>(d);
+    }
+    RTCC_CUDA(cudaGetLastError());
+    return;
+  }
   const unsigned padw = (unsigned)(d.Kpad - (long long)d.nss * d.ncs * d.K);
   if (d.transpose) {
     const unsigned nkt = (unsigned)((d.K + 31) / 32) + (padw ? 1 : 0);
