@@ -207,6 +207,25 @@ const char* rtcc_last_error(void);
 rtcc_status_t rtcc_selftest_gemm(int prec, int cplx, int batch, int M, int N, int K, const double* A,
                                  const double* Bm, double* C);
 
+/* Allocation-free tensor-core GEMM (the paper has no counterpart: this serves callers that
+ * cannot let a library allocate device memory, e.g. applications that own all device memory
+ * through their own pool).  Computes C[b][m][n] = sum_k A[b][m][k] * Bm[b][n][k] with the same
+ * packing and tcgen05 kernels as rtcc_selftest_gemm, in precision prec = TF32, 3xTF32 or BF16x3
+ * (RTCC_P64 is rejected).  cplx bit 0: A complex (interleaved), bit 1: Bm complex; C is complex
+ * when either is.  A, Bm and C are DEVICE pointers owned by the caller; C is overwritten.  The
+ * call runs on `stream` (a cudaStream_t, null = default stream) and returns after completion.
+ * It calls no cudaMalloc, cudaFree or allocating library routine: the packed operands live in a
+ * 64 MiB file-scope device array that every GPU loading the library keeps until process exit.
+ * batch*(planesA*M + planesB*N)*Kpad*element_size must fit in it (planes = 1 or 2 components x
+ * 1 split part for TF32, 2 parts otherwise; Kpad = K rounded up to 32 (TF32) or 64 (BF16)
+ * elements; 4-byte elements for TF32 modes, 2-byte for BF16x3), else RTCC_ERR_INVALID_ARG.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
+ * should come before any stream capture.  All calls share the array, which keeps the previous
+ * call's contents: calls that overlap on the GPU (other streams, other host threads) race.
+ * Errors: INVALID_ARG, CUDA, TIMEOUT. */
+rtcc_status_t rtcc_gemm_noalloc(int prec, int cplx, int batch, int M, int N, int K, const double* A,
+                                const double* Bm, double* C, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

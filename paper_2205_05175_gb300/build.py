@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "librtcc.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["gemm_tc.cu", "kernels.cu", "engine.cu", "model.cu", "rtcc.cu"]
+SOURCES = ["gemm_tc.cu", "kernels.cu", "engine.cu", "model.cu", "rtcc.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

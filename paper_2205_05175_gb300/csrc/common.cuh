@@ -30,6 +30,9 @@ struct Error : std::runtime_error {
     if (!(cond)) throw ::rtcc::Error(1, std::string(msg));                              \
   } while (0)
 
+// Records the message rtcc_last_error() returns (thread-local).
+void set_last_error(const std::string& msg);
+
 // Device error word written by kernels whose bounded waits expire (never trapped).
 enum DevErr : int { DEV_OK = 0, DEV_TIMEOUT_PRODUCER = 1, DEV_TIMEOUT_MMA = 2, DEV_TIMEOUT_EPI = 3 };
 

@@ -431,6 +431,9 @@ bool is_device_ptr(const void* p) {
 }
 
 }  // namespace
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
 }  // namespace rtcc
 
 using namespace rtcc;

@@ -71,6 +71,7 @@ _sig = {
     "rtcc_spectrum": [_vp, _vp, C.c_int, C.POINTER(rtcc_field_t), C.c_double, C.c_double, C.c_double, _vp,
                       C.c_int, _vp],
     "rtcc_selftest_gemm": [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp],
+    "rtcc_gemm_noalloc": [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp],
 }
 for _name, _args in _sig.items():
     _fn = getattr(_lib, _name)
@@ -235,3 +236,20 @@ def rtcc_selftest_gemm(prec, A, B):
     Cm = np.zeros((nb, M, N), dtype=complex if (ac or bc) else np.float64)
     _check(_lib.rtcc_selftest_gemm(int(prec), int(ac) | (int(bc) << 1), nb, M, N, K, _ptr(A), _ptr(B), _ptr(Cm)))
     return Cm
+
+
+def rtcc_gemm_noalloc(prec, A, B, Cout, stream=None):
+    """C[b] = A[b] @ B[b]^T on the GPU without any allocation by the library.
+
+    A (batch x M x K), B (batch x N x K) and Cout (batch x M x N) are contiguous CUDA tensors of
+    dtype float64 or complex128; Cout is overwritten.  For callers that own all device memory
+    themselves: the library's scratch is a fixed static device array.
+    """
+    ac, bc = A.is_complex(), B.is_complex()
+    nb, M, K = A.shape
+    N = B.shape[1]
+    assert Cout.shape == (nb, M, N) and Cout.is_complex() == (ac or bc)
+    st = stream.cuda_stream if stream is not None else 0
+    _check(_lib.rtcc_gemm_noalloc(int(prec), int(ac) | (int(bc) << 1), nb, M, N, K, _ptr(A), _ptr(B), _ptr(Cout),
+                                  C.c_void_p(st)))
+    return Cout
