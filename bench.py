@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "RT-CCSD steps/s at o=30,v=114; tensor-pipe % of peak; max |dmu(t)| vs FP64"
 UNIT = "trajectory-steps/s"
-WORKLOAD = "water-hexamer-shaped RT-CCSD, o=30 v=114 naux=576, 12 Cash-Karp trajectories (tol 1e-6)"
+WORKLOAD = "water-hexamer-shaped RT-CCSD, o={o} v={v} naux={naux}, 12 Cash-Karp trajectories (tol 1e-6)"
 E0S = (0.001, 0.01, 0.05, 0.1)
 POLS = ((1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0))
 NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25      # dense tensor-core rate ratio (nominal)
@@ -168,7 +168,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": steps, "warmup": 0, "ms_per_step": 1e3 / r["value"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": r["sample"]},
+            "config": {"workload": WORKLOAD.format(o=30, v=114, naux=576), "sample": r["sample"]},
             "cpu_baseline": {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
                              "sample": r["sample"]},
             "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -225,10 +225,12 @@ def run_gpu(args, rank, world, local):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(torch.cuda.current_device()) as clk:
         H.profile_start()
+        torch.cuda.nvtx.range_push("rtcc_timed")
         ev0.record()
         H.propagate(fields, integ, max_out, tout, mout)
         ev1.record()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         prof = H.profile_stop()
     barrier(world)
     ms = ev0.elapsed_time(ev1)
@@ -253,23 +255,26 @@ def run_gpu(args, rank, world, local):
     roof["avg_launch_ms"] = d["ms"] / max(1, d["launches"])
     roof["peak_source"] = f"{src} (bf16 sustained{'' if prec == rtcc.P32_BF16X3 else ' x nominal tf32/bf16 ratio 0.49'})"
     share = {k: round(prof[k]["ms"] / max(1e-9, sum(p["ms"] for p in prof.values())), 4) for k in prof}
-    # end to end: initial states from pinned host memory, dipoles back to the host, inside the timed region
-    yh = torch.from_numpy(y0.view(np.float64).copy()).pin_memory()
-    th = np.zeros((nz, max_out))
-    mh = np.zeros((nz, max_out, 3), complex)
-    torch.cuda.synchronize()
-    barrier(world)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for z in range(nz):
-        H.set_state(z, yh[z].numpy().view(np.complex128), 0.0, 0.0)
-    H.propagate(fields, integ, max_out, th, mh)
-    e1.record()
-    torch.cuda.synchronize()
-    ms_e2e = reduce_max(e0.elapsed_time(e1), world)
-    acc_e2e = H.last_stats()[0]
-    h2d = yh.numel() * 8 / max(1, acc_e2e)
-    d2h = (th.nbytes + mh.nbytes) / max(1, acc_e2e)
+    if args.skip_e2e:
+        acc_e2e, ms_e2e, h2d, d2h = acc, ms_max, 0.0, 0.0
+    else:
+        # end to end: initial states from pinned host memory, dipoles back to the host, inside the timed region
+        yh = torch.from_numpy(y0.view(np.float64).copy()).pin_memory()
+        th = np.zeros((nz, max_out))
+        mh = np.zeros((nz, max_out, 3), complex)
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for z in range(nz):
+            H.set_state(z, yh[z].numpy().view(np.complex128), 0.0, 0.0)
+        H.propagate(fields, integ, max_out, th, mh)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_e2e = reduce_max(e0.elapsed_time(e1), world)
+        acc_e2e = H.last_stats()[0]
+        h2d = yh.numel() * 8 / max(1, acc_e2e)
+        d2h = (th.nbytes + mh.nbytes) / max(1, acc_e2e)
     H.close()
     line = None
     if rank == 0:
@@ -277,7 +282,7 @@ def run_gpu(args, rank, world, local):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / max(1, acc / nz), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
-                "config": {"workload": WORKLOAD, "o": o, "v": v, "naux": 4 * (o + v), "trajectories_per_gpu": nz,
+                "config": {"workload": WORKLOAD.format(o=o, v=v, naux=4 * (o + v)), "o": o, "v": v, "naux": 4 * (o + v), "trajectories_per_gpu": nz,
                            "precision": args.prec, "accepted_steps": acc, "rejected_attempts": rej,
                            "rhs_evaluations": nrhs, "l2": "inputs larger than L2 (state 4.5 GB, vvvv 1.35 GB)",
                            "parallelism": f"replicas x{world}", "ground_state_setup_s": round(t_setup, 2),
@@ -306,6 +311,7 @@ def main(argv=None):
     ap.add_argument("--gs-tol", type=float, default=1e-8)
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-dipole-error", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
     args = ap.parse_args(argv)
     rank, world, local = dist_env()
     if world > 1:

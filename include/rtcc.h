@@ -157,6 +157,19 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields,
                              const rtcc_integrator_t* integ, int max_out,
                              double* t_out, double* mu_out, int* n_out);
 
+/* Gradient of a dipole-trajectory objective with respect to the pulse parameters, by the
+ * discrete adjoint of RK4 (the paper has no adjoint; it differentiates the propagation of
+ * Sec. 2.1 Eqs. rk_y/rk_k with the Eq. field pulse):
+ *   J_z = sum_{n=0..nsteps} sum_x w[n][x] Re mu_x(t_n),  t_n = t_start + n h,
+ *   grad[z] = dJ_z / d(E0, omega, sigma) of trajectory z's field.
+ * Starts from every trajectory's current state and time; leaves them unchanged.
+ * w: host, (nsteps+1)*3.  The forward sweep keeps a checkpoint every ckpt_every steps; the
+ * reverse sweep recomputes each segment and applies the transposed stages with the
+ * vector-Jacobian products of the right-hand side (state and Fock matrix) and of the dipole.
+ * grad: host, ntraj*3 (output); J: host, ntraj (output).  Errors: INVALID_ARG, OOM, CUDA. */
+rtcc_status_t rtcc_propagate_vjp(rtcc_handle_t h, const rtcc_field_t* fields, double hstep, int nsteps,
+                                 const double* w, int ckpt_every, double* grad, double* J);
+
 /* Counters of the last rtcc_propagate: accepted steps, rejected attempts and
  * right-hand-side evaluations summed over trajectories, and the number of kernels the
  * library launched (host, each may be null). */
@@ -197,6 +210,11 @@ rtcc_status_t rtcc_spectrum(const double* t, const double* mu, int n, const rtcc
 
 /* Thread-local description of the most recent error (never null). */
 const char* rtcc_last_error(void);
+
+/* Library self-test of failure reporting (not part of the method): a kernel waits on a device
+ * flag that nothing sets, gives up after `seconds` (bounded, 0..10) and reports it; the call
+ * returns RTCC_ERR_TIMEOUT and the CUDA context stays usable.  Errors: INVALID_ARG, CUDA. */
+rtcc_status_t rtcc_selftest_timeout(double seconds);
 
 /* Library self-test of the contraction core (not part of the method): computes
  * C[b][m][n] = sum_k A[b][m][k] * Bm[b][n][k] for host or device inputs with the

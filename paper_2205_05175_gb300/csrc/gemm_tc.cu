@@ -229,6 +229,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     it.bz);
         }
       }
+      if (!alive) {
+        // after an expired wait: let the copies already issued land before the CTA exits (bounded)
+        for (uint32_t q = (g > STAGES ? g - STAGES : 0); q < g; ++q) mbar_wait(&full[q % STAGES], (q / STAGES) & 1);
+      }
     }
   } else if (warp == 1) {
     if (lane == 0) {

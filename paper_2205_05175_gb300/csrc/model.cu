@@ -294,6 +294,13 @@ RhsPrograms build_rhs(Engine& E, const IntIds& I, int nz, int o, int v, double* 
   R.t2 = in.x2;
   R.l1 = in.y1;
   R.l2 = in.y2;
+  R.foo = f.oo;
+  R.fov = f.ov;
+  R.fvv = f.vv;
+  R.r1 = ou.x1;
+  R.r2 = ou.x2;
+  R.rl1 = ou.y1;
+  R.rl2 = ou.y2;
   R.tau = residual_ops(b, &I, in.x1, in.x2, f, ou.x1, ou.x2);
   if (!with_lambda) return R;
   std::map<int, int> adj;
@@ -366,10 +373,81 @@ DipolePrograms build_dipole(Engine& E, int nz, int o, int v, double* state, cons
   const int mvv = E.external("mu.vv", {3, v, v}, false, m + (size_t)o * n + o, {sf, n, 1}, true);
   const int dx = E.external("dip", {3, nz}, true, dip_out);
   P.zero_tensors = {dx};
+  D.y1 = in.x1;
+  D.y2 = in.x2;
+  D.y3 = in.y1;
+  D.y4 = in.y2;
+  D.dip = dx;
   Engine::ein(P, dx, "xz", moo, "xij", adj.at(f.oo), "zij");
   Engine::ein(P, dx, "xz", mov, "xia", adj.at(f.ov), "zia");
   Engine::ein(P, dx, "xz", mvv, "xab", adj.at(f.vv), "zab");
   return D;
+}
+
+Program build_rhs_vjp(Engine& E, const RhsPrograms& R, int nz, int o, int v, double* cot, double* ybar,
+                      double* fbar) {
+  // the right-hand side is the concatenation fwd ; rev (seeds, reverse sweep, outputs)
+  Program both;
+  both.name = "rhs";
+  both.ops = R.fwd.ops;
+  both.ops.insert(both.ops.end(), R.rev.ops.begin(), R.rev.ops.end());
+  std::map<int, int> adj;
+  const int arena = E.new_arena();
+  Program V = E.reverse(both, {R.t1, R.t2, R.l1, R.l2, R.foo, R.fov, R.fvv}, arena, adj);
+  V.name = "rhs_vjp";
+  const StateViews c = state_views(E, "cot", cot, nz, o, v);
+  const StateViews yb = state_views(E, "ybar", ybar, nz, o, v);
+  const int n = o + v;
+  const long long sf = (long long)n * n;
+  const int fboo = E.external("fbar.oo", {nz, o, o}, true, fbar, {sf, n, 1});
+  const int fbov = E.external("fbar.ov", {nz, o, v}, true, fbar + 2 * o, {sf, n, 1});
+  const int fbvv = E.external("fbar.vv", {nz, v, v}, true, fbar + 2 * ((size_t)o * n + o), {sf, n, 1});
+  const long long ns = 2ll * o * v + 2ll * o * o * v * v;
+  V.zero2d = {{ybar, (size_t)ns * 16, (size_t)ns * 16, (size_t)nz}, {fbar, (size_t)sf * 16, (size_t)sf * 16, (size_t)nz}};
+  std::vector<Op> seeds;
+  auto seed = [&](int out, int cv, const char* l) {
+    auto it = adj.find(out);
+    if (it != adj.end()) seeds.push_back(Op{OP_ADD, it->second, cv, -1, l, l, "", 1.0});
+  };
+  seed(R.r1, c.x1, "zia");
+  seed(R.r2, c.x2, "zijab");
+  seed(R.rl1, c.y1, "zia");
+  seed(R.rl2, c.y2, "zijab");
+  V.ops.insert(V.ops.begin(), seeds.begin(), seeds.end());
+  auto out = [&](int dst, const char* ld, int src) {
+    auto it = adj.find(src);
+    if (it != adj.end()) Engine::add(V, dst, ld, it->second, ld);
+  };
+  out(yb.x1, "zia", R.t1);
+  out(yb.x2, "zijab", R.t2);
+  out(yb.y1, "zia", R.l1);
+  out(yb.y2, "zijab", R.l2);
+  out(fboo, "zij", R.foo);
+  out(fbov, "zia", R.fov);
+  out(fbvv, "zab", R.fvv);
+  return V;
+}
+
+Program build_dipole_vjp(Engine& E, const DipolePrograms& D, int nz, int o, int v, double* wdip, double* ybar) {
+  std::map<int, int> adj;
+  const int arena = E.new_arena();
+  Program V = E.reverse(D.prog, {D.y1, D.y2, D.y3, D.y4}, arena, adj);
+  V.name = "dipole_vjp";
+  V.prec_override = D.prog.prec_override;
+  const int w = E.external("wdip", {3, nz}, true, wdip);
+  auto it = adj.find(D.dip);
+  RTCC_REQUIRE(it != adj.end(), "dipole does not depend on the state");
+  V.ops.insert(V.ops.begin(), Op{OP_ADD, it->second, w, -1, "xz", "xz", "", 1.0});
+  const StateViews yb = state_views(E, "ybar_obs", ybar, nz, o, v);
+  auto out = [&](int dst, const char* ld, int src) {
+    auto jt = adj.find(src);
+    if (jt != adj.end()) Engine::add(V, dst, ld, jt->second, ld);
+  };
+  out(yb.x1, "zia", D.y1);
+  out(yb.x2, "zijab", D.y2);
+  out(yb.y1, "zia", D.y3);
+  out(yb.y2, "zijab", D.y4);
+  return V;
 }
 
 Program build_energy(Engine& E, const IntIds& I, const RhsPrograms& R, int nz, int o, int v, double* fock,

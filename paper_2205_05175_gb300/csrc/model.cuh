@@ -33,6 +33,8 @@ IntIds register_integrals(Engine& E, const IntegralStore& S);
 struct RhsPrograms {
   Program fwd, rev;
   int t1, t2, l1, l2;      // input views
+  int foo, fov, fvv;       // Fock views
+  int r1, r2, rl1, rl2;    // output views
   int tau;                 // tau intermediate (used by the energy program)
 };
 RhsPrograms build_rhs(Engine& E, const IntIds& I, int nz, int o, int v, double* state, double* fock,
@@ -43,9 +45,22 @@ RhsPrograms build_rhs(Engine& E, const IntIds& I, int nz, int o, int v, double* 
 struct DipolePrograms {
   Program prog;
   double* fdummy = nullptr;   // placeholder operator buffer (owned by the caller's allocation list)
+  int y1, y2, y3, y4;          // state views (t1, t2, l1, l2)
+  int dip;                     // output [3][nz]
 };
 DipolePrograms build_dipole(Engine& E, int nz, int o, int v, double* state, const double* mu_dev,
                             double* dip_out);
+
+// Vector-Jacobian product of one right-hand-side evaluation (the programs in R, last run on
+// the state in R's input buffer): given the cotangent `cot` of the raw output (Omega | R) in the
+// state layout, accumulate ybar = (dOut/dy)^T cot (state layout) and fbar = (dOut/df)^T cot
+// (Fock layout [nz][nmo][nmo], oo/ov/vv blocks).  Holomorphic: no conjugation.
+Program build_rhs_vjp(Engine& E, const RhsPrograms& R, int nz, int o, int v, double* cot, double* ybar,
+                      double* fbar);
+
+// Vector-Jacobian product of the dipole program D (last run on its state buffer): given weights
+// wdip[3][nz] (complex) of the dipole components, ybar += (d mu / dy)^T w (state layout).
+Program build_dipole_vjp(Engine& E, const DipolePrograms& D, int nz, int o, int v, double* wdip, double* ybar);
 
 // Correlation energy E = 2 sum f_ia t_ia + sum L_ijab tau_ijab (after `fwd` has run).
 Program build_energy(Engine& E, const IntIds& I, const RhsPrograms& R, int nz, int o, int v, double* fock,

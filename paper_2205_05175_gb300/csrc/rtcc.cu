@@ -416,6 +416,69 @@ __global__ void k_dft(const double* t, const double* y, int n, double dt, rtcc_f
   }
 }
 
+// y += alpha * x over complex state-sized buffers (alpha real)
+__global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, double alpha, long long n) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < 2 * n; k += (long long)gridDim.x * blockDim.x)
+    y[k] += alpha * x[k];
+}
+
+// dE/dtheta of the pulse amplitude at time t for theta = (E0, omega, sigma)
+__device__ __forceinline__ void field_grad(const rtcc_field_t& f, double t, double g[3]) {
+  const double x = t - f.t0;
+  const double env = exp(-0.5 * x * x / (f.sigma * f.sigma));
+  const bool cosc = f.carrier == RTCC_CARRIER_COS;
+  const double car = cosc ? cos(f.omega * x) : sin(f.omega * x);
+  const double dcar = cosc ? -x * sin(f.omega * x) : x * cos(f.omega * x);   // d carrier / d omega
+  g[0] = f.sign * env * car;
+  g[1] = f.sign * f.E0 * env * dcar;
+  g[2] = f.sign * f.E0 * env * car * (x * x) / (f.sigma * f.sigma * f.sigma);
+}
+
+// grad[z][j] += Re( -dE/dtheta_j(t_z) * sum_pq fbar[z][p][q] (pol_z . mu)[p][q] ) for one stage
+__global__ void k_theta_grad(double* grad, const double* fbar, const double* mu, const rtcc_field_t* fields,
+                             const double* tz, double c, const double* hz, int n2) {
+  const int z = blockIdx.x;
+  const rtcc_field_t fl = fields[z];
+  double pr = 0.0, pi = 0.0;
+  for (int k = threadIdx.x; k < n2; k += blockDim.x) {
+    const double m = fl.pol[0] * mu[k] + fl.pol[1] * mu[n2 + k] + fl.pol[2] * mu[2 * n2 + k];
+    pr += fbar[2 * ((size_t)z * n2 + k)] * m;
+    pi += fbar[2 * ((size_t)z * n2 + k) + 1] * m;
+  }
+  __shared__ double sh[2][32];
+  for (int off = 16; off > 0; off >>= 1) {
+    pr += __shfl_down_sync(0xffffffffu, pr, off);
+    pi += __shfl_down_sync(0xffffffffu, pi, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = pr;
+    sh[1][threadIdx.x >> 5] = pi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    pr = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) pr += sh[0][w];
+    double g[3];
+    field_grad(fl, tz[z] + c * hz[z], g);
+    for (int j = 0; j < 3; ++j) grad[3 * z + j] += -g[j] * pr;   // real part of -dE/dtheta * P
+  }
+}
+
+// Bounded wait on a flag that nothing sets: returns after `ns` nanoseconds with a status word.
+__global__ void k_wait_flag(const volatile int* flag, unsigned long long ns, int* status) {
+  unsigned long long t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  while (*flag == 0) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > ns) {
+      *status = 1;
+      return;
+    }
+  }
+  *status = 0;
+}
+
 inline unsigned blocks_for(long long n, int threads = 256) {
   long long b = (n + threads - 1) / threads;
   return (unsigned)std::max(1ll, std::min(b, 152ll * 32));
@@ -449,6 +512,18 @@ struct GroundEngine {
   unsigned long long* scratch = nullptr;
 };
 
+struct AdjointEngine {
+  std::unique_ptr<Engine> E;
+  RhsPrograms rhs;
+  DipolePrograms dip;
+  Program vjp, dvjp;
+  double *Ys = nullptr, *F = nullptr, *Rout = nullptr, *cot = nullptr, *ybar = nullptr, *fbar = nullptr;
+  double *Yd = nullptr, *DIP = nullptr, *wdip = nullptr, *ybar_obs = nullptr;
+  double *k[4] = {nullptr}, *sin[4] = {nullptr}, *kbar[4] = {nullptr};
+  double *y = nullptr, *abar = nullptr, *anew = nullptr;
+  double *tdev = nullptr, *hdev = nullptr, *grad = nullptr;
+};
+
 struct rtcc_ctx {
   int dev = 0;
   cudaStream_t stream = nullptr;
@@ -467,9 +542,11 @@ struct rtcc_ctx {
   Ctl ctl{};
   std::vector<void*> allocs;
   std::unique_ptr<GroundEngine> gs[4];   // per precision, one trajectory
+  std::unique_ptr<AdjointEngine> adj;
   long long last_stats[4] = {0, 0, 0, 0};
   Profiler prof;
   ~rtcc_ctx() {
+    adj.reset();
     for (auto& g : gs) g.reset();
     E.reset();
     ints.reset();
@@ -704,6 +781,121 @@ double solve_block(rtcc_ctx* h, GroundEngine* g, bool lambda, double tol, int ma
   }
   if (floor_ok) return best;
   throw Error(RTCC_ERR_NOCONV, std::string("ground-state ") + (lambda ? "Lambda" : "T") + " equations did not converge");
+}
+
+
+// ---------------------------------------------------------------------------------------
+// Adjoint of RK4 (discrete, checkpointed): gradients of J = sum_n sum_x w[n][x] Re mu_x(t_n)
+// with respect to the pulse parameters (E0, omega, sigma).  Every map is holomorphic in the
+// complex state, so the adjoint uses unconjugated VJPs and dJ/dtheta = Re dG/dtheta.
+
+AdjointEngine* adjoint_engine(rtcc_ctx* h) {
+  if (h->adj) return h->adj.get();
+  auto a = std::make_unique<AdjointEngine>();
+  a->E = std::make_unique<Engine>(h->prec, h->stream);
+  Engine& E = *a->E;
+  const IntIds I = register_integrals(E, *h->ints);
+  const size_t nsz = (size_t)2 * h->ns * h->nz;
+  const size_t n2 = (size_t)h->nmo * h->nmo;
+  a->Ys = h->alloc<double>(nsz);
+  a->Rout = h->alloc<double>(nsz);
+  a->cot = h->alloc<double>(nsz);
+  a->ybar = h->alloc<double>(nsz);
+  a->Yd = h->alloc<double>(nsz);
+  a->ybar_obs = h->alloc<double>(nsz);
+  a->y = h->alloc<double>(nsz);
+  a->abar = h->alloc<double>(nsz);
+  a->anew = h->alloc<double>(nsz);
+  for (int s = 0; s < 4; ++s) {
+    a->k[s] = h->alloc<double>(nsz);
+    a->sin[s] = h->alloc<double>(nsz);
+    a->kbar[s] = h->alloc<double>(nsz);
+  }
+  a->F = h->alloc<double>(n2 * h->nz);
+  a->fbar = h->alloc<double>(2 * n2 * h->nz);
+  a->DIP = h->alloc<double>((size_t)6 * h->nz);
+  a->wdip = h->alloc<double>((size_t)6 * h->nz);
+  a->tdev = h->alloc<double>(h->nz);
+  a->hdev = h->alloc<double>(h->nz);
+  a->grad = h->alloc<double>((size_t)3 * h->nz);
+  a->rhs = build_rhs(E, I, h->nz, h->o, h->v, a->Ys, a->F, a->Rout, true);
+  a->vjp = build_rhs_vjp(E, a->rhs, h->nz, h->o, h->v, a->cot, a->ybar, a->fbar);
+  a->dip = build_dipole(E, h->nz, h->o, h->v, a->Yd, h->mu, a->DIP);
+  h->allocs.push_back(a->dip.fdummy);
+  a->dvjp = build_dipole_vjp(E, a->dip, h->nz, h->o, h->v, a->wdip, a->ybar_obs);
+  E.finalize({&a->rhs.fwd, &a->rhs.rev, &a->vjp, &a->dip.prog, &a->dvjp});
+  h->adj = std::move(a);
+  return h->adj.get();
+}
+
+void adj_set_time(rtcc_ctx* h, AdjointEngine* a, double t, double hs) {
+  std::vector<double> tv(h->nz, t), hv(h->nz, hs);
+  RTCC_CUDA(cudaMemcpyAsync(a->tdev, tv.data(), sizeof(double) * h->nz, cudaMemcpyHostToDevice, h->stream));
+  RTCC_CUDA(cudaMemcpyAsync(a->hdev, hv.data(), sizeof(double) * h->nz, cudaMemcpyHostToDevice, h->stream));
+}
+
+// stage st of RK4 from state y: Ys = y + h sum_j a_sj D k_j, f(t + c h), right-hand side -> Rout
+void adj_stage(rtcc_ctx* h, AdjointEngine* a, const Tableau& tb, const double* y, int st) {
+  cudaStream_t s = h->stream;
+  const long long ns = h->ns, nT = h->nT;
+  const int nz = h->nz;
+  const dim3 gst(blocks_for(ns) / nz + 1 > 4096 ? 4096 : blocks_for(ns) / nz + 1, nz);
+  StageArgs A{};
+  for (int j = 0; j < st; ++j) {
+    if (tb.a[st][j] == 0.0) continue;
+    A.R[A.nterms] = a->k[j];
+    A.coef[A.nterms] = tb.a[st][j];
+    ++A.nterms;
+  }
+  k_stage<<<gst, 256, 0, s>>>(a->Ys, y, A, a->hdev, ns, nT);
+  k_fock<<<dim3(blocks_for((long long)h->nmo * h->nmo), nz), 256, 0, s>>>(a->F, h->f0, h->mu, h->d_fields, a->tdev,
+                                                                         a->hdev, tb.c[st], nz, h->nmo * h->nmo);
+  a->E->run(a->rhs.fwd);
+  a->E->run(a->rhs.rev);
+}
+
+// one RK4 step from y (device) into ynew, keeping the stage inputs and right-hand sides
+void adj_step(rtcc_ctx* h, AdjointEngine* a, const Tableau& tb, const double* y, double* ynew) {
+  cudaStream_t s = h->stream;
+  const size_t bytes = sizeof(double) * 2 * h->ns * h->nz;
+  for (int st = 0; st < 4; ++st) {
+    adj_stage(h, a, tb, y, st);
+    RTCC_CUDA(cudaMemcpyAsync(a->sin[st], a->Ys, bytes, cudaMemcpyDeviceToDevice, s));
+    RTCC_CUDA(cudaMemcpyAsync(a->k[st], a->Rout, bytes, cudaMemcpyDeviceToDevice, s));
+  }
+  StageArgs B{}, Ew{};
+  for (int j = 0; j < 4; ++j) {
+    B.R[j] = a->k[j];
+    B.coef[j] = tb.b[j];
+  }
+  B.nterms = 4;
+  const dim3 gst(blocks_for(h->ns) / h->nz + 1 > 4096 ? 4096 : blocks_for(h->ns) / h->nz + 1, h->nz);
+  k_final<<<gst, 256, 0, s>>>(ynew, y, B, Ew, a->hdev, h->ns, h->nT, h->ctl.err_bits, 0);
+  RTCC_CUDA(cudaGetLastError());
+}
+
+// dipoles of state y (device) into host mu[z][x] (real parts) and the observable VJP seed
+void adj_dipole(rtcc_ctx* h, AdjointEngine* a, const double* y, std::vector<double>& mu) {
+  const size_t bytes = sizeof(double) * 2 * h->ns * h->nz;
+  RTCC_CUDA(cudaMemcpyAsync(a->Yd, y, bytes, cudaMemcpyDeviceToDevice, h->stream));
+  a->E->run(a->dip.prog);
+  std::vector<double> d((size_t)6 * h->nz);
+  RTCC_CUDA(cudaMemcpyAsync(d.data(), a->DIP, sizeof(double) * d.size(), cudaMemcpyDeviceToHost, h->stream));
+  RTCC_CUDA(cudaStreamSynchronize(h->stream));
+  mu.assign((size_t)3 * h->nz, 0.0);
+  for (int z = 0; z < h->nz; ++z)
+    for (int x = 0; x < 3; ++x) mu[3 * z + x] = d[2 * (x * h->nz + z)] + h->mu_ref[x];
+}
+
+// abar += (d mu / dy)^T w_n at state y (the dipole program must have run on y)
+void adj_observable(rtcc_ctx* h, AdjointEngine* a, const double* wn, double* abar) {
+  std::vector<double> wd((size_t)6 * h->nz, 0.0);
+  for (int x = 0; x < 3; ++x)
+    for (int z = 0; z < h->nz; ++z) wd[2 * (x * h->nz + z)] = wn[x];
+  RTCC_CUDA(cudaMemcpyAsync(a->wdip, wd.data(), sizeof(double) * wd.size(), cudaMemcpyHostToDevice, h->stream));
+  RTCC_CUDA(cudaMemsetAsync(a->ybar_obs, 0, sizeof(double) * 2 * h->ns * h->nz, h->stream));
+  a->E->run(a->dvjp);
+  k_axpy<<<blocks_for(h->ns * h->nz), 256, 0, h->stream>>>(abar, a->ybar_obs, 1.0, h->ns * h->nz);
 }
 
 }  // namespace
@@ -1024,6 +1216,111 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
   });
 }
 
+
+rtcc_status_t rtcc_propagate_vjp(rtcc_handle_t h, const rtcc_field_t* fields, double hstep, int nsteps,
+                                 const double* w, int ckpt_every, double* grad, double* J) {
+  if (!h || !fields || !w || !grad || !J || nsteps < 1 || !(hstep > 0) || ckpt_every < 1)
+    return fail(RTCC_ERR_INVALID_ARG, "bad argument");
+  return guarded([&] {
+    cudaStream_t s = h->stream;
+    AdjointEngine* a = adjoint_engine(h);
+    const int nz = h->nz;
+    const size_t st_bytes = sizeof(double) * 2 * h->ns * nz;
+    const Tableau tb = rk4_tableau();
+    RTCC_CUDA(cudaMemcpyAsync(h->d_fields, fields, sizeof(rtcc_field_t) * nz, cudaMemcpyHostToDevice, s));
+    double t0 = 0.0;
+    RTCC_CUDA(cudaMemcpyAsync(&t0, h->ctl.t, sizeof(double), cudaMemcpyDeviceToHost, s));
+    RTCC_CUDA(cudaStreamSynchronize(s));
+    const int nck = nsteps / ckpt_every + 1;
+    std::vector<double*> ck(nck, nullptr);
+    std::vector<void*> tmp;
+    auto cleanup = [&] {
+      for (void* p : tmp) cudaFree(p);
+    };
+    try {
+      for (int c = 0; c < nck; ++c) {
+        ck[c] = static_cast<double*>(dev_alloc(st_bytes));
+        tmp.push_back(ck[c]);
+      }
+      double* seg = static_cast<double*>(dev_alloc(st_bytes * (size_t)ckpt_every));
+      tmp.push_back(seg);
+      // forward sweep with checkpoints; J from the dipoles at every step
+      std::vector<double> Jz(nz, 0.0), mu;
+      RTCC_CUDA(cudaMemcpyAsync(a->y, h->Y, st_bytes, cudaMemcpyDeviceToDevice, s));
+      for (int n = 0; n <= nsteps; ++n) {
+        if (n % ckpt_every == 0)
+          RTCC_CUDA(cudaMemcpyAsync(ck[n / ckpt_every], a->y, st_bytes, cudaMemcpyDeviceToDevice, s));
+        adj_dipole(h, a, a->y, mu);
+        for (int z = 0; z < nz; ++z)
+          for (int x = 0; x < 3; ++x) Jz[z] += w[3 * n + x] * mu[3 * z + x];
+        if (n == nsteps) break;
+        adj_set_time(h, a, t0 + n * hstep, hstep);
+        adj_step(h, a, tb, a->y, a->anew);
+        RTCC_CUDA(cudaMemcpyAsync(a->y, a->anew, st_bytes, cudaMemcpyDeviceToDevice, s));
+      }
+      // abar = dG/dy_N: the observable at the last step (the dipole program ran on y_N last)
+      RTCC_CUDA(cudaMemsetAsync(a->abar, 0, st_bytes, s));
+      adj_observable(h, a, w + 3 * nsteps, a->abar);
+      RTCC_CUDA(cudaMemsetAsync(a->grad, 0, sizeof(double) * 3 * nz, s));
+      const long long nst = h->ns * nz;
+      const unsigned nb = blocks_for(nst);
+      for (int c = (nsteps - 1) / ckpt_every; c >= 0; --c) {
+        const int n0 = c * ckpt_every, n1 = std::min(nsteps, n0 + ckpt_every);
+        // recompute the segment's states from its checkpoint
+        RTCC_CUDA(cudaMemcpyAsync(a->y, ck[c], st_bytes, cudaMemcpyDeviceToDevice, s));
+        for (int n = n0; n < n1; ++n) {
+          RTCC_CUDA(cudaMemcpyAsync(seg + (size_t)(n - n0) * 2 * nst, a->y, st_bytes, cudaMemcpyDeviceToDevice, s));
+          if (n + 1 < n1) {
+            adj_set_time(h, a, t0 + n * hstep, hstep);
+            adj_step(h, a, tb, a->y, a->anew);
+            RTCC_CUDA(cudaMemcpyAsync(a->y, a->anew, st_bytes, cudaMemcpyDeviceToDevice, s));
+          }
+        }
+        for (int n = n1 - 1; n >= n0; --n) {
+          const double* yn = seg + (size_t)(n - n0) * 2 * nst;
+          adj_set_time(h, a, t0 + n * hstep, hstep);
+          adj_step(h, a, tb, yn, a->anew);   // stage inputs and right-hand sides of step n
+          RTCC_CUDA(cudaMemcpyAsync(a->anew, a->abar, st_bytes, cudaMemcpyDeviceToDevice, s));   // identity part
+          for (int st = 0; st < 4; ++st) RTCC_CUDA(cudaMemsetAsync(a->kbar[st], 0, st_bytes, s));
+          for (int st = 3; st >= 0; --st) {
+            k_axpy<<<nb, 256, 0, s>>>(a->kbar[st], a->abar, hstep * tb.b[st], nst);
+            if (st != 3) {   // restore this stage's intermediates
+              RTCC_CUDA(cudaMemcpyAsync(a->Ys, a->sin[st], st_bytes, cudaMemcpyDeviceToDevice, s));
+              k_fock<<<dim3(blocks_for((long long)h->nmo * h->nmo), nz), 256, 0, s>>>(
+                  a->F, h->f0, h->mu, h->d_fields, a->tdev, a->hdev, tb.c[st], nz, h->nmo * h->nmo);
+              a->E->run(a->rhs.fwd);
+              a->E->run(a->rhs.rev);
+            }
+            k_apply_D<<<nb, 256, 0, s>>>(a->cot, a->kbar[st], h->ns, h->nT, nz);   // F = D R, D symmetric
+            a->E->run(a->vjp);
+            k_theta_grad<<<nz, 256, 0, s>>>(a->grad, a->fbar, h->mu, h->d_fields, a->tdev, tb.c[st], a->hdev,
+                                            h->nmo * h->nmo);
+            k_axpy<<<nb, 256, 0, s>>>(a->anew, a->ybar, 1.0, nst);
+            for (int j = 0; j < st; ++j)
+              if (tb.a[st][j] != 0.0) k_axpy<<<nb, 256, 0, s>>>(a->kbar[j], a->ybar, hstep * tb.a[st][j], nst);
+          }
+          // observable at step n
+          adj_dipole(h, a, yn, mu);
+          adj_observable(h, a, w + 3 * n, a->anew);
+          RTCC_CUDA(cudaMemcpyAsync(a->abar, a->anew, st_bytes, cudaMemcpyDeviceToDevice, s));
+        }
+      }
+      std::vector<double> g((size_t)3 * nz);
+      RTCC_CUDA(cudaMemcpyAsync(g.data(), a->grad, sizeof(double) * g.size(), cudaMemcpyDeviceToHost, s));
+      RTCC_CUDA(cudaStreamSynchronize(s));
+      a->E->check_error();
+      for (int z = 0; z < nz; ++z) {
+        J[z] = Jz[z];
+        for (int j = 0; j < 3; ++j) grad[3 * z + j] = g[3 * z + j];
+      }
+    } catch (...) {
+      cleanup();
+      throw;
+    }
+    cleanup();
+  });
+}
+
 rtcc_status_t rtcc_last_stats(rtcc_handle_t h, long long* accepted, long long* rejected, long long* rhs_evals,
                               long long* launches) {
   if (!h) return fail(RTCC_ERR_INVALID_ARG, "null handle");
@@ -1109,6 +1406,21 @@ rtcc_status_t rtcc_spectrum(const double* t, const double* mu, int n, const rtcc
     }
     for (void* p : al) cudaFree(p);
     cudaStreamDestroy(s);
+  });
+}
+
+rtcc_status_t rtcc_selftest_timeout(double seconds) {
+  if (!(seconds >= 0.0) || seconds > 10.0) return fail(RTCC_ERR_INVALID_ARG, "seconds must be in [0, 10]");
+  return guarded([&] {
+    int* d = static_cast<int*>(dev_alloc(2 * sizeof(int)));
+    RTCC_CUDA(cudaMemset(d, 0, 2 * sizeof(int)));
+    k_wait_flag<<<1, 1>>>(d, (unsigned long long)(seconds * 1e9), d + 1);
+    cudaError_t e = cudaDeviceSynchronize();
+    int st = -1;
+    if (e == cudaSuccess) e = cudaMemcpy(&st, d + 1, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) throw Error(RTCC_ERR_CUDA, cudaGetErrorString(e));
+    if (st != 0) throw Error(RTCC_ERR_TIMEOUT, "bounded device wait expired (flag never set)");
   });
 }
 

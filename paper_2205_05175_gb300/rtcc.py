@@ -68,9 +68,11 @@ _sig = {
     "rtcc_last_stats": [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                         C.POINTER(C.c_longlong)],
     "rtcc_profile": [_vp, C.c_int, C.POINTER(rtcc_profile_t)],
+    "rtcc_propagate_vjp": [_vp, C.POINTER(rtcc_field_t), C.c_double, C.c_int, _vp, C.c_int, _vp, _vp],
     "rtcc_spectrum": [_vp, _vp, C.c_int, C.POINTER(rtcc_field_t), C.c_double, C.c_double, C.c_double, _vp,
                       C.c_int, _vp],
     "rtcc_selftest_gemm": [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp],
+    "rtcc_selftest_timeout": [C.c_double],
     "rtcc_gemm_noalloc": [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp],
 }
 for _name, _args in _sig.items():
@@ -201,6 +203,15 @@ class Handle:
                                    n_out.ctypes.data_as(_ip)))
         return t_out, mu_out, n_out
 
+    def propagate_vjp(self, fields, hstep, nsteps, w, ckpt_every=25):
+        """(J[z], dJ/d(E0, omega, sigma)[z]) by the checkpointed discrete adjoint of RK4."""
+        fa = (rtcc_field_t * self.ntraj)(*fields)
+        w = _as_c(w).reshape(nsteps + 1, 3)
+        grad = np.zeros((self.ntraj, 3))
+        J = np.zeros(self.ntraj)
+        _check(_lib.rtcc_propagate_vjp(self.h, fa, hstep, nsteps, _ptr(w), ckpt_every, _ptr(grad), _ptr(J)))
+        return J, grad
+
     def last_stats(self):
         """(accepted steps, rejected attempts, rhs evaluations, kernel launches) of the last propagate."""
         a, r, e, n = C.c_longlong(), C.c_longlong(), C.c_longlong(), C.c_longlong()
@@ -223,6 +234,12 @@ def rtcc_spectrum(t, mu_re, field, omegas, kappa=0.0, gamma=0.01, dt=0.0):
     _check(_lib.rtcc_spectrum(_ptr(t), _ptr(mu_re), len(t), C.byref(field), kappa, gamma, dt, _ptr(omegas),
                               len(omegas), _ptr(I)))
     return I
+
+
+def rtcc_selftest_timeout(seconds):
+    """Returns the status of a bounded device wait on a flag that nothing sets (expects TIMEOUT)."""
+    code = _lib.rtcc_selftest_timeout(float(seconds))
+    return STATUS.get(code, str(code))
 
 
 def rtcc_selftest_gemm(prec, A, B):
@@ -253,3 +270,27 @@ def rtcc_gemm_noalloc(prec, A, B, Cout, stream=None):
     _check(_lib.rtcc_gemm_noalloc(int(prec), int(ac) | (int(bc) << 1), nb, M, N, K, _ptr(A), _ptr(B), _ptr(Cout),
                                   C.c_void_p(st)))
     return Cout
+
+
+def make_objective(handle, hstep, nsteps, w, ckpt_every=25, field_kw=None):
+    """torch.autograd.Function: theta = (E0, omega, sigma) -> J = sum_n sum_x w[n][x] Re mu_x(t_n)
+    for trajectory 0 of `handle`, differentiated by rtcc_propagate_vjp.  The state at the start
+    (the handle's current state) is restored by the library after every call."""
+    import torch
+    kw = dict(field_kw or {})
+
+    class _Objective(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, theta):
+            e0, om, sg = (float(x) for x in theta.detach().cpu())
+            f = make_field(E0=e0, omega=om, sigma=sg, **kw)
+            J, g = handle.propagate_vjp([f] * handle.ntraj, hstep, nsteps, w, ckpt_every)
+            ctx.save_for_backward(torch.tensor(g[0], dtype=theta.dtype))
+            return torch.tensor(J[0], dtype=theta.dtype)
+
+        @staticmethod
+        def backward(ctx, gout):
+            (g,) = ctx.saved_tensors
+            return gout * g
+
+    return _Objective.apply
