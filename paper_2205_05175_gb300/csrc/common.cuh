@@ -113,12 +113,15 @@ struct DirectDesc {
   IndexMap am, ak, ab, bn, bk, bb, cm, cn, cb;
   long long M, N, K, NB;
   double ar, ai;
+  int store;        // 1: C is known to be zero: store instead of read-modify-write
+  int f32;          // 1: sum products in float32 (reduced-precision programs)
 };
 
 // C[lc] += alpha * A[la] with labels(A) a subset of labels(C) (broadcast over the rest).
 struct AddDesc {
   const double* A; double* C;
   int a_cplx, c_cplx;
+  int store;        // 1: C is known to be zero: store instead of read-modify-write
   IndexMap c_all;   // all C labels
   IndexMap a_all;   // same labels, A's strides (0 where A lacks the label)
   long long n;
@@ -150,11 +153,13 @@ struct TcEpilogue {
   int flat_n;          // 1: C offset of column n is rowoff + n * sn
   long long sn;
   int unit_n;          // 1: the output's unit stride runs along n (write through a shared-memory transpose)
+  int store;           // 1: the output region is known to be zero: store instead of read-modify-write
 };
 struct TcGemmParams {
   CUtensorMap tmA, tmB;
   int M, N, nkb;       // rows of one A plane, rows of one B plane, K blocks per plane
   int nrb;             // output planes
+  int fused;           // 1: one work item covers both planes of a complex output (nseg[0] == nseg[1])
   int nseg[2];
   TcSeg seg[2][kMaxSeg];
   int vper;            // virtual K blocks (segments x nkb) per split
@@ -183,6 +188,60 @@ __device__ __forceinline__ long long imap32(const IndexMap& m, unsigned idx) {
     idx = q;
   }
   return off;
+}
+
+// Same decode without the innermost label (the caller walks that one itself).
+__device__ __forceinline__ long long imap32_outer(const IndexMap& m, unsigned idx) {
+  long long off = 0;
+  for (int d = m.n - 2; d >= 0; --d) {
+    const unsigned dim = (unsigned)m.dims[d];
+    const unsigned q = idx / dim;
+    off += (long long)(idx - q * dim) * m.strides[d];
+    idx = q;
+  }
+  return off;
+}
+
+// IEEE binary64 <-> binary32 conversions written with integer operations on the bit fields.
+// Bandwidth-bound kernels use them so that they issue no instruction to the float64 pipe,
+// which on this part runs at a small fraction of the float32 rate.
+//
+// binary64 -> binary32: the 52-bit significand is cut to 23 bits, rounding to nearest with
+// ties away from zero (add half a unit in the last kept place, then truncate; a carry out of
+// the significand moves into the exponent, which is the correctly rounded result).  Results
+// below the smallest normal binary32 (2^-126) flush to signed zero; overflow gives infinity;
+// NaN stays NaN.
+__device__ __forceinline__ float f64_to_f32_bits(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  if (e >= 255) {
+    const bool nan = ((hi >> 20) & 0x7ffu) == 0x7ffu && (((hi & 0xfffffu) | lo) != 0u);
+    return __uint_as_float(sign | (nan ? 0x7fc00000u : 0x7f800000u));
+  }
+  if (e <= 0) return __uint_as_float(sign);
+  unsigned bits = ((unsigned)e << 23) + ((((hi & 0xfffffu) << 3) | (lo >> 29)) + ((lo >> 28) & 1u));
+  if (bits > 0x7f800000u) bits = 0x7f800000u;
+  return __uint_as_float(sign | bits);
+}
+
+// binary32 -> binary64, exact (subnormal inputs are normalised).
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  unsigned long long bits;
+  if (e == 0xffu) {
+    bits = (0x7ffull << 52) | ((unsigned long long)m << 29);
+  } else if (e != 0u) {
+    bits = ((unsigned long long)(e + 1023 - 127) << 52) | ((unsigned long long)m << 29);
+  } else if (m != 0u) {
+    const int p = 31 - __clz((int)m);   // value = m * 2^-149 = 1.f * 2^(p - 149)
+    bits = ((unsigned long long)(p - 149 + 1023) << 52) | (((unsigned long long)m << (52 - p)) & 0xfffffffffffffull);
+  } else {
+    bits = 0;
+  }
+  return __longlong_as_double((long long)(bits | sign));
 }
 
 }  // namespace rtcc

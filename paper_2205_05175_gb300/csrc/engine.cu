@@ -1,5 +1,6 @@
 // Contraction engine: planning and execution of einsum programs (see engine.cuh).
 #include "engine.cuh"
+#include <array>
 #include <algorithm>
 #include <set>
 #include <cstdlib>
@@ -312,6 +313,29 @@ Program Engine::reverse(const Program& fwd, const std::vector<int>& active_input
 void Engine::plan(Program& P) {
   P.comp.clear();
   const Prec prec = P.prec_override >= 0 ? (Prec)P.prec_override : prec_;
+  // an arena temporary of an arena this program zeroes, not yet written by an earlier op of the
+  // program, is known to be zero: its first writer stores instead of read-modify-writing
+  // (tracked by arena extent, so temporaries that share reused arena space are never fresh twice)
+  std::vector<std::array<long long, 3>> written;   // arena, first double, one past the last
+  const std::set<int> zeroed(P.zero_arenas.begin(), P.zero_arenas.end());
+  auto extent = [&](const Tensor& t) {
+    long long hi = 1;
+    for (size_t i = 0; i < t.dims.size(); ++i) hi += (long long)(t.dims[i] - 1) * t.strides[i];
+    const long long w = t.cplx ? 2 : 1;
+    return std::array<long long, 3>{t.arena, t.arena_off, t.arena_off + hi * w};
+  };
+  auto fresh = [&](int id) {
+    const Tensor& t = tensors_[id];
+    if (t.storage != ST_ARENA || !zeroed.count(t.arena)) return false;
+    const auto x = extent(t);
+    for (const auto& w : written)
+      if (w[0] == x[0] && w[1] < x[2] && x[1] < w[2]) return false;
+    return true;
+  };
+  auto mark_written = [&](int id) {
+    const Tensor& t = tensors_[id];
+    if (t.storage == ST_ARENA) written.push_back(extent(t));
+  };
   for (const Op& op : P.ops) {
     auto cp = std::make_shared<Compiled>();
     Compiled& k = *cp;
@@ -322,9 +346,12 @@ void Engine::plan(Program& P) {
     RTCC_REQUIRE(C.cplx || (!A.cplx && (op.kind == OP_ADD || !tensors_[op.b].cplx)),
                  "complex result into real tensor " + C.name);
     RTCC_REQUIRE(!C.constant || P.name == "setup", "write to constant tensor " + C.name);
+    const bool c_fresh = fresh(op.c);
+    mark_written(op.c);
     if (op.kind == OP_ADD) {
       k.kind = CK_ADD;
       AddDesc& d = k.add;
+      d.store = c_fresh ? 1 : 0;
       d.A = A.ptr;
       d.C = C.ptr;
       d.a_cplx = A.cplx;
@@ -413,10 +440,13 @@ void Engine::plan(Program& P) {
     d.NB = NB;
     d.ar = op.alpha.real();
     d.ai = op.alpha.imag();
+    d.store = 0;
+    d.f32 = (prec != Prec::P64) ? 1 : 0;
 
     const long long nout = NB * M * N;
     if (Lk.empty()) {
       k.kind = CK_DIRECT;
+      d.store = c_fresh ? 1 : 0;
     } else if (force_gemm_) {
       k.kind = CK_GEMM;
     } else if (nout <= kReduceMaxOut && K >= 256) {
@@ -425,6 +455,7 @@ void Engine::plan(Program& P) {
       k.splits = std::max(1ll, std::min(want, (K + 1023) / 1024));
     } else if (work < kDirectMaxWork) {
       k.kind = CK_DIRECT;
+      d.store = c_fresh ? 1 : 0;
     } else {
       k.kind = CK_GEMM;
     }
@@ -508,6 +539,7 @@ void Engine::plan(Program& P) {
         if (ep.cn.strides[i] != ep.cn.strides[i + 1] * ep.cn.dims[i + 1]) ep.flat_n = 0;
       ep.sn = ep.cn.n ? ep.cn.strides[ep.cn.n - 1] : 0;
       ep.unit_n = (Ln.size() > 0 && !row_is_unit(C, op.lc, Lm, Ln)) ? 1 : 0;
+      ep.store = c_fresh ? 1 : 0;
       k.Kpad = Kp;
       k.NB = NB;
       k.GM = (long long)k.pa.nrb * M;
@@ -725,7 +757,7 @@ void Engine::run(const Program& P) {
       case CK_ADD:
         pr.start(stream_);
         launch_add(k.add, stream_);
-        pr.stop(stream_, KC_ADD, 0.0, (double)k.add.n * ((k.add.a_cplx ? 16 : 8) + 2 * (k.add.c_cplx ? 16 : 8)), tag);
+        pr.stop(stream_, KC_ADD, 0.0, (double)k.add.n * ((k.add.a_cplx ? 16 : 8) + (k.add.store ? 1 : 2) * (k.add.c_cplx ? 16 : 8)), tag);
         break;
       case CK_DIRECT:
         pr.start(stream_);

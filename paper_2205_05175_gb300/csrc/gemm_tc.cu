@@ -5,18 +5,20 @@
 // with A and B packed K-major as planes (re/im x hi/lo split parts, 128-byte K blocks) and C a
 // strided float64 tensor addressed through index maps (no intermediate output buffer).
 //
-// Persistent, warp-specialised: one CTA per SM walks work items (batch, plane, split-K slice,
-// 128 x BN tile in grouped order) with 192 threads:
+// Persistent, warp-specialised: one CTA per SM walks work items (batch, output plane or both
+// planes, split-K slice, 128 x BN tile in grouped order):
 //   warp 0 lane 0 : TMA producer (cp.async.bulk.tensor, 128-byte swizzle, mbarrier tx count)
 //   warp 1 lane 0 : MMA issuer (tcgen05.mma kind::tf32, or kind::f16 with bf16 inputs; the
 //                   instruction descriptor's negate-A bit gives -Ai Bi), tcgen05.commit
 //                   releases smem stages and hands a finished accumulator to the epilogue
-//   warps 2-5     : epilogue (tcgen05.ld 32x32b over the warp's TMEM lane quarter, batched
-//                   read-modify-write of C, shared-memory transpose when C is unit-stride in n)
-// Two TMEM accumulators (2 x BN columns) overlap the epilogue of one tile with the main loop
-// of the next.  Every mbarrier wait is bounded (2 s of %globaltimer): on expiry the thread
-// records a code in the device error word and leaves its loop; the MMA thread still commits
-// so that issued MMAs drain before TMEM is released.
+//   warps 2..     : epilogue (tcgen05.ld 32x32b over the warp's TMEM lane quarter, batched
+//                   read-modify-write of C, shared-memory transpose when C is unit-stride in n);
+//                   four warps, or eight that split the tile's columns for narrow tiles
+// Two TMEM accumulator sets overlap the epilogue of one tile with the main loop of the next.
+// When the K loop is short the epilogue dominates, so one item then covers both planes of a
+// complex output and writes whole 16-byte elements once.  Every mbarrier wait is bounded (2 s
+// of %globaltimer): on expiry the thread records a code in the device error word and leaves its
+// loop; the MMA thread still commits so that issued MMAs drain before TMEM is released.
 #include "common.cuh"
 #include <cudaTypedefs.h>
 #include <algorithm>
@@ -25,6 +27,7 @@ namespace rtcc {
 namespace {
 
 constexpr int BM = 128;
+constexpr int kFuseMaxBlocks = 24;   // segment x K-block count per plane below which planes are fused
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -128,28 +131,30 @@ __device__ __forceinline__ uint32_t idesc_make() {
 }
 
 constexpr int kGroupM = 8;   // M tiles per rasterisation group (a wave shares A and B panels in L2)
-constexpr int kThreads = 192;  // warp 0 TMA, warp 1 MMA (+ TMEM allocation), warps 2-5 epilogue
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
 
 struct Item {
-  int m0, n0, rb, bz, v0, nvl;
+  int m0, n0, rb, np, bz, v0, nvl;   // output planes rb .. rb + np - 1
 };
 
 template <int BN>
 __device__ __forceinline__ Item decode_item(const TcGemmParams& p, int w, int splits) {
   const int num_m = (p.M + BM - 1) / BM, num_n = (p.N + BN - 1) / BN;
   const int tiles = num_m * num_n;
-  const int per_b = p.nrb * splits * tiles;
+  const int pitems = p.fused ? 1 : p.nrb;   // plane items per tile
+  const int per_b = pitems * splits * tiles;
   Item it;
   it.bz = w / per_b;
   int rem = w - it.bz * per_b;
-  const int rbs = rem / tiles;
-  const int tile = rem - rbs * tiles;
-  it.rb = rbs % p.nrb;
-  const int sp = rbs / p.nrb;
+  // output plane fastest: both planes of a tile run on neighbouring CTAs and share A/B panels in L2
+  it.rb = p.fused ? 0 : rem % pitems;
+  it.np = p.fused ? p.nrb : 1;
+  rem /= pitems;
+  const int tile = rem % tiles;
+  const int sp = rem / tiles;
   const int group = tile / (kGroupM * num_n);
   const int first_m = group * kGroupM;
   const int gsize = min(num_m - first_m, kGroupM);
@@ -162,21 +167,32 @@ __device__ __forceinline__ Item decode_item(const TcGemmParams& p, int w, int sp
   return it;
 }
 
-// Persistent warp-specialised GEMM: each CTA walks work items (batch, output plane, split, tile);
-// two TMEM accumulators let the epilogue of one tile overlap the main loop of the next.
-template <int BN, int KIND, int STAGES>
-__global__ void __launch_bounds__(kThreads, 1)
+__device__ __forceinline__ void put_out(double* dst, double val, bool split, bool store, double old) {
+  if (split) atomicAdd(dst, val);
+  else *dst = store ? val : old + val;
+}
+
+// Persistent warp-specialised GEMM: each CTA walks work items (batch, output plane(s), split, tile);
+// two TMEM accumulator sets let the epilogue of one tile overlap the main loop of the next.
+// EPW epilogue warps: with 8, two warps share each TMEM lane quarter and split its columns.
+template <int BN, int KIND, int STAGES, int EPW>
+__global__ void __launch_bounds__(64 + 32 * EPW, 1)
     tc_gemm_kernel(const __grid_constant__ TcGemmParams p, int splits, int total_items) {
   constexpr int A_BYTES = BM * 128;
   constexpr int B_BYTES = BN * 128;
   constexpr int KBLK = (KIND == 0) ? 32 : 64;
+  constexpr int WCOLS = BN * 4 / EPW;   // accumulator columns per epilogue warp
+  // rows (or columns) of C in flight per epilogue batch: fewer with eight warps, whose register
+  // budget is smaller
+  constexpr int kCB = EPW == 8 ? 4 : 8, kSB = EPW == 8 ? 8 : 16;
+  static_assert(WCOLS % 32 == 0, "epilogue column split");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = base;
   uint8_t* sB = base + STAGES * A_BYTES;
-  float* etile = reinterpret_cast<float*>(sB + STAGES * B_BYTES);        // 4 x 32 x 33 floats
-  long long* coloff_all = reinterpret_cast<long long*>(etile + 4 * 32 * 33);   // 4 warps x BN entries
-  uint64_t* full = reinterpret_cast<uint64_t*>(coloff_all + 4 * BN);
+  float* etile = reinterpret_cast<float*>(sB + STAGES * B_BYTES);          // EPW x 32 x 33 floats
+  long long* coloff_all = reinterpret_cast<long long*>(etile + EPW * 32 * 33);   // EPW x WCOLS entries
+  uint64_t* full = reinterpret_cast<uint64_t*>(coloff_all + EPW * WCOLS);
   uint64_t* empty = full + STAGES;
   uint64_t* tfull = empty + STAGES;
   uint64_t* tempty = tfull + 2;
@@ -184,6 +200,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool split = splits > 1;
+  const int np_all = p.fused ? p.nrb : 1;                 // planes per work item
+  const uint32_t tcols = (uint32_t)(2 * np_all * BN);      // two accumulator sets
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -192,13 +210,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], 128);
+      mbar_init(&tempty[a], 32 * EPW);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_holder)),
-                 "r"((uint32_t)(2 * BN))
+                 "r"(tcols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -213,20 +231,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool alive = true;
       for (int w = blockIdx.x; w < total_items && alive; w += gridDim.x) {
         const Item it = decode_item<BN>(p, w, splits);
-        for (int i = 0; i < it.nvl; ++i, ++g) {
-          const int v = it.v0 + i;
-          const int sg = v / p.nkb, kb = v - sg * p.nkb;
-          const uint32_t s = g % STAGES;
-          if (g >= STAGES && !mbar_wait(&empty[s], ((g / STAGES) - 1) & 1)) {
-            atomicExch(p.err, DEV_TIMEOUT_PRODUCER);
-            alive = false;
-            break;
+        for (int pl = 0; pl < it.np && alive; ++pl) {
+          const int rb = it.rb + pl;
+          for (int i = 0; i < it.nvl; ++i, ++g) {
+            const int v = it.v0 + i;
+            const int sg = v / p.nkb, kb = v - sg * p.nkb;
+            const uint32_t s = g % STAGES;
+            if (g >= STAGES && !mbar_wait(&empty[s], ((g / STAGES) - 1) & 1)) {
+              atomicExch(p.err, DEV_TIMEOUT_PRODUCER);
+              alive = false;
+              break;
+            }
+            mbar_arrive_tx(&full[s], A_BYTES + B_BYTES);
+            tma_load3(su32(sA + s * A_BYTES), &p.tmA, su32(&full[s]), kb * KBLK, p.seg[rb][sg].pa * p.M + it.m0,
+                      it.bz);
+            tma_load3(su32(sB + s * B_BYTES), &p.tmB, su32(&full[s]), kb * KBLK, p.seg[rb][sg].pb * p.N + it.n0,
+                      it.bz);
           }
-          mbar_arrive_tx(&full[s], A_BYTES + B_BYTES);
-          tma_load3(su32(sA + s * A_BYTES), &p.tmA, su32(&full[s]), kb * KBLK, p.seg[it.rb][sg].pa * p.M + it.m0,
-                    it.bz);
-          tma_load3(su32(sB + s * B_BYTES), &p.tmB, su32(&full[s]), kb * KBLK, p.seg[it.rb][sg].pb * p.N + it.n0,
-                    it.bz);
         }
       }
       if (!alive) {
@@ -248,34 +269,41 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t acc = tmem + (uint32_t)(a * BN);
-        for (int i = 0; i < it.nvl; ++i, ++g) {
-          const int sg = (it.v0 + i) / p.nkb;
-          const uint32_t s = g % STAGES;
-          if (!mbar_wait(&full[s], (g / STAGES) & 1)) {
-            atomicExch(p.err, DEV_TIMEOUT_MMA);
-            alive = false;
-            break;
-          }
-          tc_fence_after();
-          const uint64_t ad = sdesc_sw128(su32(sA + s * A_BYTES));
-          const uint64_t bd = sdesc_sw128(su32(sB + s * B_BYTES));
-          const uint32_t id = idesc | ((uint32_t)p.seg[it.rb][sg].neg << 13);   // negate A for -Ai Bi
+        for (int pl = 0; pl < it.np && alive; ++pl) {
+          const int rb = it.rb + pl;
+          const uint32_t acc = tmem + (uint32_t)((a * it.np + pl) * BN);
+          for (int i = 0; i < it.nvl; ++i, ++g) {
+            const int sg = (it.v0 + i) / p.nkb;
+            const uint32_t s = g % STAGES;
+            if (!mbar_wait(&full[s], (g / STAGES) & 1)) {
+              atomicExch(p.err, DEV_TIMEOUT_MMA);
+              alive = false;
+              break;
+            }
+            tc_fence_after();
+            const uint64_t ad = sdesc_sw128(su32(sA + s * A_BYTES));
+            const uint64_t bd = sdesc_sw128(su32(sB + s * B_BYTES));
+            const uint32_t id = idesc | ((uint32_t)p.seg[rb][sg].neg << 13);   // negate A for -Ai Bi
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk)   // 4 MMAs of 32 bytes of K per 128-byte block
-            tc_mma<KIND>(acc, ad + 2ull * kk, bd + 2ull * kk, id, (i | kk) ? 1u : 0u);
-          tc_commit(su32(&empty[s]));
+            for (int kk = 0; kk < 4; ++kk)   // 4 MMAs of 32 bytes of K per 128-byte block
+              tc_mma<KIND>(acc, ad + 2ull * kk, bd + 2ull * kk, id, (i | kk) ? 1u : 0u);
+            tc_commit(su32(&empty[s]));
+          }
         }
         tc_commit(su32(&tfull[a]));   // arrives when this tile's MMAs have completed
       }
     }
     __syncwarp();
   } else {
-    // epilogue warps 2..5: TMEM lane quarter q = warp % 4
+    // epilogue warps: TMEM lane quarter q = warp % 4, columns [hc, hc + WCOLS) of the tile
     const int q = warp & 3, ew = warp - 2;
+    const int hc = (ew / 4) * WCOLS;
     const TcEpilogue& e = p.epi;
+    // the scale is applied in float32 (its rounding, 2^-24 relative, is far below the operand
+    // split's resolution) and the result widened exactly with integer operations
+    const float alpha_f = (float)e.alpha;
     float* tile = etile + ew * (32 * 33);
-    long long* coloff = coloff_all + ew * BN;   // warp-private: no cross-warp barrier in the epilogue
+    long long* coloff = coloff_all + ew * WCOLS;   // warp-private: no cross-warp barrier in the epilogue
     int local = 0;
     for (int w = blockIdx.x; w < total_items; w += gridDim.x, ++local) {
       const Item it = decode_item<BN>(p, w, splits);
@@ -287,73 +315,161 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       tc_fence_after();
-      // column offsets of this tile (each epilogue warp keeps its own copy)
       __syncwarp();
-      for (int c = lane; c < BN; c += 32) {
-        const int n = it.n0 + c;
+      for (int c = lane; c < WCOLS; c += 32) {
+        const int n = it.n0 + hc + c;
         coloff[c] = (n < p.N) ? (e.flat_n ? (long long)n * e.sn : imap32(e.cn, (unsigned)n)) : -1;
       }
       __syncwarp();
       const int row = it.m0 + q * 32 + lane;
       long long rowoff = 0;
       if (row < p.M) rowoff = imap32(e.cb, (unsigned)it.bz) + imap32(e.cm, (unsigned)row);
-      const uint32_t acc = tmem + (uint32_t)(a * BN) + ((uint32_t)(q * 32) << 16);
+      const uint32_t acc = tmem + (uint32_t)(a * it.np * BN + hc) + ((uint32_t)(q * 32) << 16);
+      const bool both = it.np == 2 && e.c_cplx;   // write complex elements whole
 #pragma unroll 1
-      for (int c = 0; c < BN; c += 32) {
-        uint32_t r[32];
-        tmem_ld32(acc + (uint32_t)c, r);
-        if (it.nvl == 0) continue;
-        if (e.unit_n) {
+      for (int c = 0; c < WCOLS; c += 32) {
+        if (it.nvl == 0) continue;   // uniform over the warp
+        if (both) {
+          double2* C2 = reinterpret_cast<double2*>(e.C);
+          if (e.unit_n) {
+            // transpose both planes through the warp's tile: lane then owns column c + lane
+            float tre[32], tim[32];
+            {
+              uint32_t r[32];
+              tmem_ld32(acc + (uint32_t)c, r);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = __uint_as_float(r[j]);
-          __syncwarp();
-          const long long noff = coloff[c + lane];
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            double* dst[16];
-            double old[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int rr = h * 16 + j;
-              const long long ro = __shfl_sync(0xffffffffu, rowoff, rr);
-              const bool valid = (it.m0 + q * 32 + rr < p.M) && (noff >= 0);
-              const long long off = ro + noff;
-              dst[j] = valid ? e.C + (e.c_cplx ? 2 * off + it.rb : off) : nullptr;
+              for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = __uint_as_float(r[j]);
             }
-            if (!split) {
+            __syncwarp();
 #pragma unroll
-              for (int j = 0; j < 16; ++j) old[j] = dst[j] ? *dst[j] : 0.0;
+            for (int j = 0; j < 32; ++j) tre[j] = tile[j * 33 + lane];
+            __syncwarp();
+            {
+              uint32_t r[32];
+              tmem_ld32(acc + (uint32_t)(BN + c), r);
+#pragma unroll
+              for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = __uint_as_float(r[j]);
             }
+            __syncwarp();
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              if (!dst[j]) continue;
-              const double val = e.alpha * (double)tile[(h * 16 + j) * 33 + lane];
-              if (split) atomicAdd(dst[j], val);
-              else *dst[j] = old[j] + val;
+            for (int j = 0; j < 32; ++j) tim[j] = tile[j * 33 + lane];
+            __syncwarp();
+            const long long noff = coloff[c + lane];
+#pragma unroll
+            for (int h = 0; h < 32 / kCB; ++h) {
+              double2* dst[kCB];
+              double2 old[kCB];
+#pragma unroll
+              for (int j = 0; j < kCB; ++j) {
+                const int rr = h * kCB + j;
+                const long long ro = __shfl_sync(0xffffffffu, rowoff, rr);
+                const bool valid = (it.m0 + q * 32 + rr < p.M) && (noff >= 0);
+                dst[j] = valid ? C2 + (ro + noff) : nullptr;
+              }
+              if (!split && !e.store) {
+#pragma unroll
+                for (int j = 0; j < kCB; ++j) old[j] = dst[j] ? *dst[j] : make_double2(0.0, 0.0);
+              }
+#pragma unroll
+              for (int j = 0; j < kCB; ++j) {
+                if (!dst[j]) continue;
+                const double vr = f32_to_f64_bits(alpha_f * tre[h * kCB + j]);
+                const double vi = f32_to_f64_bits(alpha_f * tim[h * kCB + j]);
+                if (split) {
+                  atomicAdd(&dst[j]->x, vr);
+                  atomicAdd(&dst[j]->y, vi);
+                } else {
+                  *dst[j] = e.store ? make_double2(vr, vi) : make_double2(old[j].x + vr, old[j].y + vi);
+                }
+              }
+            }
+          } else {
+            uint32_t rre[32], rim[32];
+            tmem_ld32(acc + (uint32_t)c, rre);
+            tmem_ld32(acc + (uint32_t)(BN + c), rim);
+            if (row >= p.M) continue;
+#pragma unroll
+            for (int h = 0; h < 32 / kCB; ++h) {
+              double2* dst[kCB];
+              double2 old[kCB];
+#pragma unroll
+              for (int j = 0; j < kCB; ++j) {
+                const long long no = coloff[c + h * kCB + j];
+                dst[j] = (no >= 0) ? C2 + (rowoff + no) : nullptr;
+              }
+              if (!split && !e.store) {
+#pragma unroll
+                for (int j = 0; j < kCB; ++j) old[j] = dst[j] ? *dst[j] : make_double2(0.0, 0.0);
+              }
+#pragma unroll
+              for (int j = 0; j < kCB; ++j) {
+                if (!dst[j]) continue;
+                const double vr = f32_to_f64_bits(alpha_f * __uint_as_float(rre[h * kCB + j]));
+                const double vi = f32_to_f64_bits(alpha_f * __uint_as_float(rim[h * kCB + j]));
+                if (split) {
+                  atomicAdd(&dst[j]->x, vr);
+                  atomicAdd(&dst[j]->y, vi);
+                } else {
+                  *dst[j] = e.store ? make_double2(vr, vi) : make_double2(old[j].x + vr, old[j].y + vi);
+                }
+              }
             }
           }
-          __syncwarp();
-        } else if (row < p.M) {
+          continue;
+        }
+        // one plane per pass: plane it.rb + pl of the output, one component of C at a time
+        for (int pl = 0; pl < it.np; ++pl) {
+          const int comp = it.rb + pl;
+          uint32_t r[32];
+          tmem_ld32(acc + (uint32_t)(pl * BN + c), r);
+          if (e.unit_n) {
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            double* dst[16];
-            double old[16];
+            for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = __uint_as_float(r[j]);
+            __syncwarp();
+            const long long noff = coloff[c + lane];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const long long no = coloff[c + h * 16 + j];
-              const long long off = rowoff + no;
-              dst[j] = (no >= 0) ? e.C + (e.c_cplx ? 2 * off + it.rb : off) : nullptr;
+            for (int h = 0; h < 32 / kSB; ++h) {
+              double* dst[kSB];
+              double old[kSB];
+#pragma unroll
+              for (int j = 0; j < kSB; ++j) {
+                const int rr = h * kSB + j;
+                const long long ro = __shfl_sync(0xffffffffu, rowoff, rr);
+                const bool valid = (it.m0 + q * 32 + rr < p.M) && (noff >= 0);
+                const long long off = ro + noff;
+                dst[j] = valid ? e.C + (e.c_cplx ? 2 * off + comp : off) : nullptr;
+              }
+              if (!split && !e.store) {
+#pragma unroll
+                for (int j = 0; j < kSB; ++j) old[j] = dst[j] ? *dst[j] : 0.0;
+              }
+#pragma unroll
+              for (int j = 0; j < kSB; ++j) {
+                if (!dst[j]) continue;
+                put_out(dst[j], f32_to_f64_bits(alpha_f * tile[(h * kSB + j) * 33 + lane]), split, e.store, old[j]);
+              }
             }
-            if (!split) {
+            __syncwarp();
+          } else if (row < p.M) {
 #pragma unroll
-              for (int j = 0; j < 16; ++j) old[j] = dst[j] ? *dst[j] : 0.0;
-            }
+            for (int h = 0; h < 32 / kSB; ++h) {
+              double* dst[kSB];
+              double old[kSB];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              if (!dst[j]) continue;
-              const double val = e.alpha * (double)__uint_as_float(r[h * 16 + j]);
-              if (split) atomicAdd(dst[j], val);
-              else *dst[j] = old[j] + val;
+              for (int j = 0; j < kSB; ++j) {
+                const long long no = coloff[c + h * kSB + j];
+                const long long off = rowoff + no;
+                dst[j] = (no >= 0) ? e.C + (e.c_cplx ? 2 * off + comp : off) : nullptr;
+              }
+              if (!split && !e.store) {
+#pragma unroll
+                for (int j = 0; j < kSB; ++j) old[j] = dst[j] ? *dst[j] : 0.0;
+              }
+#pragma unroll
+              for (int j = 0; j < kSB; ++j) {
+                if (!dst[j]) continue;
+                put_out(dst[j], f32_to_f64_bits(alpha_f * __uint_as_float(r[h * kSB + j])), split, e.store, old[j]);
+              }
             }
           }
         }
@@ -366,14 +482,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN))
-                 : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
   }
 }
 
-template <int BN, int KIND, int STAGES>
+template <int BN, int KIND, int STAGES, int EPW>
 constexpr size_t smem_bytes() {
-  return 1024 + (size_t)STAGES * (BM * 128 + BN * 128) + 4 * 32 * 33 * 4 + 4 * BN * 8 + (2 * STAGES + 4) * 8 + 16;
+  return 1024 + (size_t)STAGES * (BM * 128 + BN * 128) + (size_t)EPW * 32 * 33 * 4 + (size_t)4 * BN * 8 +
+         (2 * STAGES + 4) * 8 + 16;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -405,10 +521,10 @@ void make_map(CUtensorMap* tm, int kind, const void* ptr, long long rows, long l
   if (r != CUDA_SUCCESS) throw Error(3, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
 }
 
-template <int BN, int KIND, int STAGES>
+template <int BN, int KIND, int STAGES, int EPW>
 void launch_inst(const TcGemmPlan& pl, cudaStream_t s) {
-  auto kern = tc_gemm_kernel<BN, KIND, STAGES>;
-  constexpr size_t sm = smem_bytes<BN, KIND, STAGES>();
+  auto kern = tc_gemm_kernel<BN, KIND, STAGES, EPW>;
+  constexpr size_t sm = smem_bytes<BN, KIND, STAGES, EPW>();
   static_assert(sm <= 227 * 1024, "shared memory budget");
   static bool attr = false;
   static int nsm = 0;
@@ -420,10 +536,10 @@ void launch_inst(const TcGemmPlan& pl, cudaStream_t s) {
     attr = true;
   }
   const long long tiles = (long long)((pl.p.M + BM - 1) / BM) * ((pl.p.N + BN - 1) / BN);
-  const long long items = tiles * pl.p.nrb * pl.splits * pl.NB;
+  const long long items = tiles * (pl.p.fused ? 1 : pl.p.nrb) * pl.splits * pl.NB;
   RTCC_REQUIRE(items < (1ll << 31), "too many GEMM tiles");
   const unsigned grid = (unsigned)std::min<long long>(items, nsm);
-  kern<<<grid, kThreads, sm, s>>>(pl.p, pl.splits, (int)items);
+  kern<<<grid, 64 + 32 * EPW, sm, s>>>(pl.p, pl.splits, (int)items);
   RTCC_CUDA(cudaGetLastError());
 }
 
@@ -437,6 +553,12 @@ void tc_gemm_plan(TcGemmPlan& pl, int kind, const void* A, int planesA, const vo
   RTCC_REQUIRE(M * planesA < (1ll << 31) && N * planesB < (1ll << 31) && NB < 65536, "GEMM extents too large");
   pl.kind = kind;
   pl.bn = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
+  // Short K loops leave the epilogue as the bottleneck: one item then covers both planes of a
+  // complex output (whole 16-byte elements written once, by eight epilogue warps).  Two planes
+  // of accumulators, double-buffered, fit TMEM's 512 columns up to a 128-column tile.
+  const bool both = pl.p.nrb == 2 && pl.p.epi.c_cplx && pl.p.nseg[0] == pl.p.nseg[1];
+  pl.p.fused = (both && (long long)pl.p.nseg[0] * (Kpad / tc_kblock_elems(kind)) <= kFuseMaxBlocks) ? 1 : 0;
+  if (pl.p.fused) pl.bn = std::min(pl.bn, 128);
   pl.NB = NB;
   pl.p.M = (int)M;
   pl.p.N = (int)N;
@@ -445,7 +567,7 @@ void tc_gemm_plan(TcGemmPlan& pl, int kind, const void* A, int planesA, const vo
   make_map(&pl.p.tmA, kind, A, M * planesA, Kpad, NB, BM);
   make_map(&pl.p.tmB, kind, B, N * planesB, Kpad, NB, pl.bn);
   // split K when the output has less than one wave of tiles and the K loop is long
-  const long long tiles = ((M + BM - 1) / BM) * ((N + pl.bn - 1) / pl.bn) * NB * pl.p.nrb;
+  const long long tiles = ((M + BM - 1) / BM) * ((N + pl.bn - 1) / pl.bn) * NB * (pl.p.fused ? 1 : pl.p.nrb);
   const int nv = pl.p.nseg[0] * pl.p.nkb;
   int splits = 1;
   if (tiles < 152 && nv >= 32) splits = (int)std::max(1ll, std::min<long long>((2 * 152 + tiles - 1) / tiles, nv / 16));
@@ -456,13 +578,13 @@ void tc_gemm_plan(TcGemmPlan& pl, int kind, const void* A, int planesA, const vo
 
 void launch_tc_gemm(const TcGemmPlan& p, cudaStream_t s) {
   if (p.kind == 0) {
-    if (p.bn == 64) launch_inst<64, 0, 8>(p, s);
-    else if (p.bn == 128) launch_inst<128, 0, 6>(p, s);
-    else launch_inst<256, 0, 4>(p, s);
+    if (p.bn == 64) launch_inst<64, 0, 7, 8>(p, s);
+    else if (p.bn == 128) launch_inst<128, 0, 5, 8>(p, s);
+    else launch_inst<256, 0, 4, 4>(p, s);
   } else {
-    if (p.bn == 64) launch_inst<64, 1, 8>(p, s);
-    else if (p.bn == 128) launch_inst<128, 1, 6>(p, s);
-    else launch_inst<256, 1, 4>(p, s);
+    if (p.bn == 64) launch_inst<64, 1, 7, 8>(p, s);
+    else if (p.bn == 128) launch_inst<128, 1, 5, 8>(p, s);
+    else launch_inst<256, 1, 4, 4>(p, s);
   }
 }
 

@@ -9,6 +9,7 @@
 #include "common.cuh"
 #include <cuda_bf16.h>
 #include <algorithm>
+#include <type_traits>
 
 namespace rtcc {
 namespace {
@@ -27,6 +28,14 @@ __device__ __forceinline__ float tf32_rn(float x) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
 }
+
+template <typename R>
+__device__ __forceinline__ R cvt_r(double x) {
+  if constexpr (std::is_same<R, float>::value) return f64_to_f32_bits(x);
+  else return x;
+}
+__device__ __forceinline__ double cvt_d(float x) { return f32_to_f64_bits(x); }
+__device__ __forceinline__ double cvt_d(double x) { return x; }
 
 template <int ELEM>
 __device__ __forceinline__ void put(void* dst, size_t i, double x, int part, int round_tf32) {
@@ -172,16 +181,17 @@ struct Vec4<PE_BF16> {
   using T = uint2;
 };
 
+// One split part of a value already rounded to binary32: hi = x rounded to the plane type,
+// lo = x - hi (exact in binary32; the bf16 store rounds it).  The residual of the binary64 ->
+// binary32 rounding (2^-24 relative) is far below what the hi/lo pair resolves.
 template <int ELEM>
-__device__ __forceinline__ float part_value(double x, int part) {
+__device__ __forceinline__ float part_value(float x, int part) {
   if constexpr (ELEM == PE_F32) {
-    if (part == SP_FULL) return tf32_rn((float)x);
-    const float hi = tf32_rn((float)x);
-    return part == SP_HI ? hi : tf32_rn((float)(x - (double)hi));
+    const float hi = tf32_rn(x);
+    return part == SP_LO ? tf32_rn(x - hi) : hi;
   } else {
-    if (part == SP_FULL) return __bfloat162float(__float2bfloat16_rn((float)x));
-    const __nv_bfloat16 hi = __float2bfloat16_rn((float)x);
-    return part == SP_HI ? __bfloat162float(hi) : __bfloat162float(__float2bfloat16_rn((float)(x - (double)__bfloat162float(hi))));
+    const float hi = __bfloat162float(__float2bfloat16_rn(x));
+    return part == SP_LO ? x - hi : hi;
   }
 }
 
@@ -226,18 +236,18 @@ __global__ void pack_planes_direct_kernel(PackDesc d) {
   for (unsigned row = blockIdx.y * blockDim.y + threadIdx.y; row < NR; row += gridDim.y * blockDim.y) {
     const unsigned bt = row / R, m = row - bt * R;
     const long long base = imap32(d.bat, bt) + imap32(d.rows, m);
-    double xr[4], xi[4];
+    float xr[4], xi[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      xr[j] = 0.0;
-      xi[j] = 0.0;
+      xr[j] = 0.f;
+      xi[j] = 0.f;
       if (kv[j]) {
         if (d.src_cplx) {
           const double2 v = reinterpret_cast<const double2*>(d.src)[base + coff[j]];
-          xr[j] = v.x;
-          xi[j] = v.y;
+          xr[j] = f64_to_f32_bits(v.x);
+          xi[j] = f64_to_f32_bits(v.y);
         } else {
-          xr[j] = d.src[base + coff[j]];
+          xr[j] = f64_to_f32_bits(d.src[base + coff[j]]);
         }
       }
     }
@@ -257,7 +267,7 @@ __global__ void pack_planes_direct_kernel(PackDesc d) {
 // the store phase writes 2 consecutive k per thread (a warp covers 64 k of one row).
 template <int ELEM>
 __global__ void __launch_bounds__(256) pack_planes_transpose_kernel(PackDesc d) {
-  __shared__ double2 tl[64][33];
+  __shared__ float2 tl[64][33];
   const unsigned R = (unsigned)d.R, K = (unsigned)d.K, Kp = (unsigned)d.Kpad;
   const unsigned NR = (unsigned)(d.NB * d.R);
   const unsigned nkt = (Kp + 63) / 64, nrt = (NR + 31) / 32;
@@ -276,11 +286,15 @@ __global__ void __launch_bounds__(256) pack_planes_transpose_kernel(PackDesc d) 
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const unsigned k = k0 + ty + 8 * i;
-          double2 v = make_double2(0.0, 0.0);
+          float2 v = make_float2(0.f, 0.f);
           if (rbase >= 0 && k < K) {
             const long long off = rbase + imap32(d.cols, k);
-            if (d.src_cplx) v = reinterpret_cast<const double2*>(d.src)[off];
-            else v.x = d.src[off];
+            if (d.src_cplx) {
+              const double2 x = reinterpret_cast<const double2*>(d.src)[off];
+              v = make_float2(f64_to_f32_bits(x.x), f64_to_f32_bits(x.y));
+            } else {
+              v.x = f64_to_f32_bits(d.src[off]);
+            }
           }
           tl[ty + 8 * i][tx] = v;
         }
@@ -291,7 +305,7 @@ __global__ void __launch_bounds__(256) pack_planes_transpose_kernel(PackDesc d) 
         const unsigned row = r0 + ty + 8 * i, kk = 2 * tx, k = k0 + kk;
         if (row < NR && k < Kp) {
           const unsigned bt = row / R, m = (unsigned)imap32(d.rd_dst, row - bt * R);
-          const double2 v0 = tl[kk][ty + 8 * i], v1 = tl[kk + 1][ty + 8 * i];
+          const float2 v0 = tl[kk][ty + 8 * i], v1 = tl[kk + 1][ty + 8 * i];
           for (int pl = 0; pl < np; ++pl) {
             const int part = d.rb_part[pl];
             const bool im = d.comp[pl][0] != 0;
@@ -390,35 +404,62 @@ __global__ void __launch_bounds__(256) unpack_transpose_kernel(UnpackDesc d) {
 }
 
 // rows (bt, m) over blockIdx.y/threadIdx.y, n over x; K walked with an odometer (no divisions)
-__global__ void direct_kernel(DirectDesc d) {
+// F32: operands rounded to binary32 with integer operations and products summed in float32
+// (reduced-precision programs, whose contractions resolve far less than 2^-24); otherwise
+// float64 throughout.
+template <bool F32>
+__global__ void __launch_bounds__(128) direct_kernel(DirectDesc d) {
+  using R = typename std::conditional<F32, float, double>::type;
+  constexpr int RB = 32;   // rows per tile: their offsets are decoded once into shared memory
+  __shared__ long long s_a[RB], s_b[RB], s_c[RB];
   const unsigned M = (unsigned)d.M, N = (unsigned)d.N;
   const unsigned NR = (unsigned)(d.NB * d.M);
-  for (unsigned row = blockIdx.y * blockDim.y + threadIdx.y; row < NR; row += gridDim.y * blockDim.y) {
-    const unsigned bt = row / M, m = row - bt * M;
-    const long long a0 = imap32(d.ab, bt) + imap32(d.am, m);
-    const long long bb0 = imap32(d.bb, bt);
-    const long long cb0 = imap32(d.cb, bt) + imap32(d.cm, m);
-    for (unsigned n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
-      const long long b0 = bb0 + imap32(d.bn, n);
+  const unsigned nrt = (NR + RB - 1) / RB;
+  const unsigned tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const R ar = (R)d.ar, ai = (R)d.ai;
+  const unsigned n = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool col_ok = n < N;
+  const long long bn_off = col_ok ? imap32(d.bn, n) : 0, cn_off = col_ok ? imap32(d.cn, n) : 0;
+  for (unsigned rt = blockIdx.y; rt < nrt; rt += gridDim.y) {
+    const unsigned r0 = rt * RB;
+    __syncthreads();
+    if (tid < RB) {
+      const unsigned row = r0 + tid;
+      long long a = 0, b = 0, c = 0;
+      if (row < NR) {
+        const unsigned bt = row / M, m = row - bt * M;
+        a = imap32(d.ab, bt) + imap32(d.am, m);
+        b = imap32(d.bb, bt);
+        c = imap32(d.cb, bt) + imap32(d.cm, m);
+      }
+      s_a[tid] = a;
+      s_b[tid] = b;
+      s_c[tid] = c;
+    }
+    __syncthreads();
+    if (!col_ok) continue;
+    const unsigned nrows = min((unsigned)RB, NR - r0);
+    for (unsigned r = threadIdx.y; r < nrows; r += blockDim.y) {
+      const long long a0 = s_a[r], b0 = s_b[r] + bn_off;
       int ctr[kMaxLab];
       for (int q = 0; q < kMaxLab; ++q) ctr[q] = 0;
       long long ao = 0, bo = 0;
-      double sr = 0.0, si = 0.0;
+      R sr = 0, si = 0;
       for (long long k = 0; k < d.K; ++k) {
-        double ar_, ai_ = 0.0, br_, bi_ = 0.0;
+        R ar_, ai_ = 0, br_, bi_ = 0;
         if (d.a_cplx) {
           const double2 x = reinterpret_cast<const double2*>(d.A)[a0 + ao];
-          ar_ = x.x;
-          ai_ = x.y;
+          ar_ = cvt_r<R>(x.x);
+          ai_ = cvt_r<R>(x.y);
         } else {
-          ar_ = d.A[a0 + ao];
+          ar_ = cvt_r<R>(d.A[a0 + ao]);
         }
         if (d.b_cplx) {
           const double2 x = reinterpret_cast<const double2*>(d.B)[b0 + bo];
-          br_ = x.x;
-          bi_ = x.y;
+          br_ = cvt_r<R>(x.x);
+          bi_ = cvt_r<R>(x.y);
         } else {
-          br_ = d.B[b0 + bo];
+          br_ = cvt_r<R>(d.B[b0 + bo]);
         }
         sr += ar_ * br_ - ai_ * bi_;
         si += ar_ * bi_ + ai_ * br_;
@@ -432,31 +473,40 @@ __global__ void direct_kernel(DirectDesc d) {
           ctr[q] = 0;
         }
       }
-      const long long off = cb0 + imap32(d.cn, n);
-      const double vr = d.ar * sr - d.ai * si;
-      const double vi = d.ar * si + d.ai * sr;
+      const long long off = s_c[r] + cn_off;
+      const double vr = cvt_d(ar * sr - ai * si);
+      const double vi = cvt_d(ar * si + ai * sr);
       if (d.c_cplx) {
         double2* c = reinterpret_cast<double2*>(d.C) + off;
-        double2 x = *c;
-        x.x += vr;
-        x.y += vi;
-        *c = x;
+        if (d.store) {
+          *c = make_double2(vr, vi);
+        } else {
+          double2 x = *c;
+          x.x += vr;
+          x.y += vi;
+          *c = x;
+        }
       } else {
-        d.C[off] += vr;
+        d.C[off] = d.store ? vr : d.C[off] + vr;
       }
     }
   }
 }
 
-// C[all labels] += alpha * A: the innermost label over threadIdx.x, the rest over rows
+__device__ __forceinline__ double flip_sign(double x) {
+  return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
+}
+
+// C[all labels] (+)= alpha * A: the innermost label over threadIdx.x, the rest over rows.
+// A real scale costs one float64 fused multiply-add per component; storing into a fresh output
+// with a unit scale is a copy (a sign-bit flip for -1) with no float64 instruction at all.
 __global__ void add_kernel(AddDesc d, unsigned inner) {
   const unsigned rows = (unsigned)(d.n / inner);
-  IndexMap co = d.c_all, ao = d.a_all;   // outer labels (all but the innermost)
-  co.n -= 1;
-  ao.n -= 1;
   const long long cs = d.c_all.strides[d.c_all.n - 1], as = d.a_all.strides[d.a_all.n - 1];
+  const double ar = d.ar, ai = d.ai;
+  const bool real_scale = ai == 0.0, unit = real_scale && (ar == 1.0 || ar == -1.0), neg = ar < 0.0;
   for (unsigned r = blockIdx.y * blockDim.y + threadIdx.y; r < rows; r += gridDim.y * blockDim.y) {
-    const long long cb = imap32(co, r), ab = imap32(ao, r);
+    const long long cb = imap32_outer(d.c_all, r), ab = imap32_outer(d.a_all, r);
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < inner; i += gridDim.x * blockDim.x) {
       const long long c_off = cb + (long long)i * cs, a_off = ab + (long long)i * as;
       double xr, xi = 0.0;
@@ -467,15 +517,26 @@ __global__ void add_kernel(AddDesc d, unsigned inner) {
       } else {
         xr = d.A[a_off];
       }
-      const double vr = d.ar * xr - d.ai * xi, vi = d.ar * xi + d.ai * xr;
       if (d.c_cplx) {
         double2* c = reinterpret_cast<double2*>(d.C) + c_off;
-        double2 x = *c;
-        x.x += vr;
-        x.y += vi;
-        *c = x;
+        if (d.store) {
+          if (unit) *c = neg ? make_double2(flip_sign(xr), flip_sign(xi)) : make_double2(xr, xi);
+          else if (real_scale) *c = make_double2(ar * xr, ar * xi);
+          else *c = make_double2(ar * xr - ai * xi, ar * xi + ai * xr);
+        } else {
+          double2 x = *c;
+          if (real_scale) {
+            x.x = fma(ar, xr, x.x);
+            x.y = fma(ar, xi, x.y);
+          } else {
+            x.x += ar * xr - ai * xi;
+            x.y += ar * xi + ai * xr;
+          }
+          *c = x;
+        }
       } else {
-        d.C[c_off] += vr;
+        if (d.store) d.C[c_off] = unit ? (neg ? flip_sign(xr) : xr) : ar * xr;
+        else d.C[c_off] = fma(ar, xr, d.C[c_off]);
       }
     }
   }
@@ -649,8 +710,9 @@ void launch_direct(const DirectDesc& d, cudaStream_t s) {
   const unsigned bx = N >= 128 ? 128u : std::max(32u, (N + 31) / 32 * 32);
   const unsigned by = 128 / bx;
   dim3 blk(bx, by);
-  dim3 grid(std::min((N + bx - 1) / bx, 4096u), (unsigned)std::min((NR + by - 1) / by, 65535ll));
-  direct_kernel<<<grid, blk, 0, s>>>(d);
+  dim3 grid((N + bx - 1) / bx, (unsigned)std::min((NR + 31) / 32, 65535ll));
+  if (d.f32) direct_kernel<true><<<grid, blk, 0, s>>>(d);
+  else direct_kernel<false><<<grid, blk, 0, s>>>(d);
   RTCC_CUDA(cudaGetLastError());
 }
 void launch_reduce(const DirectDesc& d, long long splits, cudaStream_t s) {

@@ -28,9 +28,10 @@ def test_gemm_matches_float64(prec, shape):
 
 @pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("kinds", ["cr", "rc", "cc"])
-@pytest.mark.parametrize("shape", [(2, 150, 70, 90), (1, 33, 300, 1200)])
+@pytest.mark.parametrize("shape", [(2, 150, 70, 90), (1, 33, 300, 1200), (3, 300, 130, 40), (1, 1000, 50, 200)])
 def test_complex_gemm_matches_float64(prec, kinds, shape):
-    """Complex operands: re/im planes and the segment table (Ar Br - Ai Bi, Ar Bi + Ai Br)."""
+    """Complex operands: re/im planes and the segment table (Ar Br - Ai Bi, Ar Bi + Ai Br).
+    Short K loops take the both-planes work items (ragged 128-wide and 64-wide tiles)."""
     from paper_2205_05175_gb300 import rtcc
     nb, M, N, K = shape
     rng = np.random.default_rng(99 + N)
