@@ -117,15 +117,20 @@ struct DirectDesc {
   int f32;          // 1: sum products in float32 (reduced-precision programs)
 };
 
-// C[lc] += alpha * A[la] with labels(A) a subset of labels(C) (broadcast over the rest).
+// C[lc] (+)= sum_s alpha_s * A_s[la_s] with labels(A_s) a subset of labels(C) (broadcast over the
+// rest); several sources when consecutive adds into one output are merged.
+constexpr int kMaxAddSrc = 4;
 struct AddDesc {
-  const double* A; double* C;
-  int a_cplx, c_cplx;
+  double* C;
+  int c_cplx;
   int store;        // 1: C is known to be zero: store instead of read-modify-write
   IndexMap c_all;   // all C labels
-  IndexMap a_all;   // same labels, A's strides (0 where A lacks the label)
   long long n;
-  double ar, ai;
+  int nsrc;
+  const double* A[kMaxAddSrc];
+  int a_cplx[kMaxAddSrc];
+  IndexMap a_all[kMaxAddSrc];   // C's labels, source s's strides (0 where the source lacks the label)
+  double ar[kMaxAddSrc], ai[kMaxAddSrc];
 };
 
 // ---------------------------------------------------------------------------------------
@@ -213,16 +218,18 @@ __device__ __forceinline__ long long imap32_outer(const IndexMap& m, unsigned id
 // NaN stays NaN.
 __device__ __forceinline__ float f64_to_f32_bits(double x) {
   const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-  const unsigned sign = hi & 0x80000000u;
-  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
-  if (e >= 255) {
-    const bool nan = ((hi >> 20) & 0x7ffu) == 0x7ffu && (((hi & 0xfffffu) | lo) != 0u);
-    return __uint_as_float(sign | (nan ? 0x7fc00000u : 0x7f800000u));
+  const unsigned ahi = hi & 0x7fffffffu;
+  // bits 31..23 = the low 9 exponent bits, 22..0 = the top 23 significand bits
+  unsigned t = __funnelshift_l(lo, hi, 3);
+  // for biased exponents 897..1150 the binary32 exponent (E - 896) is E's low 8 bits with the
+  // top one flipped; adding the first dropped bit rounds (a carry moves into the exponent)
+  t = ((t & 0x7fffffffu) ^ 0x40000000u) + ((lo >> 28) & 1u);
+  if (ahi < 0x38100000u) {
+    t = 0u;   // below 2^-126
+  } else if (ahi >= 0x47f00000u) {
+    t = (ahi > 0x7ff00000u || (ahi == 0x7ff00000u && lo != 0u)) ? 0x7fc00000u : 0x7f800000u;
   }
-  if (e <= 0) return __uint_as_float(sign);
-  unsigned bits = ((unsigned)e << 23) + ((((hi & 0xfffffu) << 3) | (lo >> 29)) + ((lo >> 28) & 1u));
-  if (bits > 0x7f800000u) bits = 0x7f800000u;
-  return __uint_as_float(sign | bits);
+  return __uint_as_float(t | (hi & 0x80000000u));
 }
 
 // binary32 -> binary64, exact (subnormal inputs are normalised).

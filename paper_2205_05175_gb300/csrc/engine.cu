@@ -11,7 +11,7 @@ void launch_reduce(const DirectDesc& d, long long splits, cudaStream_t s);
 
 namespace {
 
-enum CompKind : int { CK_ADD = 0, CK_DIRECT = 1, CK_REDUCE = 2, CK_GEMM = 3 };
+enum CompKind : int { CK_ADD = 0, CK_DIRECT = 1, CK_REDUCE = 2, CK_GEMM = 3, CK_MERGED = 4 };   // CK_MERGED: folded into an earlier add
 
 constexpr long long kDirectMaxWork = 1ll << 21;   // real multiply-adds below which a term runs direct
 constexpr long long kReduceMaxOut = 2048;         // outputs up to which a long-K term is split-K reduced
@@ -96,6 +96,7 @@ bool row_is_unit(const Tensor& t, const std::string& tl, const std::string& rows
 struct Compiled {
   int kind = CK_ADD;
   AddDesc add{};
+  std::vector<int> add_ops;   // CK_ADD: the program ops whose sources this kernel sums (first = own op)
   DirectDesc dir{};
   long long splits = 1;
   // GEMM path
@@ -352,24 +353,12 @@ void Engine::plan(Program& P) {
       k.kind = CK_ADD;
       AddDesc& d = k.add;
       d.store = c_fresh ? 1 : 0;
-      d.A = A.ptr;
       d.C = C.ptr;
-      d.a_cplx = A.cplx;
       d.c_cplx = C.cplx;
       d.c_all = map_for(C, op.lc, op.lc);
-      d.a_all = d.c_all;
-      for (int i = 0; i < d.c_all.n; ++i) {
-        const size_t p = op.la.find(op.lc[i]);
-        if (p == std::string::npos) d.a_all.strides[i] = 0;
-        else {
-          RTCC_REQUIRE(A.dims[p] == C.dims[i], "extent mismatch in add " + A.name + " -> " + C.name);
-          d.a_all.strides[i] = A.strides[p];
-        }
-      }
-      for (char l : op.la) RTCC_REQUIRE(op.lc.find(l) != std::string::npos, "add reduces a label: " + A.name);
       d.n = prod_dims(d.c_all);
-      d.ar = op.alpha.real();
-      d.ai = op.alpha.imag();
+      d.nsrc = 0;
+      add_source(k, P.ops, (int)P.comp.size(), op.lc);
       P.comp.push_back(cp);
       continue;
     }
@@ -658,6 +647,90 @@ void Engine::plan(Program& P) {
     }
     P.comp.push_back(cp);
   }
+  merge_adds(P);
+}
+
+// Source `oi` (an add into the output of kernel k) expressed in the labels `lc` that k uses for
+// its output: the op's own output labels are renamed position by position onto lc.
+bool Engine::add_source(Compiled& k, const std::vector<Op>& ops, int oi, const std::string& lc) {
+  AddDesc& d = k.add;
+  if (d.nsrc >= kMaxAddSrc) return false;
+  const Op& op = ops[oi];
+  const Tensor& C = tensors_[op.c];
+  const Tensor& A = tensors_[op.a];
+  std::string la = op.la;
+  if (op.lc != lc) {
+    for (size_t x = 0; x < op.lc.size(); ++x)
+      for (size_t y = x + 1; y < op.lc.size(); ++y)
+        if (op.lc[x] == op.lc[y]) return false;   // repeated output labels: no renaming
+    for (char& l : la) {
+      const size_t p = op.lc.find(l);
+      if (p == std::string::npos) return false;
+      l = lc[p];
+    }
+  }
+  for (char l : la) RTCC_REQUIRE(lc.find(l) != std::string::npos, "add reduces a label: " + A.name);
+  const int q = d.nsrc;
+  d.a_cplx[q] = A.cplx;
+  d.a_all[q] = d.c_all;
+  for (int i = 0; i < d.c_all.n; ++i) {
+    const size_t p = la.find(lc[i]);
+    if (p == std::string::npos) d.a_all[q].strides[i] = 0;
+    else {
+      RTCC_REQUIRE(A.dims[p] == C.dims[i], "extent mismatch in add " + A.name + " -> " + C.name);
+      d.a_all[q].strides[i] = A.strides[p];
+    }
+  }
+  d.A[q] = A.ptr;
+  d.ar[q] = op.alpha.real();
+  d.ai[q] = op.alpha.imag();
+  d.nsrc = q + 1;
+  k.add_ops.push_back(oi);
+  return true;
+}
+
+// Within a run of consecutive adds that neither read what the run writes nor write what it reads,
+// adds into the same output become one kernel that reads each source once and writes the output once.
+void Engine::merge_adds(Program& P) {
+  const size_t n = P.ops.size();
+  for (size_t i = 0; i < n;) {
+    if (P.ops[i].kind != OP_ADD) {
+      ++i;
+      continue;
+    }
+    size_t j = i;
+    std::set<int> wr, rd;
+    while (j < n && P.ops[j].kind == OP_ADD) {
+      wr.insert(P.ops[j].c);
+      rd.insert(P.ops[j].a);
+      ++j;
+    }
+    // independence by address range, so that views of one buffer count as the same data
+    auto range = [&](int id) {
+      const Tensor& t = tensors_[id];
+      long long hi = 1;
+      for (size_t q = 0; q < t.dims.size(); ++q) hi += (long long)(t.dims[q] - 1) * std::llabs(t.strides[q]);
+      const char* b = reinterpret_cast<const char*>(t.ptr);
+      return std::make_pair(b, b + hi * (t.cplx ? 16 : 8));
+    };
+    bool indep = true;
+    for (int w : wr)
+      for (int r : rd) {
+        const auto x = range(w), y = range(r);
+        if (x.first < y.second && y.first < x.second) indep = false;
+      }
+    if (indep) {
+      for (size_t h = i; h < j; ++h) {
+        Compiled& head = *P.comp[h];
+        if (head.kind != CK_ADD) continue;
+        for (size_t r = h + 1; r < j; ++r) {
+          if (P.comp[r]->kind != CK_ADD || P.ops[r].c != P.ops[h].c) continue;
+          if (add_source(head, P.ops, (int)r, P.ops[h].lc)) P.comp[r]->kind = CK_MERGED;
+        }
+      }
+    }
+    i = j;
+  }
 }
 
 void Engine::bind(Program& P) {
@@ -668,10 +741,11 @@ void Engine::bind(Program& P) {
     const Tensor& C = tensors_[op.c];
     const Tensor& A = tensors_[op.a];
     if (k.kind == CK_ADD) {
-      k.add.A = A.ptr;
       k.add.C = C.ptr;
+      for (size_t q = 0; q < k.add_ops.size(); ++q) k.add.A[q] = tensors_[P.ops[k.add_ops[q]].a].ptr;
       continue;
     }
+    if (k.kind == CK_MERGED) continue;
     const Tensor& B = tensors_[op.b];
     k.dir.A = A.ptr;
     k.dir.B = B.ptr;
@@ -754,11 +828,16 @@ void Engine::run(const Program& P) {
       tag = tagbuf.c_str();
     }
     switch (k.kind) {
-      case CK_ADD:
+      case CK_MERGED:
+        break;
+      case CK_ADD: {
+        double abytes = 0.0;
+        for (int q = 0; q < k.add.nsrc; ++q) abytes += k.add.a_cplx[q] ? 16 : 8;
         pr.start(stream_);
         launch_add(k.add, stream_);
-        pr.stop(stream_, KC_ADD, 0.0, (double)k.add.n * ((k.add.a_cplx ? 16 : 8) + (k.add.store ? 1 : 2) * (k.add.c_cplx ? 16 : 8)), tag);
+        pr.stop(stream_, KC_ADD, 0.0, (double)k.add.n * (abytes + (k.add.store ? 1 : 2) * (k.add.c_cplx ? 16 : 8)), tag);
         break;
+      }
       case CK_DIRECT:
         pr.start(stream_);
         launch_direct(k.dir, stream_);
@@ -809,9 +888,11 @@ void Engine::run(const Program& P) {
 EngineStats Engine::stats_of(const Program& P) const {
   EngineStats s;
   for (const auto& cp : P.comp) {
+    if (cp->kind == CK_MERGED) continue;
     if (cp->kind == CK_GEMM) {
       s.gemm_flops += cp->alg_flops;
-      s.launches += 2 + (cp->a_const ? 0 : 1) + (cp->b_const ? 0 : 1);
+      // packs of non-constant operands, the GEMM, and the unpack of the float64 SIMT path
+      s.launches += (cp->tc_kind >= 0 ? 1 : 2) + (cp->a_const ? 0 : 1) + (cp->b_const ? 0 : 1);
     } else {
       s.direct_flops += cp->alg_flops;
       s.launches += 1;

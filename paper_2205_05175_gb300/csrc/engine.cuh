@@ -137,6 +137,8 @@ class Engine {
  private:
   void plan(Program& P);
   void bind(Program& P);
+  bool add_source(Compiled& k, const std::vector<Op>& ops, int oi, const std::string& lc);
+  void merge_adds(Program& P);
 
   Prec prec_;
   cudaStream_t stream_;

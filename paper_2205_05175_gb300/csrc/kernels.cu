@@ -218,13 +218,19 @@ __device__ __forceinline__ void store2(void* dst, size_t idx, float a, float b) 
   }
 }
 
-// Source unit stride along K: 4 consecutive k per thread (offsets computed once), rows strided over y.
+// Source unit stride along K: 4 consecutive k per thread (their source offsets decoded once),
+// rows in tiles of 32 whose offsets are decoded once per tile into shared memory.
 template <int ELEM>
-__global__ void pack_planes_direct_kernel(PackDesc d) {
+__global__ void __launch_bounds__(256) pack_planes_direct_kernel(PackDesc d) {
+  constexpr int RT = 32;
+  __shared__ long long s_src[RT];
+  __shared__ unsigned long long s_dst[RT];   // packed element index of (row, plane 0, k = 0)
   const unsigned R = (unsigned)d.R, K = (unsigned)d.K, Kp = (unsigned)d.Kpad;
   const unsigned NR = (unsigned)(d.NB * d.R);
+  const unsigned nrt = (NR + RT - 1) / RT;
+  const unsigned tid = threadIdx.y * blockDim.x + threadIdx.x;
   const unsigned k4 = 4u * (blockIdx.x * blockDim.x + threadIdx.x);
-  if (k4 >= Kp) return;
+  const bool kok = k4 < Kp;
   long long coff[4];
   bool kv[4];
 #pragma unroll
@@ -233,62 +239,95 @@ __global__ void pack_planes_direct_kernel(PackDesc d) {
     coff[j] = kv[j] ? imap32(d.cols, k4 + j) : 0;
   }
   const int np = d.nrb;
-  for (unsigned row = blockIdx.y * blockDim.y + threadIdx.y; row < NR; row += gridDim.y * blockDim.y) {
-    const unsigned bt = row / R, m = row - bt * R;
-    const long long base = imap32(d.bat, bt) + imap32(d.rows, m);
-    float xr[4], xi[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      xr[j] = 0.f;
-      xi[j] = 0.f;
-      if (kv[j]) {
-        if (d.src_cplx) {
-          const double2 v = reinterpret_cast<const double2*>(d.src)[base + coff[j]];
-          xr[j] = f64_to_f32_bits(v.x);
-          xi[j] = f64_to_f32_bits(v.y);
-        } else {
-          xr[j] = f64_to_f32_bits(d.src[base + coff[j]]);
-        }
+  const unsigned long long pstride = (unsigned long long)R * Kp;   // plane stride in elements
+  for (unsigned rt = blockIdx.y; rt < nrt; rt += gridDim.y) {
+    __syncthreads();
+    if (tid < RT) {
+      const unsigned row = rt * RT + tid;
+      if (row < NR) {
+        const unsigned bt = row / R, m = row - bt * R;
+        s_src[tid] = imap32(d.bat, bt) + imap32(d.rows, m);
+        s_dst[tid] = ((unsigned long long)bt * np * R + m) * Kp;
       }
     }
-    for (int pl = 0; pl < np; ++pl) {
-      const int part = d.rb_part[pl];
-      const bool im = d.comp[pl][0] != 0;
-      float o[4];
+    __syncthreads();
+    if (!kok) continue;
+    const unsigned nrows = min((unsigned)RT, NR - rt * RT);
+    for (unsigned r = threadIdx.y; r < nrows; r += blockDim.y) {
+      const long long base = s_src[r];
+      float xr[4], xi[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) o[j] = part_value<ELEM>(im ? xi[j] : xr[j], part);
-      const size_t idx = (((size_t)bt * np + pl) * R + m) * (size_t)Kp + k4;
-      store4<ELEM>(d.dst, idx, o[0], o[1], o[2], o[3]);
+      for (int j = 0; j < 4; ++j) {
+        xr[j] = 0.f;
+        xi[j] = 0.f;
+        if (kv[j]) {
+          if (d.src_cplx) {
+            const double2 v = reinterpret_cast<const double2*>(d.src)[base + coff[j]];
+            xr[j] = f64_to_f32_bits(v.x);
+            xi[j] = f64_to_f32_bits(v.y);
+          } else {
+            xr[j] = f64_to_f32_bits(d.src[base + coff[j]]);
+          }
+        }
+      }
+      const unsigned long long drow = s_dst[r] + k4;
+      for (int pl = 0; pl < np; ++pl) {
+        const int part = d.rb_part[pl];
+        const bool im = d.comp[pl][0] != 0;
+        float o[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) o[j] = part_value<ELEM>(im ? xi[j] : xr[j], part);
+        store4<ELEM>(d.dst, drow + pl * pstride, o[0], o[1], o[2], o[3]);
+      }
     }
   }
 }
 
-// Source unit stride along a row label: 32 read-order rows x 64 k per tile through shared memory;
-// the store phase writes 2 consecutive k per thread (a warp covers 64 k of one row).
+// Source unit stride along a row label: 32 read-order rows x 64 k per tile through shared memory,
+// with the tile's k offsets and row offsets decoded once into shared memory; the store phase
+// writes 2 consecutive k per thread (a warp covers 64 k of one row).
 template <int ELEM>
 __global__ void __launch_bounds__(256) pack_planes_transpose_kernel(PackDesc d) {
   __shared__ float2 tl[64][33];
+  __shared__ long long s_k[64];
+  __shared__ long long s_src[32];
+  __shared__ unsigned long long s_dst[32];
   const unsigned R = (unsigned)d.R, K = (unsigned)d.K, Kp = (unsigned)d.Kpad;
   const unsigned NR = (unsigned)(d.NB * d.R);
   const unsigned nkt = (Kp + 63) / 64, nrt = (NR + 31) / 32;
-  const unsigned tx = threadIdx.x, ty = threadIdx.y;
+  const unsigned tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const int np = d.nrb;
+  const unsigned long long pstride = (unsigned long long)R * Kp;
   for (unsigned rt = blockIdx.y; rt < nrt; rt += gridDim.y) {
+    const unsigned r0 = rt * 32;
+    __syncthreads();
+    if (tid < 32) {
+      const unsigned row = r0 + tid;
+      long long src = -1;
+      unsigned long long dst = 0;
+      if (row < NR) {
+        const unsigned bt = row / R, mr = row - bt * R;
+        src = imap32(d.bat, bt) + imap32(d.rd_src, mr);
+        dst = ((unsigned long long)bt * np * R + (unsigned)imap32(d.rd_dst, mr)) * Kp;
+      }
+      s_src[tid] = src;
+      s_dst[tid] = dst;
+    }
     for (unsigned kt = blockIdx.x; kt < nkt; kt += gridDim.x) {
-      const unsigned r0 = rt * 32, k0 = kt * 64;
+      const unsigned k0 = kt * 64;
+      if (tid >= 64 && tid < 128) {
+        const unsigned k = k0 + tid - 64;
+        s_k[tid - 64] = (k < K) ? imap32(d.cols, k) : -1;
+      }
+      __syncthreads();
       {
-        const unsigned row = r0 + tx;
-        long long rbase = -1;
-        if (row < NR) {
-          const unsigned bt = row / R, mr = row - bt * R;
-          rbase = imap32(d.bat, bt) + imap32(d.rd_src, mr);
-        }
+        const long long rbase = s_src[tx];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const unsigned k = k0 + ty + 8 * i;
+          const long long ko = s_k[ty + 8 * i];
           float2 v = make_float2(0.f, 0.f);
-          if (rbase >= 0 && k < K) {
-            const long long off = rbase + imap32(d.cols, k);
+          if (rbase >= 0 && ko >= 0) {
+            const long long off = rbase + ko;
             if (d.src_cplx) {
               const double2 x = reinterpret_cast<const double2*>(d.src)[off];
               v = make_float2(f64_to_f32_bits(x.x), f64_to_f32_bits(x.y));
@@ -302,16 +341,16 @@ __global__ void __launch_bounds__(256) pack_planes_transpose_kernel(PackDesc d) 
       __syncthreads();
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const unsigned row = r0 + ty + 8 * i, kk = 2 * tx, k = k0 + kk;
-        if (row < NR && k < Kp) {
-          const unsigned bt = row / R, m = (unsigned)imap32(d.rd_dst, row - bt * R);
-          const float2 v0 = tl[kk][ty + 8 * i], v1 = tl[kk + 1][ty + 8 * i];
+        const unsigned r = ty + 8 * i, kk = 2 * tx, k = k0 + kk;
+        if (r0 + r < NR && k < Kp) {
+          const unsigned long long drow = s_dst[r] + k;
+          const float2 v0 = tl[kk][r], v1 = tl[kk + 1][r];
           for (int pl = 0; pl < np; ++pl) {
             const int part = d.rb_part[pl];
             const bool im = d.comp[pl][0] != 0;
             const float a = part_value<ELEM>(im ? v0.y : v0.x, part);
             const float b = part_value<ELEM>(im ? v1.y : v1.x, part);
-            store2<ELEM>(d.dst, (((size_t)bt * np + pl) * R + m) * (size_t)Kp + k, a, b);
+            store2<ELEM>(d.dst, drow + pl * pstride, a, b);
           }
         }
       }
@@ -497,47 +536,82 @@ __device__ __forceinline__ double flip_sign(double x) {
   return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
 }
 
-// C[all labels] (+)= alpha * A: the innermost label over threadIdx.x, the rest over rows.
-// A real scale costs one float64 fused multiply-add per component; storing into a fresh output
-// with a unit scale is a copy (a sign-bit flip for -1) with no float64 instruction at all.
-__global__ void add_kernel(AddDesc d, unsigned inner) {
+// C[all labels] (+)= sum_s alpha_s * A_s: the innermost label over threadIdx.x, the rest over
+// rows.  A real scale costs one float64 fused multiply-add per component; a fresh output whose
+// first source has a unit scale starts from a copy (a sign-bit flip for -1), no float64 work.
+template <int NS>
+__global__ void __launch_bounds__(256) add_kernel(AddDesc d, unsigned inner) {
+  constexpr int RT = 32;   // rows per tile: their offsets are decoded once into shared memory
+  __shared__ long long s_c[RT], s_a[NS][RT];
   const unsigned rows = (unsigned)(d.n / inner);
-  const long long cs = d.c_all.strides[d.c_all.n - 1], as = d.a_all.strides[d.a_all.n - 1];
-  const double ar = d.ar, ai = d.ai;
-  const bool real_scale = ai == 0.0, unit = real_scale && (ar == 1.0 || ar == -1.0), neg = ar < 0.0;
-  for (unsigned r = blockIdx.y * blockDim.y + threadIdx.y; r < rows; r += gridDim.y * blockDim.y) {
-    const long long cb = imap32_outer(d.c_all, r), ab = imap32_outer(d.a_all, r);
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < inner; i += gridDim.x * blockDim.x) {
-      const long long c_off = cb + (long long)i * cs, a_off = ab + (long long)i * as;
-      double xr, xi = 0.0;
-      if (d.a_cplx) {
-        const double2 x = reinterpret_cast<const double2*>(d.A)[a_off];
-        xr = x.x;
-        xi = x.y;
-      } else {
-        xr = d.A[a_off];
+  const unsigned nrt = (rows + RT - 1) / RT;
+  const unsigned tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const long long cs = d.c_all.strides[d.c_all.n - 1];
+  long long as[NS];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) as[q] = d.a_all[q].strides[d.a_all[q].n - 1];
+  const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+  for (unsigned rt = blockIdx.y; rt < nrt; rt += gridDim.y) {
+    __syncthreads();
+    if (tid < RT) {
+      const unsigned row = rt * RT + tid;
+      if (row < rows) {
+        s_c[tid] = imap32_outer(d.c_all, row);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) s_a[q][tid] = imap32_outer(d.a_all[q], row);
       }
-      if (d.c_cplx) {
-        double2* c = reinterpret_cast<double2*>(d.C) + c_off;
-        if (d.store) {
-          if (unit) *c = neg ? make_double2(flip_sign(xr), flip_sign(xi)) : make_double2(xr, xi);
-          else if (real_scale) *c = make_double2(ar * xr, ar * xi);
-          else *c = make_double2(ar * xr - ai * xi, ar * xi + ai * xr);
+    }
+    __syncthreads();
+    if (i >= inner) continue;
+    const unsigned nrows = min((unsigned)RT, rows - rt * RT);
+    for (unsigned r = threadIdx.y; r < nrows; r += blockDim.y) {
+      const long long c_off = s_c[r] + (long long)i * cs;
+      double2* c2 = reinterpret_cast<double2*>(d.C) + c_off;
+      double accr = 0.0, acci = 0.0;
+      if (!d.store) {
+        if (d.c_cplx) {
+          const double2 x = *c2;
+          accr = x.x;
+          acci = x.y;
         } else {
-          double2 x = *c;
-          if (real_scale) {
-            x.x = fma(ar, xr, x.x);
-            x.y = fma(ar, xi, x.y);
-          } else {
-            x.x += ar * xr - ai * xi;
-            x.y += ar * xi + ai * xr;
-          }
-          *c = x;
+          accr = d.C[c_off];
         }
-      } else {
-        if (d.store) d.C[c_off] = unit ? (neg ? flip_sign(xr) : xr) : ar * xr;
-        else d.C[c_off] = fma(ar, xr, d.C[c_off]);
       }
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        const long long a_off = s_a[q][r] + (long long)i * as[q];
+        double xr, xi = 0.0;
+        if (d.a_cplx[q]) {
+          const double2 x = reinterpret_cast<const double2*>(d.A[q])[a_off];
+          xr = x.x;
+          xi = x.y;
+        } else {
+          xr = d.A[q][a_off];
+        }
+        const double ar = d.ar[q], ai = d.ai[q];
+        if (ai == 0.0) {
+          if (q == 0 && d.store) {
+            if (ar == 1.0) {
+              accr = xr;
+              acci = xi;
+            } else if (ar == -1.0) {
+              accr = flip_sign(xr);
+              acci = flip_sign(xi);
+            } else {
+              accr = ar * xr;
+              acci = ar * xi;
+            }
+          } else {
+            accr = fma(ar, xr, accr);
+            acci = fma(ar, xi, acci);
+          }
+        } else {
+          accr += ar * xr - ai * xi;
+          acci += ar * xi + ai * xr;
+        }
+      }
+      if (d.c_cplx) *c2 = make_double2(accr, acci);
+      else d.C[c_off] = accr;
     }
   }
 }
@@ -645,7 +719,10 @@ void launch_pack(const PackDesc& d, cudaStream_t s) {
   if (d.ncs == 1 && d.nss == 1 && d.elem != PE_F64 && d.Kpad % 4 == 0) {
     // tensor-core operand planes
     if (d.transpose) {
-      dim3 grid((unsigned)std::min((d.Kpad + 63) / 64, 4096ll), (unsigned)std::min((NR + 31) / 32, 65535ll));
+      const long long nkt = (d.Kpad + 63) / 64, nrt = (NR + 31) / 32;
+      // each block walks several k tiles of one row tile (the row offsets are decoded once)
+      const long long gx = std::max(1ll, std::min(nkt, (152ll * 32 + nrt - 1) / nrt));
+      dim3 grid((unsigned)gx, (unsigned)std::min(nrt, 65535ll));
       dim3 blk(32, 8);
       if (d.elem == PE_F32) pack_planes_transpose_kernel<PE_F32><<<grid, blk, 0, s>>>(d);
       else pack_planes_transpose_kernel<PE_BF16><<<grid, blk, 0, s>>>(d);
@@ -654,7 +731,7 @@ void launch_pack(const PackDesc& d, cudaStream_t s) {
       const unsigned bx = nq >= 128 ? 128u : std::max(32u, (nq + 31) / 32 * 32);
       const unsigned by = 256 / bx;
       dim3 blk(bx, by);
-      dim3 grid((nq + bx - 1) / bx, (unsigned)std::min((NR + by - 1) / by, 16384ll));
+      dim3 grid((nq + bx - 1) / bx, (unsigned)std::min((NR + 31) / 32, 65535ll));
       if (d.elem == PE_F32) pack_planes_direct_kernel<PE_F32><<<grid, blk, 0, s>>>(d);
       else pack_planes_direct_kernel<PE_BF16><<<grid, blk, 0, s>>>(d);
     }
@@ -728,11 +805,17 @@ void launch_add(const AddDesc& d, cudaStream_t s) {
   RTCC_REQUIRE(d.n < (1ll << 32) && d.c_all.n >= 1, "add extents exceed 32-bit indexing");
   const unsigned inner = (unsigned)d.c_all.dims[d.c_all.n - 1];
   const unsigned rows = (unsigned)(d.n / inner);
-  const unsigned bx = inner >= 256 ? 256u : std::max(32u, (inner + 31) / 32 * 32);
+  const unsigned bx = inner >= 128 ? 128u : std::max(32u, (inner + 31) / 32 * 32);
   const unsigned by = 256 / bx;
   dim3 blk(bx, by);
-  dim3 grid(std::min((inner + bx - 1) / bx, 4096u), std::min((rows + by - 1) / by, 65535u));
-  add_kernel<<<grid, blk, 0, s>>>(d, inner);
+  dim3 grid((inner + bx - 1) / bx, std::min((rows + 31) / 32, 65535u));
+  switch (d.nsrc) {
+    case 1: add_kernel<1><<<grid, blk, 0, s>>>(d, inner); break;
+    case 2: add_kernel<2><<<grid, blk, 0, s>>>(d, inner); break;
+    case 3: add_kernel<3><<<grid, blk, 0, s>>>(d, inner); break;
+    case 4: add_kernel<4><<<grid, blk, 0, s>>>(d, inner); break;
+    default: throw Error(3, "add with an unsupported number of sources");
+  }
   RTCC_CUDA(cudaGetLastError());
 }
 void launch_gemm_f64(const double* A, const double* B, double* C, long long M, long long N, long long Kpad,
