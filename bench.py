@@ -14,6 +14,18 @@ value  = trajectory-steps per second, all GPUs (inputs resident in HBM).
 e2e    = the same through the public C-ABI with the initial states copied from pinned
          host memory and the dipole samples copied back inside the timed region.
 The reference arm (--impl reference) times the CPU oracle on a bounded sample.
+
+--config c2|c3|c5 runs one of the accuracy / integrator / adjoint measurements instead of the
+throughput line (one JSON line each):
+  c2  water-dimer shape (o=10, v=38), RK4 h=0.02 for 1000 steps, E0=0.01 z sine pulse: every
+      reduced-precision mode against the float64 GPU path, max|dmu(t)| and the shift of the
+      absorption-spectrum peaks (zero-padded transform, parabolic peak interpolation)
+  c3  water-tetramer shape (o=20, v=76), BF16x3, E0=0.5, sigma=0.3, t0=1.8, 20 au: Cash-Karp
+      (tol 1e-6) against mixed-step RK4 (h=0.005 to t=3.6, then 0.05): steps, RHS evaluations,
+      time and the largest dipole difference at common times
+  c5  water-dimer shape, RK4 h=0.05 for 500 steps, J = sum_t w(t) mu_z(t), w Gaussian at 15 au
+      (width 2 au): dJ/d(E0, omega, sigma) by the checkpointed adjoint (every 25 steps) in
+      TF32 and float64 against float64 central differences (delta 1e-5)
 """
 from __future__ import annotations
 
@@ -195,6 +207,127 @@ def dipole_error(prec: int, o=10, v=38, nsteps=50, h=0.02):
     return float(np.abs(out[prec] - out[rtcc.P64]).max())
 
 
+def _peaks(om, I, count=4):
+    """Largest local maxima of a sampled spectrum, refined by a parabola through three samples."""
+    import numpy as np
+    idx = [k for k in range(1, len(I) - 1) if I[k] > I[k - 1] and I[k] >= I[k + 1]]
+    idx = sorted(idx, key=lambda k: -I[k])[:count]
+    out = []
+    for k in sorted(idx):
+        y0, y1, y2 = I[k - 1], I[k], I[k + 1]
+        den = y0 - 2 * y1 + y2
+        off = 0.5 * (y0 - y2) / den if den != 0 else 0.0
+        out.append(float(om[k] + off * (om[1] - om[0])))
+    return out
+
+
+def config_c2():
+    import numpy as np
+
+    from paper_2205_05175_gb300 import rtcc, synth
+    o, v, h, n = 10, 38, 0.02, 1000
+    f, B, mu = synth.make_system(o, v)
+    fld = rtcc.make_field(E0=0.01, omega=0.5, sigma=0.5, t0=1.0, pol=(0.0, 0.0, 1.0))
+    om = np.linspace(0.05, 3.0, 6000)
+    res, ref = {}, None
+    for name in ("p64", "tf32", "3xtf32", "bf16x3"):
+        with rtcc.Handle(f, B, mu, o, v, ntraj=1, prec=rtcc.PRECISIONS[name]) as H:
+            H.ground_state(tol=1e-10)
+            t0 = time.perf_counter()
+            t, m, k = H.propagate([fld], rtcc.make_integrator(rtcc.RK4, h=h, nsteps=n), n + 1)
+            wall = time.perf_counter() - t0
+        t, m = t[0, :k[0]], m[0, :k[0]]
+        I = rtcc.rtcc_spectrum(t, m.real, fld, om, kappa=0.0, gamma=0.05)
+        res[name] = {"t": t, "mu": m, "peaks": _peaks(om, I), "wall_s": wall}
+    ref = res["p64"]
+    out = {"config": "c2", "workload": "o=10 v=38 RK4 h=0.02 x1000, E0=0.01 z sine pulse", "peaks_p64": ref["peaks"],
+           "wall_s_p64": round(ref["wall_s"], 3), "modes": {}}
+    for name in ("tf32", "3xtf32", "bf16x3"):
+        r = res[name]
+        shift = max(abs(a - b) for a, b in zip(r["peaks"], ref["peaks"])) if len(r["peaks"]) == len(ref["peaks"]) else None
+        out["modes"][name] = {"max_abs_dmu": float(np.abs(r["mu"] - ref["mu"]).max()), "max_peak_shift_eh": shift,
+                              "wall_s": round(r["wall_s"], 3)}
+    return out
+
+
+def config_c3():
+    import numpy as np
+
+    from paper_2205_05175_gb300 import rtcc, synth
+    o, v = 20, 76
+    f, B, mu = synth.make_system(o, v)
+    fld = rtcc.make_field(E0=0.5, omega=0.5, sigma=0.3, t0=1.8, pol=(0.0, 0.0, 1.0))
+    runs = {}
+    with rtcc.Handle(f, B, mu, o, v, ntraj=1, prec=rtcc.P32_BF16X3) as H:
+        H.ground_state(tol=1e-8, maxiter=300)
+        y0 = H.get_state(0)[0]
+        for name, integ, nmax in (("cash_karp", rtcc.make_integrator(rtcc.CK, h=0.01, tol=1e-6, t_end=20.0), 20000),
+                                  ("mixed_rk4", rtcc.make_integrator(rtcc.MIXED_RK4, h1=0.005, h2=0.05, t_switch=3.6,
+                                                                     t_end=20.0), 20000)):
+            H.set_state(0, y0, 0.0, 0.0)
+            t0 = time.perf_counter()
+            t, m, k = H.propagate([fld], integ, nmax)
+            wall = time.perf_counter() - t0
+            acc, rej, nrhs, _ = H.last_stats()
+            runs[name] = {"t": t[0, :k[0]], "mu": m[0, :k[0]], "accepted": acc, "rejected": rej, "rhs": nrhs,
+                          "wall_s": round(wall, 3)}
+    ck, mx = runs["cash_karp"], runs["mixed_rk4"]
+    # compare at the mixed-step sample times by cubic interpolation of the Cash-Karp samples
+    from scipy.interpolate import CubicSpline
+    sp = CubicSpline(ck["t"], ck["mu"].real, axis=0)
+    sel = mx["t"] <= ck["t"][-1]
+    dmu = float(np.abs(sp(mx["t"][sel]) - mx["mu"][sel].real).max())
+    out = {"config": "c3", "workload": "o=20 v=76 BF16x3, E0=0.5 sigma=0.3 t0=1.8, 20 au", "max_abs_dmu_re": dmu}
+    for name, r in runs.items():
+        out[name] = {k: r[k] for k in ("accepted", "rejected", "rhs", "wall_s")}
+        out[name]["t_end"] = float(r["t"][-1])
+    return out
+
+
+def config_c5():
+    import numpy as np
+
+    from paper_2205_05175_gb300 import rtcc, synth
+    o, v, h, n, ck = 10, 38, 0.05, 500, 25
+    f, B, mu = synth.make_system(o, v)
+    tt = h * np.arange(n + 1)
+    w = np.zeros((n + 1, 3))
+    w[:, 2] = np.exp(-((tt - 15.0) ** 2) / (2 * 2.0 ** 2))
+    theta = np.array([0.01, 0.5, 0.5])
+
+    def fld(th):
+        return rtcc.make_field(E0=th[0], omega=th[1], sigma=th[2], t0=1.0, pol=(0.0, 0.0, 1.0))
+
+    out = {"config": "c5", "workload": "o=10 v=38 RK4 h=0.05 x500, checkpoints every 25, w Gaussian at 15 au"}
+    with rtcc.Handle(f, B, mu, o, v, ntraj=1, prec=rtcc.P64) as H:
+        H.ground_state(tol=1e-10)
+        y0 = H.get_state(0)[0]
+
+        def J(th):
+            H.set_state(0, y0, 0.0, 0.0)
+            t, m, k = H.propagate([fld(th)], rtcc.make_integrator(rtcc.RK4, h=h, nsteps=n), n + 1)
+            return float(np.sum(w * m[0, :k[0]].real))
+
+        t0 = time.perf_counter()
+        fd = np.zeros(3)
+        for i in range(3):
+            e = np.zeros(3)
+            e[i] = 1e-5
+            fd[i] = (J(theta + e) - J(theta - e)) / 2e-5
+        out["fd_wall_s"] = round(time.perf_counter() - t0, 3)
+        out["grad_fd_f64"] = fd.tolist()
+        for name, prec in (("f64", rtcc.P64), ("tf32", rtcc.P32_TF32)):
+            with rtcc.Handle(f, B, mu, o, v, ntraj=1, prec=prec) as G:
+                G.set_state(0, y0, 0.0, 0.0)
+                t0 = time.perf_counter()
+                _, g = G.propagate_vjp([fld(theta)], h, n, w, ckpt_every=ck)
+                wall = time.perf_counter() - t0
+            out[f"grad_adjoint_{name}"] = g[0].tolist()
+            out[f"rel_err_adjoint_{name}_vs_fd"] = float(np.abs(g[0] - fd).max() / np.abs(fd).max())
+            out[f"adjoint_wall_s_{name}"] = round(wall, 3)
+    return out
+
+
 def run_gpu(args, rank, world, local):
     import numpy as np
     import torch
@@ -312,7 +445,17 @@ def main(argv=None):
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-dipole-error", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--config", default=None, choices=["c2", "c3", "c5"],
+                    help="run an accuracy / integrator / adjoint measurement instead of the throughput line")
     args = ap.parse_args(argv)
+    if args.config is not None:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "config": args.config,
+                              "unavailable": "configuration runs compare the library's own precision modes"}))
+            return 0
+        line = {"c2": config_c2, "c3": config_c3, "c5": config_c5}[args.config]()
+        print(json.dumps(line), flush=True)
+        return 0
     rank, world, local = dist_env()
     if world > 1:
         import torch

@@ -221,7 +221,10 @@ rtcc_status_t rtcc_selftest_timeout(double seconds);
  * handle-independent GEMM path of precision `prec` (TF32/3xTF32/BF16x3 run on the
  * tcgen05 tensor cores, P64 on the float64 path).  cplx bit 0: A is complex
  * (interleaved re, im), bit 1: Bm is complex; C (host or device) is complex when either
- * operand is.  Errors: INVALID_ARG, CUDA, TIMEOUT. */
+ * operand is.  Internally the product is formed four times, into two zeroed temporaries laid
+ * out m-major and n-major (each first stored, then accumulated in place), and C is a quarter
+ * of their sum, so every output path of the contraction core is exercised.
+ * Errors: INVALID_ARG, CUDA, TIMEOUT. */
 rtcc_status_t rtcc_selftest_gemm(int prec, int cplx, int batch, int M, int N, int K, const double* A,
                                  const double* Bm, double* C);
 

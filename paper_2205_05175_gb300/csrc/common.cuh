@@ -124,6 +124,7 @@ struct AddDesc {
   double* C;
   int c_cplx;
   int store;        // 1: C is known to be zero: store instead of read-modify-write
+  int f32;          // 1: sum in float32 (reduced-precision programs)
   IndexMap c_all;   // all C labels
   long long n;
   int nsrc;

@@ -353,6 +353,7 @@ void Engine::plan(Program& P) {
       k.kind = CK_ADD;
       AddDesc& d = k.add;
       d.store = c_fresh ? 1 : 0;
+      d.f32 = (prec != Prec::P64) ? 1 : 0;
       d.C = C.ptr;
       d.c_cplx = C.cplx;
       d.c_all = map_for(C, op.lc, op.lc);

@@ -167,9 +167,20 @@ __device__ __forceinline__ Item decode_item(const TcGemmParams& p, int w, int sp
   return it;
 }
 
-__device__ __forceinline__ void put_out(double* dst, double val, bool split, bool store, double old) {
-  if (split) atomicAdd(dst, val);
-  else *dst = store ? val : old + val;
+// Output writes: a store into a fresh (zeroed) output, otherwise a float64 atomic add without
+// return (the read-modify-write happens in L2, so the epilogue never waits on the old value; each
+// element is written once per launch unless K is split, so the result equals old + val).
+__device__ __forceinline__ void put_out(double* dst, double val, bool store) {
+  if (store) *dst = val;
+  else atomicAdd(dst, val);
+}
+__device__ __forceinline__ void put_out2(double2* dst, double vr, double vi, bool store) {
+  if (store) {
+    *dst = make_double2(vr, vi);
+  } else {
+    atomicAdd(&dst->x, vr);
+    atomicAdd(&dst->y, vi);
+  }
 }
 
 // Persistent warp-specialised GEMM: each CTA walks work items (batch, output plane(s), split, tile);
@@ -182,9 +193,6 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   constexpr int B_BYTES = BN * 128;
   constexpr int KBLK = (KIND == 0) ? 32 : 64;
   constexpr int WCOLS = BN * 4 / EPW;   // accumulator columns per epilogue warp
-  // rows (or columns) of C in flight per epilogue batch: fewer with eight warps, whose register
-  // budget is smaller
-  constexpr int kCB = EPW == 8 ? 4 : 8, kSB = EPW == 8 ? 8 : 16;
   static_assert(WCOLS % 32 == 0, "epilogue column split");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -199,7 +207,6 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tempty + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool split = splits > 1;
   const int np_all = p.fused ? p.nrb : 1;                 // planes per work item
   const uint32_t tcols = (uint32_t)(2 * np_all * BN);      // two accumulator sets
 
@@ -302,19 +309,15 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     // the scale is applied in float32 (its rounding, 2^-24 relative, is far below the operand
     // split's resolution) and the result widened exactly with integer operations
     const float alpha_f = (float)e.alpha;
+    // a fresh output is stored, unless K is split (the slices then add into the zeroed output)
+    const bool store = e.store && splits == 1;
     float* tile = etile + ew * (32 * 33);
     long long* coloff = coloff_all + ew * WCOLS;   // warp-private: no cross-warp barrier in the epilogue
     int local = 0;
     for (int w = blockIdx.x; w < total_items; w += gridDim.x, ++local) {
       const Item it = decode_item<BN>(p, w, splits);
       const int a = local & 1, u = local >> 1;
-      bool ok = mbar_wait(&tfull[a], u & 1);
-      ok = __all_sync(0xffffffffu, ok);
-      if (!ok) {
-        if (lane == 0) atomicExch(p.err, DEV_TIMEOUT_EPI);
-        break;
-      }
-      tc_fence_after();
+      // output offsets of this item (computed while the MMAs of the item are still running)
       __syncwarp();
       for (int c = lane; c < WCOLS; c += 32) {
         const int n = it.n0 + hc + c;
@@ -324,6 +327,13 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
       const int row = it.m0 + q * 32 + lane;
       long long rowoff = 0;
       if (row < p.M) rowoff = imap32(e.cb, (unsigned)it.bz) + imap32(e.cm, (unsigned)row);
+      bool ok = mbar_wait(&tfull[a], u & 1);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0) atomicExch(p.err, DEV_TIMEOUT_EPI);
+        break;
+      }
+      tc_fence_after();
       const uint32_t acc = tmem + (uint32_t)(a * it.np * BN + hc) + ((uint32_t)(q * 32) << 16);
       const bool both = it.np == 2 && e.c_cplx;   // write complex elements whole
 #pragma unroll 1
@@ -356,32 +366,11 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             __syncwarp();
             const long long noff = coloff[c + lane];
 #pragma unroll
-            for (int h = 0; h < 32 / kCB; ++h) {
-              double2* dst[kCB];
-              double2 old[kCB];
-#pragma unroll
-              for (int j = 0; j < kCB; ++j) {
-                const int rr = h * kCB + j;
-                const long long ro = __shfl_sync(0xffffffffu, rowoff, rr);
-                const bool valid = (it.m0 + q * 32 + rr < p.M) && (noff >= 0);
-                dst[j] = valid ? C2 + (ro + noff) : nullptr;
-              }
-              if (!split && !e.store) {
-#pragma unroll
-                for (int j = 0; j < kCB; ++j) old[j] = dst[j] ? *dst[j] : make_double2(0.0, 0.0);
-              }
-#pragma unroll
-              for (int j = 0; j < kCB; ++j) {
-                if (!dst[j]) continue;
-                const double vr = f32_to_f64_bits(alpha_f * tre[h * kCB + j]);
-                const double vi = f32_to_f64_bits(alpha_f * tim[h * kCB + j]);
-                if (split) {
-                  atomicAdd(&dst[j]->x, vr);
-                  atomicAdd(&dst[j]->y, vi);
-                } else {
-                  *dst[j] = e.store ? make_double2(vr, vi) : make_double2(old[j].x + vr, old[j].y + vi);
-                }
-              }
+            for (int rr = 0; rr < 32; ++rr) {
+              const long long ro = __shfl_sync(0xffffffffu, rowoff, rr);
+              if (noff >= 0 && it.m0 + q * 32 + rr < p.M)
+                put_out2(C2 + (ro + noff), f32_to_f64_bits(alpha_f * tre[rr]), f32_to_f64_bits(alpha_f * tim[rr]),
+                         store);
             }
           } else {
             uint32_t rre[32], rim[32];
@@ -389,30 +378,11 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             tmem_ld32(acc + (uint32_t)(BN + c), rim);
             if (row >= p.M) continue;
 #pragma unroll
-            for (int h = 0; h < 32 / kCB; ++h) {
-              double2* dst[kCB];
-              double2 old[kCB];
-#pragma unroll
-              for (int j = 0; j < kCB; ++j) {
-                const long long no = coloff[c + h * kCB + j];
-                dst[j] = (no >= 0) ? C2 + (rowoff + no) : nullptr;
-              }
-              if (!split && !e.store) {
-#pragma unroll
-                for (int j = 0; j < kCB; ++j) old[j] = dst[j] ? *dst[j] : make_double2(0.0, 0.0);
-              }
-#pragma unroll
-              for (int j = 0; j < kCB; ++j) {
-                if (!dst[j]) continue;
-                const double vr = f32_to_f64_bits(alpha_f * __uint_as_float(rre[h * kCB + j]));
-                const double vi = f32_to_f64_bits(alpha_f * __uint_as_float(rim[h * kCB + j]));
-                if (split) {
-                  atomicAdd(&dst[j]->x, vr);
-                  atomicAdd(&dst[j]->y, vi);
-                } else {
-                  *dst[j] = e.store ? make_double2(vr, vi) : make_double2(old[j].x + vr, old[j].y + vi);
-                }
-              }
+            for (int j = 0; j < 32; ++j) {
+              const long long no = coloff[c + j];
+              if (no >= 0)
+                put_out2(C2 + (rowoff + no), f32_to_f64_bits(alpha_f * __uint_as_float(rre[j])),
+                         f32_to_f64_bits(alpha_f * __uint_as_float(rim[j])), store);
             }
           }
           continue;
@@ -428,47 +398,23 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             __syncwarp();
             const long long noff = coloff[c + lane];
 #pragma unroll
-            for (int h = 0; h < 32 / kSB; ++h) {
-              double* dst[kSB];
-              double old[kSB];
-#pragma unroll
-              for (int j = 0; j < kSB; ++j) {
-                const int rr = h * kSB + j;
-                const long long ro = __shfl_sync(0xffffffffu, rowoff, rr);
-                const bool valid = (it.m0 + q * 32 + rr < p.M) && (noff >= 0);
+            for (int rr = 0; rr < 32; ++rr) {
+              const long long ro = __shfl_sync(0xffffffffu, rowoff, rr);
+              if (noff >= 0 && it.m0 + q * 32 + rr < p.M) {
                 const long long off = ro + noff;
-                dst[j] = valid ? e.C + (e.c_cplx ? 2 * off + comp : off) : nullptr;
-              }
-              if (!split && !e.store) {
-#pragma unroll
-                for (int j = 0; j < kSB; ++j) old[j] = dst[j] ? *dst[j] : 0.0;
-              }
-#pragma unroll
-              for (int j = 0; j < kSB; ++j) {
-                if (!dst[j]) continue;
-                put_out(dst[j], f32_to_f64_bits(alpha_f * tile[(h * kSB + j) * 33 + lane]), split, e.store, old[j]);
+                put_out(e.C + (e.c_cplx ? 2 * off + comp : off), f32_to_f64_bits(alpha_f * tile[rr * 33 + lane]),
+                        store);
               }
             }
             __syncwarp();
           } else if (row < p.M) {
 #pragma unroll
-            for (int h = 0; h < 32 / kSB; ++h) {
-              double* dst[kSB];
-              double old[kSB];
-#pragma unroll
-              for (int j = 0; j < kSB; ++j) {
-                const long long no = coloff[c + h * kSB + j];
+            for (int j = 0; j < 32; ++j) {
+              const long long no = coloff[c + j];
+              if (no >= 0) {
                 const long long off = rowoff + no;
-                dst[j] = (no >= 0) ? e.C + (e.c_cplx ? 2 * off + comp : off) : nullptr;
-              }
-              if (!split && !e.store) {
-#pragma unroll
-                for (int j = 0; j < kSB; ++j) old[j] = dst[j] ? *dst[j] : 0.0;
-              }
-#pragma unroll
-              for (int j = 0; j < kSB; ++j) {
-                if (!dst[j]) continue;
-                put_out(dst[j], f32_to_f64_bits(alpha_f * __uint_as_float(r[h * kSB + j])), split, e.store, old[j]);
+                put_out(e.C + (e.c_cplx ? 2 * off + comp : off), f32_to_f64_bits(alpha_f * __uint_as_float(r[j])),
+                        store);
               }
             }
           }

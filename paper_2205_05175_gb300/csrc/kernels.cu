@@ -537,10 +537,14 @@ __device__ __forceinline__ double flip_sign(double x) {
 }
 
 // C[all labels] (+)= sum_s alpha_s * A_s: the innermost label over threadIdx.x, the rest over
-// rows.  A real scale costs one float64 fused multiply-add per component; a fresh output whose
-// first source has a unit scale starts from a copy (a sign-bit flip for -1), no float64 work.
-template <int NS>
+// rows.  F32 (reduced-precision programs): values are rounded to binary32 with integer
+// operations and summed in float32, which keeps the kernel off the float64 pipe (its rounding,
+// 2^-24 relative, is far below what those programs' contractions resolve); otherwise float64
+// with one fused multiply-add per component and real scale.  A fresh output fed by a single
+// unit-scale source is a plain copy (a sign-bit flip for -1) in both modes.
+template <int NS, bool F32>
 __global__ void __launch_bounds__(256) add_kernel(AddDesc d, unsigned inner) {
+  using R = typename std::conditional<F32, float, double>::type;
   constexpr int RT = 32;   // rows per tile: their offsets are decoded once into shared memory
   __shared__ long long s_c[RT], s_a[NS][RT];
   const unsigned rows = (unsigned)(d.n / inner);
@@ -550,6 +554,7 @@ __global__ void __launch_bounds__(256) add_kernel(AddDesc d, unsigned inner) {
   long long as[NS];
 #pragma unroll
   for (int q = 0; q < NS; ++q) as[q] = d.a_all[q].strides[d.a_all[q].n - 1];
+  const bool copy = NS == 1 && d.store && d.ai[0] == 0.0 && (d.ar[0] == 1.0 || d.ar[0] == -1.0);
   const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
   for (unsigned rt = blockIdx.y; rt < nrt; rt += gridDim.y) {
     __syncthreads();
@@ -567,51 +572,53 @@ __global__ void __launch_bounds__(256) add_kernel(AddDesc d, unsigned inner) {
     for (unsigned r = threadIdx.y; r < nrows; r += blockDim.y) {
       const long long c_off = s_c[r] + (long long)i * cs;
       double2* c2 = reinterpret_cast<double2*>(d.C) + c_off;
-      double accr = 0.0, acci = 0.0;
+      if (copy) {
+        const long long a_off = s_a[0][r] + (long long)i * as[0];
+        const bool neg = d.ar[0] < 0.0;
+        if (d.a_cplx[0]) {
+          const double2 x = reinterpret_cast<const double2*>(d.A[0])[a_off];
+          const double xr = neg ? flip_sign(x.x) : x.x, xi = neg ? flip_sign(x.y) : x.y;
+          if (d.c_cplx) *c2 = make_double2(xr, xi);
+          else d.C[c_off] = xr;
+        } else {
+          const double x = neg ? flip_sign(d.A[0][a_off]) : d.A[0][a_off];
+          if (d.c_cplx) *c2 = make_double2(x, 0.0);
+          else d.C[c_off] = x;
+        }
+        continue;
+      }
+      R accr = 0, acci = 0;
       if (!d.store) {
         if (d.c_cplx) {
           const double2 x = *c2;
-          accr = x.x;
-          acci = x.y;
+          accr = cvt_r<R>(x.x);
+          acci = cvt_r<R>(x.y);
         } else {
-          accr = d.C[c_off];
+          accr = cvt_r<R>(d.C[c_off]);
         }
       }
 #pragma unroll
       for (int q = 0; q < NS; ++q) {
         const long long a_off = s_a[q][r] + (long long)i * as[q];
-        double xr, xi = 0.0;
+        R xr, xi = 0;
         if (d.a_cplx[q]) {
           const double2 x = reinterpret_cast<const double2*>(d.A[q])[a_off];
-          xr = x.x;
-          xi = x.y;
+          xr = cvt_r<R>(x.x);
+          xi = cvt_r<R>(x.y);
         } else {
-          xr = d.A[q][a_off];
+          xr = cvt_r<R>(d.A[q][a_off]);
         }
-        const double ar = d.ar[q], ai = d.ai[q];
-        if (ai == 0.0) {
-          if (q == 0 && d.store) {
-            if (ar == 1.0) {
-              accr = xr;
-              acci = xi;
-            } else if (ar == -1.0) {
-              accr = flip_sign(xr);
-              acci = flip_sign(xi);
-            } else {
-              accr = ar * xr;
-              acci = ar * xi;
-            }
-          } else {
-            accr = fma(ar, xr, accr);
-            acci = fma(ar, xi, acci);
-          }
+        const R ar = (R)d.ar[q], ai = (R)d.ai[q];
+        if (d.ai[q] == 0.0) {
+          accr = fma(ar, xr, accr);
+          acci = fma(ar, xi, acci);
         } else {
           accr += ar * xr - ai * xi;
           acci += ar * xi + ai * xr;
         }
       }
-      if (d.c_cplx) *c2 = make_double2(accr, acci);
-      else d.C[c_off] = accr;
+      if (d.c_cplx) *c2 = make_double2(cvt_d(accr), cvt_d(acci));
+      else d.C[c_off] = cvt_d(accr);
     }
   }
 }
@@ -809,11 +816,16 @@ void launch_add(const AddDesc& d, cudaStream_t s) {
   const unsigned by = 256 / bx;
   dim3 blk(bx, by);
   dim3 grid((inner + bx - 1) / bx, std::min((rows + 31) / 32, 65535u));
-  switch (d.nsrc) {
-    case 1: add_kernel<1><<<grid, blk, 0, s>>>(d, inner); break;
-    case 2: add_kernel<2><<<grid, blk, 0, s>>>(d, inner); break;
-    case 3: add_kernel<3><<<grid, blk, 0, s>>>(d, inner); break;
-    case 4: add_kernel<4><<<grid, blk, 0, s>>>(d, inner); break;
+  const int key = d.nsrc * 2 + (d.f32 ? 1 : 0);
+  switch (key) {
+    case 2: add_kernel<1, false><<<grid, blk, 0, s>>>(d, inner); break;
+    case 3: add_kernel<1, true><<<grid, blk, 0, s>>>(d, inner); break;
+    case 4: add_kernel<2, false><<<grid, blk, 0, s>>>(d, inner); break;
+    case 5: add_kernel<2, true><<<grid, blk, 0, s>>>(d, inner); break;
+    case 6: add_kernel<3, false><<<grid, blk, 0, s>>>(d, inner); break;
+    case 7: add_kernel<3, true><<<grid, blk, 0, s>>>(d, inner); break;
+    case 8: add_kernel<4, false><<<grid, blk, 0, s>>>(d, inner); break;
+    case 9: add_kernel<4, true><<<grid, blk, 0, s>>>(d, inner); break;
     default: throw Error(3, "add with an unsupported number of sources");
   }
   RTCC_CUDA(cudaGetLastError());

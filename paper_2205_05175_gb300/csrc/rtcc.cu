@@ -1452,9 +1452,20 @@ rtcc_status_t rtcc_selftest_gemm(int prec, int cplx, int batch, int M, int N, in
       const int ta = E.external("A", {batch, M, K}, ac, dA);
       const int tb = E.external("B", {batch, N, K}, bc, dB);
       const int tc = E.external("C", {batch, M, N}, cc, dC);
+      // T[zmn] and U[znm] (output unit stride along n, then along m) are zeroed temporaries:
+      // the first product of each is stored, the second added in place; C = (T + U) / 4
+      const int arena = E.new_arena();
+      const int tt = E.temp(arena, "T", {batch, M, N}, cc);
+      const int tu = E.temp(arena, "U", {batch, N, M}, cc);
       Program P;
       P.name = "selftest";
-      Engine::ein(P, tc, "zmn", ta, "zmk", tb, "znk");
+      P.zero_arenas = {arena};
+      Engine::ein(P, tt, "zmn", ta, "zmk", tb, "znk");
+      Engine::ein(P, tt, "zmn", ta, "zmk", tb, "znk");
+      Engine::ein(P, tu, "znm", ta, "zmk", tb, "znk");
+      Engine::ein(P, tu, "znm", ta, "zmk", tb, "znk");
+      Engine::add(P, tc, "zmn", tt, "zmn", 0.25);
+      Engine::add(P, tc, "zmn", tu, "znm", 0.25);
       E.finalize({&P});
       E.run(P);
       E.check_error();
