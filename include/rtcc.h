@@ -110,6 +110,18 @@ typedef struct rtcc_ctx* rtcc_handle_t;
 rtcc_status_t rtcc_create(const double* f, const double* B, int naux, const double* mu,
                           int o, int v, int ntraj, int prec, rtcc_handle_t* out);
 
+/* Create a handle with a frozen core (the paper's water runs freeze the O 1s orbitals, Sec. 3).
+ * Same inputs as rtcc_create over all nmo = o + v orbitals; the lowest nfc occupied orbitals
+ * (0 <= nfc < o) stay doubly occupied and are not correlated.  The handle then works in the
+ * active space: o - nfc occupied and v virtual orbitals (the state layout, rtcc_state_size and
+ * every amplitude index refer to the active orbitals only), with the active blocks of f (which
+ * already carries the core's mean field), of B and of mu.  Every dipole the handle reports
+ * includes the core's constant contribution 2 sum_c mu_x[c][c].  nfc = 0 is rtcc_create.
+ * Errors: as rtcc_create; INVALID_ARG for nfc outside [0, o). */
+rtcc_status_t rtcc_create_frozen_core(const double* f, const double* B, int naux, const double* mu,
+                                      int o, int v, int nfc, int ntraj, int prec,
+                                      rtcc_handle_t* out);
+
 /* Free every device resource of the handle.  Null is accepted. */
 rtcc_status_t rtcc_destroy(rtcc_handle_t h);
 

@@ -69,8 +69,9 @@ enum PackElem : int { PE_F32 = 0, PE_BF16 = 1, PE_F64 = 2 };
 enum SplitPart : int { SP_FULL = 0, SP_HI = 1, SP_LO = 2 };
 constexpr int kMaxRb = 4;
 struct PackDesc {
-  const double* src;
+  const void* src;
   int src_cplx;
+  int src_f32;      // source elements are float32 (complex64) instead of float64
   IndexMap rows;    // R labels
   IndexMap cols;    // K labels
   IndexMap bat;     // batch labels
@@ -108,8 +109,9 @@ struct UnpackDesc {
 
 // Direct (small) contraction C[bt,m,n] += alpha * sum_k A[bt,m,k] B[bt,n,k] in float64.
 struct DirectDesc {
-  const double* A; const double* B; double* C;
+  const void* A; const void* B; void* C;
   int a_cplx, b_cplx, c_cplx;
+  int a_f32, b_f32, c_f32;   // float32 (complex64) elements
   IndexMap am, ak, ab, bn, bk, bb, cm, cn, cb;
   long long M, N, K, NB;
   double ar, ai;
@@ -121,15 +123,17 @@ struct DirectDesc {
 // rest); several sources when consecutive adds into one output are merged.
 constexpr int kMaxAddSrc = 4;
 struct AddDesc {
-  double* C;
+  void* C;
   int c_cplx;
+  int c_f32;
   int store;        // 1: C is known to be zero: store instead of read-modify-write
   int f32;          // 1: sum in float32 (reduced-precision programs)
   IndexMap c_all;   // all C labels
   long long n;
   int nsrc;
-  const double* A[kMaxAddSrc];
+  const void* A[kMaxAddSrc];
   int a_cplx[kMaxAddSrc];
+  int a_f32[kMaxAddSrc];
   IndexMap a_all[kMaxAddSrc];   // C's labels, source s's strides (0 where the source lacks the label)
   double ar[kMaxAddSrc], ai[kMaxAddSrc];
 };
@@ -152,8 +156,9 @@ struct TcSeg {
   int pa, pb, neg;
 };
 struct TcEpilogue {
-  double* C;
+  void* C;
   int c_cplx;
+  int c_f32;           // float32 (complex64) output elements
   double alpha;
   IndexMap cm, cn, cb;
   int flat_n;          // 1: C offset of column n is rowoff + n * sn

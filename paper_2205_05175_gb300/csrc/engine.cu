@@ -260,9 +260,12 @@ int Engine::temp(int arena, const std::string& name, const std::vector<int>& dim
   t.strides = contiguous_strides(dims);
   t.cplx = cplx;
   t.storage = ST_ARENA;
+  // temporaries of reduced-precision engines hold float32 (complex64) elements: their
+  // contractions resolve far less than float32 does, and every pass over them moves half the bytes
+  t.f32 = (prec_ != Prec::P64);
   t.arena = arena;
   t.arena_off = arena_size_[arena];
-  const long long nd = t.numel() * (cplx ? 2 : 1);
+  const long long nd = ((long long)(t.numel() * t.esz()) + 7) / 8;   // in doubles
   arena_size_[arena] += round_up(nd, 32);   // 256-byte alignment of every temporary
   tensors_.push_back(t);
   return (int)tensors_.size() - 1;
@@ -319,11 +322,10 @@ void Engine::plan(Program& P) {
   // (tracked by arena extent, so temporaries that share reused arena space are never fresh twice)
   std::vector<std::array<long long, 3>> written;   // arena, first double, one past the last
   const std::set<int> zeroed(P.zero_arenas.begin(), P.zero_arenas.end());
-  auto extent = [&](const Tensor& t) {
+  auto extent = [&](const Tensor& t) {   // arena, first byte, one past the last byte
     long long hi = 1;
     for (size_t i = 0; i < t.dims.size(); ++i) hi += (long long)(t.dims[i] - 1) * t.strides[i];
-    const long long w = t.cplx ? 2 : 1;
-    return std::array<long long, 3>{t.arena, t.arena_off, t.arena_off + hi * w};
+    return std::array<long long, 3>{t.arena, t.arena_off * 8, t.arena_off * 8 + hi * (long long)t.esz()};
   };
   auto fresh = [&](int id) {
     const Tensor& t = tensors_[id];
@@ -356,6 +358,7 @@ void Engine::plan(Program& P) {
       d.f32 = (prec != Prec::P64) ? 1 : 0;
       d.C = C.ptr;
       d.c_cplx = C.cplx;
+      d.c_f32 = C.f32;
       d.c_all = map_for(C, op.lc, op.lc);
       d.n = prod_dims(d.c_all);
       d.nsrc = 0;
@@ -412,6 +415,9 @@ void Engine::plan(Program& P) {
     d.A = A.ptr;
     d.B = B.ptr;
     d.C = C.ptr;
+    d.a_f32 = A.f32;
+    d.b_f32 = B.f32;
+    d.c_f32 = C.f32;
     d.a_cplx = A.cplx;
     d.b_cplx = B.cplx;
     d.c_cplx = C.cplx;
@@ -462,6 +468,7 @@ void Engine::plan(Program& P) {
         pd = PackDesc{};
         pd.src = T.ptr;
         pd.src_cplx = T.cplx;
+        pd.src_f32 = T.f32;
         pd.rows = rows;
         pd.cols = cols;
         pd.bat = bat;
@@ -520,6 +527,7 @@ void Engine::plan(Program& P) {
       RTCC_REQUIRE(op.alpha.imag() == 0.0, "tensor-core contractions take a real scale factor");
       TcEpilogue& ep = g.epi;
       ep.c_cplx = C.cplx;
+      ep.c_f32 = C.f32;
       ep.alpha = op.alpha.real();
       ep.cm = d.cm;
       ep.cn = d.cn;
@@ -683,6 +691,7 @@ bool Engine::add_source(Compiled& k, const std::vector<Op>& ops, int oi, const s
     }
   }
   d.A[q] = A.ptr;
+  d.a_f32[q] = A.f32;
   d.ar[q] = op.alpha.real();
   d.ai[q] = op.alpha.imag();
   d.nsrc = q + 1;
@@ -712,7 +721,7 @@ void Engine::merge_adds(Program& P) {
       long long hi = 1;
       for (size_t q = 0; q < t.dims.size(); ++q) hi += (long long)(t.dims[q] - 1) * std::llabs(t.strides[q]);
       const char* b = reinterpret_cast<const char*>(t.ptr);
-      return std::make_pair(b, b + hi * (t.cplx ? 16 : 8));
+      return std::make_pair(b, b + hi * (long long)t.esz());
     };
     bool indep = true;
     for (int w : wr)
@@ -813,7 +822,7 @@ void Engine::run(const Program& P) {
     RTCC_CUDA(cudaMemsetAsync(arena_ptr_[a], 0, (size_t)std::max(1ll, arena_size_[a]) * 8, stream_));
   for (int t : P.zero_tensors) {
     const Tensor& x = tensors_[t];
-    RTCC_CUDA(cudaMemsetAsync(x.ptr, 0, (size_t)x.numel() * (x.cplx ? 16 : 8), stream_));
+    RTCC_CUDA(cudaMemsetAsync(x.ptr, 0, (size_t)x.numel() * x.esz(), stream_));
   }
   for (const auto& z : P.zero2d) RTCC_CUDA(cudaMemset2DAsync(z.ptr, z.pitch, 0, z.width, z.height, stream_));
   Profiler dummy;
@@ -833,10 +842,11 @@ void Engine::run(const Program& P) {
         break;
       case CK_ADD: {
         double abytes = 0.0;
-        for (int q = 0; q < k.add.nsrc; ++q) abytes += k.add.a_cplx[q] ? 16 : 8;
+        for (int q = 0; q < k.add.nsrc; ++q) abytes += (k.add.a_cplx[q] ? 2 : 1) * (k.add.a_f32[q] ? 4 : 8);
+        const double cbytes = (k.add.c_cplx ? 2 : 1) * (k.add.c_f32 ? 4 : 8);
         pr.start(stream_);
         launch_add(k.add, stream_);
-        pr.stop(stream_, KC_ADD, 0.0, (double)k.add.n * (abytes + (k.add.store ? 1 : 2) * (k.add.c_cplx ? 16 : 8)), tag);
+        pr.stop(stream_, KC_ADD, 0.0, (double)k.add.n * (abytes + (k.add.store ? 1 : 2) * cbytes), tag);
         break;
       }
       case CK_DIRECT:
@@ -855,20 +865,20 @@ void Engine::run(const Program& P) {
           pr.start(stream_);
           launch_pack(k.pa, stream_);
           pr.stop(stream_, KC_PACK, 0.0,
-                  (double)k.NB * k.pa.R * k.pa.K * (k.pa.src_cplx ? 16 : 8) + (double)k.NB * k.GM * k.Kpad * esz, tag);
+                  (double)k.NB * k.pa.R * k.pa.K * (k.pa.src_cplx ? 2 : 1) * (k.pa.src_f32 ? 4 : 8) + (double)k.NB * k.GM * k.Kpad * esz, tag);
         }
         if (!k.b_const) {
           pr.start(stream_);
           launch_pack(k.pb, stream_);
           pr.stop(stream_, KC_PACK, 0.0,
-                  (double)k.NB * k.pb.R * k.pb.K * (k.pb.src_cplx ? 16 : 8) + (double)k.NB * k.GN * k.Kpad * esz, tag);
+                  (double)k.NB * k.pb.R * k.pb.K * (k.pb.src_cplx ? 2 : 1) * (k.pb.src_f32 ? 4 : 8) + (double)k.NB * k.GN * k.Kpad * esz, tag);
         }
         if (k.tc_kind >= 0) {
           // kernel-level algorithmic flops: real multiply-adds of all segments, without padding
           pr.start(stream_);
           launch_tc_gemm(k.tcp, stream_);
           pr.stop(stream_, KC_TC_GEMM, (double)k.exec_flops,
-                  (double)k.NB * (k.GM + k.GN) * k.Kpad * esz + 2.0 * k.NB * k.pa.R * k.pb.R * (C_cplx_of(k) ? 16 : 8), tag);
+                  (double)k.NB * (k.GM + k.GN) * k.Kpad * esz + 2.0 * k.NB * k.pa.R * k.pb.R * (C_cplx_of(k) ? 2 : 1) * (k.tcp.p.epi.c_f32 ? 4 : 8), tag);
           break;
         }
         const double kflops = 2.0 * k.NB * k.GM * k.GN * (double)(k.pa.nss * k.pa.ncs * k.pa.K);

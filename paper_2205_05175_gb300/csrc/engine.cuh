@@ -23,11 +23,13 @@ struct Tensor {
   std::vector<int> dims;
   std::vector<long long> strides;   // element strides (complex elements for complex tensors)
   bool cplx = true;
+  bool f32 = false;                 // float32 / complex64 elements (temporaries of reduced-precision engines)
   bool constant = false;            // never differentiated; packed once when used in a GEMM
   int storage = ST_EXTERNAL;
   int arena = -1;                   // arena index for ST_ARENA
   long long arena_off = 0;          // offset in doubles
   double* ptr = nullptr;
+  size_t esz() const { return (f32 ? 4u : 8u) * (cplx ? 2u : 1u); }   // bytes per element
   long long numel() const {
     long long n = 1;
     for (int d : dims) n *= d;

@@ -167,19 +167,35 @@ __device__ __forceinline__ Item decode_item(const TcGemmParams& p, int w, int sp
   return it;
 }
 
-// Output writes: a store into a fresh (zeroed) output, otherwise a float64 atomic add without
-// return (the read-modify-write happens in L2, so the epilogue never waits on the old value; each
+// Output writes: a store into a fresh (zeroed) output, otherwise an atomic add without return
+// (the read-modify-write happens in L2, so the epilogue never waits on the old value; each
 // element is written once per launch unless K is split, so the result equals old + val).
-__device__ __forceinline__ void put_out(double* dst, double val, bool store) {
-  if (store) *dst = val;
-  else atomicAdd(dst, val);
-}
-__device__ __forceinline__ void put_out2(double2* dst, double vr, double vi, bool store) {
-  if (store) {
-    *dst = make_double2(vr, vi);
+// Outputs hold float64 (complex128) or float32 (complex64) elements; float64 values are widened
+// exactly from the float32 accumulators with integer operations.
+__device__ __forceinline__ void put_real(void* C, long long i, bool f32, float v, bool store) {
+  if (f32) {
+    float* p = static_cast<float*>(C) + i;
+    if (store) *p = v;
+    else atomicAdd(p, v);
   } else {
-    atomicAdd(&dst->x, vr);
-    atomicAdd(&dst->y, vi);
+    double* p = static_cast<double*>(C) + i;
+    if (store) *p = f32_to_f64_bits(v);
+    else atomicAdd(p, f32_to_f64_bits(v));
+  }
+}
+__device__ __forceinline__ void put_cplx(void* C, long long i, bool f32, float vr, float vi, bool store) {
+  if (f32) {
+    float2* p = static_cast<float2*>(C) + i;
+    if (store) *p = make_float2(vr, vi);
+    else atomicAdd(p, make_float2(vr, vi));
+  } else {
+    double2* p = static_cast<double2*>(C) + i;
+    if (store) {
+      *p = make_double2(f32_to_f64_bits(vr), f32_to_f64_bits(vi));
+    } else {
+      atomicAdd(&p->x, f32_to_f64_bits(vr));
+      atomicAdd(&p->y, f32_to_f64_bits(vi));
+    }
   }
 }
 
@@ -340,7 +356,6 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
       for (int c = 0; c < WCOLS; c += 32) {
         if (it.nvl == 0) continue;   // uniform over the warp
         if (both) {
-          double2* C2 = reinterpret_cast<double2*>(e.C);
           if (e.unit_n) {
             // transpose both planes through the warp's tile: lane then owns column c + lane
             float tre[32], tim[32];
@@ -369,8 +384,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             for (int rr = 0; rr < 32; ++rr) {
               const long long ro = __shfl_sync(0xffffffffu, rowoff, rr);
               if (noff >= 0 && it.m0 + q * 32 + rr < p.M)
-                put_out2(C2 + (ro + noff), f32_to_f64_bits(alpha_f * tre[rr]), f32_to_f64_bits(alpha_f * tim[rr]),
-                         store);
+                put_cplx(e.C, ro + noff, e.c_f32, alpha_f * tre[rr], alpha_f * tim[rr], store);
             }
           } else {
             uint32_t rre[32], rim[32];
@@ -381,8 +395,8 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             for (int j = 0; j < 32; ++j) {
               const long long no = coloff[c + j];
               if (no >= 0)
-                put_out2(C2 + (rowoff + no), f32_to_f64_bits(alpha_f * __uint_as_float(rre[j])),
-                         f32_to_f64_bits(alpha_f * __uint_as_float(rim[j])), store);
+                put_cplx(e.C, rowoff + no, e.c_f32, alpha_f * __uint_as_float(rre[j]),
+                         alpha_f * __uint_as_float(rim[j]), store);
             }
           }
           continue;
@@ -402,8 +416,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
               const long long ro = __shfl_sync(0xffffffffu, rowoff, rr);
               if (noff >= 0 && it.m0 + q * 32 + rr < p.M) {
                 const long long off = ro + noff;
-                put_out(e.C + (e.c_cplx ? 2 * off + comp : off), f32_to_f64_bits(alpha_f * tile[rr * 33 + lane]),
-                        store);
+                put_real(e.C, e.c_cplx ? 2 * off + comp : off, e.c_f32, alpha_f * tile[rr * 33 + lane], store);
               }
             }
             __syncwarp();
@@ -413,8 +426,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
               const long long no = coloff[c + j];
               if (no >= 0) {
                 const long long off = rowoff + no;
-                put_out(e.C + (e.c_cplx ? 2 * off + comp : off), f32_to_f64_bits(alpha_f * __uint_as_float(r[j])),
-                        store);
+                put_real(e.C, e.c_cplx ? 2 * off + comp : off, e.c_f32, alpha_f * __uint_as_float(r[j]), store);
               }
             }
           }

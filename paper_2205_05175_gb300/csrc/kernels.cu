@@ -36,6 +36,48 @@ __device__ __forceinline__ R cvt_r(double x) {
 }
 __device__ __forceinline__ double cvt_d(float x) { return f32_to_f64_bits(x); }
 __device__ __forceinline__ double cvt_d(double x) { return x; }
+__device__ __forceinline__ float cvt_f(float x) { return x; }
+__device__ __forceinline__ float cvt_f(double x) { return f64_to_f32_bits(x); }
+template <typename R>
+__device__ __forceinline__ R from_f(float x) {
+  if constexpr (std::is_same<R, float>::value) return x;
+  else return f32_to_f64_bits(x);
+}
+
+// Element access to a tensor of float64 or float32 (complex128 / complex64) elements; values
+// move between the two widths with the integer conversions above (no float64 instructions).
+template <typename R>
+__device__ __forceinline__ void ld_elem(const void* p, long long i, int cplx, int f32, R& re, R& im) {
+  if (f32) {
+    if (cplx) {
+      const float2 x = reinterpret_cast<const float2*>(p)[i];
+      re = from_f<R>(x.x);
+      im = from_f<R>(x.y);
+    } else {
+      re = from_f<R>(reinterpret_cast<const float*>(p)[i]);
+      im = 0;
+    }
+  } else {
+    if (cplx) {
+      const double2 x = reinterpret_cast<const double2*>(p)[i];
+      re = cvt_r<R>(x.x);
+      im = cvt_r<R>(x.y);
+    } else {
+      re = cvt_r<R>(reinterpret_cast<const double*>(p)[i]);
+      im = 0;
+    }
+  }
+}
+template <typename R>
+__device__ __forceinline__ void st_elem(void* p, long long i, int cplx, int f32, R re, R im) {
+  if (f32) {
+    if (cplx) reinterpret_cast<float2*>(p)[i] = make_float2(cvt_f(re), cvt_f(im));
+    else reinterpret_cast<float*>(p)[i] = cvt_f(re);
+  } else {
+    if (cplx) reinterpret_cast<double2*>(p)[i] = make_double2(cvt_d(re), cvt_d(im));
+    else reinterpret_cast<double*>(p)[i] = cvt_d(re);
+  }
+}
 
 template <int ELEM>
 __device__ __forceinline__ void put(void* dst, size_t i, double x, int part, int round_tf32) {
@@ -106,7 +148,7 @@ __global__ void pack_direct_kernel(PackDesc d, unsigned kext, unsigned padw) {
           xr = v.x;
           xi = v.y;
         } else {
-          xr = d.src[off];
+          xr = static_cast<const double*>(d.src)[off];
         }
         pack_store<ELEM>(d, bt, m, k, xr, xi);
       } else if (k - K < padw) {
@@ -148,7 +190,7 @@ __global__ void __launch_bounds__(256) pack_transpose_kernel(PackDesc d, unsigne
             xr = v.x;
             xi = v.y;
           } else {
-            xr = d.src[off];
+            xr = static_cast<const double*>(d.src)[off];
           }
         }
         tre[ty + 8 * i][tx] = xr;
@@ -260,15 +302,7 @@ __global__ void __launch_bounds__(256) pack_planes_direct_kernel(PackDesc d) {
       for (int j = 0; j < 4; ++j) {
         xr[j] = 0.f;
         xi[j] = 0.f;
-        if (kv[j]) {
-          if (d.src_cplx) {
-            const double2 v = reinterpret_cast<const double2*>(d.src)[base + coff[j]];
-            xr[j] = f64_to_f32_bits(v.x);
-            xi[j] = f64_to_f32_bits(v.y);
-          } else {
-            xr[j] = f64_to_f32_bits(d.src[base + coff[j]]);
-          }
-        }
+        if (kv[j]) ld_elem<float>(d.src, base + coff[j], d.src_cplx, d.src_f32, xr[j], xi[j]);
       }
       const unsigned long long drow = s_dst[r] + k4;
       for (int pl = 0; pl < np; ++pl) {
@@ -326,15 +360,7 @@ __global__ void __launch_bounds__(256) pack_planes_transpose_kernel(PackDesc d) 
         for (int i = 0; i < 8; ++i) {
           const long long ko = s_k[ty + 8 * i];
           float2 v = make_float2(0.f, 0.f);
-          if (rbase >= 0 && ko >= 0) {
-            const long long off = rbase + ko;
-            if (d.src_cplx) {
-              const double2 x = reinterpret_cast<const double2*>(d.src)[off];
-              v = make_float2(f64_to_f32_bits(x.x), f64_to_f32_bits(x.y));
-            } else {
-              v.x = f64_to_f32_bits(d.src[off]);
-            }
-          }
+          if (rbase >= 0 && ko >= 0) ld_elem<float>(d.src, rbase + ko, d.src_cplx, d.src_f32, v.x, v.y);
           tl[ty + 8 * i][tx] = v;
         }
       }
@@ -485,21 +511,9 @@ __global__ void __launch_bounds__(128) direct_kernel(DirectDesc d) {
       long long ao = 0, bo = 0;
       R sr = 0, si = 0;
       for (long long k = 0; k < d.K; ++k) {
-        R ar_, ai_ = 0, br_, bi_ = 0;
-        if (d.a_cplx) {
-          const double2 x = reinterpret_cast<const double2*>(d.A)[a0 + ao];
-          ar_ = cvt_r<R>(x.x);
-          ai_ = cvt_r<R>(x.y);
-        } else {
-          ar_ = cvt_r<R>(d.A[a0 + ao]);
-        }
-        if (d.b_cplx) {
-          const double2 x = reinterpret_cast<const double2*>(d.B)[b0 + bo];
-          br_ = cvt_r<R>(x.x);
-          bi_ = cvt_r<R>(x.y);
-        } else {
-          br_ = cvt_r<R>(d.B[b0 + bo]);
-        }
+        R ar_, ai_, br_, bi_;
+        ld_elem<R>(d.A, a0 + ao, d.a_cplx, d.a_f32, ar_, ai_);
+        ld_elem<R>(d.B, b0 + bo, d.b_cplx, d.b_f32, br_, bi_);
         sr += ar_ * br_ - ai_ * bi_;
         si += ar_ * bi_ + ai_ * br_;
         for (int q = d.ak.n - 1; q >= 0; --q) {
@@ -513,21 +527,14 @@ __global__ void __launch_bounds__(128) direct_kernel(DirectDesc d) {
         }
       }
       const long long off = s_c[r] + cn_off;
-      const double vr = cvt_d(ar * sr - ai * si);
-      const double vi = cvt_d(ar * si + ai * sr);
-      if (d.c_cplx) {
-        double2* c = reinterpret_cast<double2*>(d.C) + off;
-        if (d.store) {
-          *c = make_double2(vr, vi);
-        } else {
-          double2 x = *c;
-          x.x += vr;
-          x.y += vi;
-          *c = x;
-        }
-      } else {
-        d.C[off] = d.store ? vr : d.C[off] + vr;
+      R vr = ar * sr - ai * si, vi = ar * si + ai * sr;
+      if (!d.store) {
+        R cr, ci;
+        ld_elem<R>(d.C, off, d.c_cplx, d.c_f32, cr, ci);
+        vr += cr;
+        vi += ci;
       }
+      st_elem<R>(d.C, off, d.c_cplx, d.c_f32, vr, vi);
     }
   }
 }
@@ -571,43 +578,35 @@ __global__ void __launch_bounds__(256) add_kernel(AddDesc d, unsigned inner) {
     const unsigned nrows = min((unsigned)RT, rows - rt * RT);
     for (unsigned r = threadIdx.y; r < nrows; r += blockDim.y) {
       const long long c_off = s_c[r] + (long long)i * cs;
-      double2* c2 = reinterpret_cast<double2*>(d.C) + c_off;
       if (copy) {
         const long long a_off = s_a[0][r] + (long long)i * as[0];
-        const bool neg = d.ar[0] < 0.0;
-        if (d.a_cplx[0]) {
-          const double2 x = reinterpret_cast<const double2*>(d.A[0])[a_off];
-          const double xr = neg ? flip_sign(x.x) : x.x, xi = neg ? flip_sign(x.y) : x.y;
-          if (d.c_cplx) *c2 = make_double2(xr, xi);
-          else d.C[c_off] = xr;
+        if (!d.a_f32[0] && !d.c_f32) {   // float64 to float64: a bit copy (sign flip for -1)
+          const bool neg = d.ar[0] < 0.0;
+          double xr, xi;
+          ld_elem<double>(d.A[0], a_off, d.a_cplx[0], 0, xr, xi);
+          if (neg) {
+            xr = flip_sign(xr);
+            xi = flip_sign(xi);
+          }
+          st_elem<double>(d.C, c_off, d.c_cplx, 0, xr, xi);
         } else {
-          const double x = neg ? flip_sign(d.A[0][a_off]) : d.A[0][a_off];
-          if (d.c_cplx) *c2 = make_double2(x, 0.0);
-          else d.C[c_off] = x;
+          float xr, xi;
+          ld_elem<float>(d.A[0], a_off, d.a_cplx[0], d.a_f32[0], xr, xi);
+          if (d.ar[0] < 0.0) {
+            xr = -xr;
+            xi = -xi;
+          }
+          st_elem<float>(d.C, c_off, d.c_cplx, d.c_f32, xr, xi);
         }
         continue;
       }
       R accr = 0, acci = 0;
-      if (!d.store) {
-        if (d.c_cplx) {
-          const double2 x = *c2;
-          accr = cvt_r<R>(x.x);
-          acci = cvt_r<R>(x.y);
-        } else {
-          accr = cvt_r<R>(d.C[c_off]);
-        }
-      }
+      if (!d.store) ld_elem<R>(d.C, c_off, d.c_cplx, d.c_f32, accr, acci);
 #pragma unroll
       for (int q = 0; q < NS; ++q) {
         const long long a_off = s_a[q][r] + (long long)i * as[q];
-        R xr, xi = 0;
-        if (d.a_cplx[q]) {
-          const double2 x = reinterpret_cast<const double2*>(d.A[q])[a_off];
-          xr = cvt_r<R>(x.x);
-          xi = cvt_r<R>(x.y);
-        } else {
-          xr = cvt_r<R>(d.A[q][a_off]);
-        }
+        R xr, xi;
+        ld_elem<R>(d.A[q], a_off, d.a_cplx[q], d.a_f32[q], xr, xi);
         const R ar = (R)d.ar[q], ai = (R)d.ai[q];
         if (d.ai[q] == 0.0) {
           accr = fma(ar, xr, accr);
@@ -617,8 +616,7 @@ __global__ void __launch_bounds__(256) add_kernel(AddDesc d, unsigned inner) {
           acci += ar * xi + ai * xr;
         }
       }
-      if (d.c_cplx) *c2 = make_double2(cvt_d(accr), cvt_d(acci));
-      else d.C[c_off] = cvt_d(accr);
+      st_elem<R>(d.C, c_off, d.c_cplx, d.c_f32, accr, acci);
     }
   }
 }
@@ -638,11 +636,9 @@ __global__ void reduce_kernel(DirectDesc d, long long chunk) {
   double sr = 0.0, si = 0.0;
   for (long long k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
     const long long ao = a0 + imap_offset(d.ak, k), bo = b0 + imap_offset(d.bk, k);
-    double ar_, ai_ = 0.0, br_, bi_ = 0.0;
-    if (d.a_cplx) { ar_ = d.A[2 * ao]; ai_ = d.A[2 * ao + 1]; }
-    else ar_ = d.A[ao];
-    if (d.b_cplx) { br_ = d.B[2 * bo]; bi_ = d.B[2 * bo + 1]; }
-    else br_ = d.B[bo];
+    double ar_, ai_, br_, bi_;
+    ld_elem<double>(d.A, ao, d.a_cplx, d.a_f32, ar_, ai_);
+    ld_elem<double>(d.B, bo, d.b_cplx, d.b_f32, br_, bi_);
     sr += ar_ * br_ - ai_ * bi_;
     si += ar_ * bi_ + ai_ * br_;
   }
@@ -659,8 +655,15 @@ __global__ void reduce_kernel(DirectDesc d, long long chunk) {
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { sr += shr[q]; si += shi[q]; }
     const long long off = imap_offset(d.cb, bt) + imap_offset(d.cm, m) + imap_offset(d.cn, n);
     const double vr = d.ar * sr - d.ai * si, vi = d.ar * si + d.ai * sr;
-    if (d.c_cplx) { atomicAdd(&d.C[2 * off], vr); atomicAdd(&d.C[2 * off + 1], vi); }
-    else atomicAdd(&d.C[off], vr);
+    if (d.c_f32) {
+      float* C = static_cast<float*>(d.C);
+      if (d.c_cplx) { atomicAdd(&C[2 * off], f64_to_f32_bits(vr)); atomicAdd(&C[2 * off + 1], f64_to_f32_bits(vi)); }
+      else atomicAdd(&C[off], f64_to_f32_bits(vr));
+    } else {
+      double* C = static_cast<double*>(d.C);
+      if (d.c_cplx) { atomicAdd(&C[2 * off], vr); atomicAdd(&C[2 * off + 1], vi); }
+      else atomicAdd(&C[off], vr);
+    }
   }
 }
 
@@ -745,6 +748,7 @@ void launch_pack(const PackDesc& d, cudaStream_t s) {
     RTCC_CUDA(cudaGetLastError());
     return;
   }
+  RTCC_REQUIRE(!d.src_f32, "the float64 GEMM path packs float64 tensors only");
   const unsigned padw = (unsigned)(d.Kpad - (long long)d.nss * d.ncs * d.K);
   if (d.transpose) {
     const unsigned nkt = (unsigned)((d.K + 31) / 32) + (padw ? 1 : 0);

@@ -1,6 +1,7 @@
 // C-ABI of the RT-CCSD library (include/rtcc.h): handle, ground state, Runge-Kutta
 // propagation with a device-side step controller, dipole recording, spectrum.
 #include "model.cuh"
+#include <vector>
 #include "../../include/rtcc.h"
 #include <cmath>
 #include <cstring>
@@ -906,9 +907,42 @@ const char* rtcc_last_error(void) { return g_last_error.c_str(); }
 
 rtcc_status_t rtcc_create(const double* f, const double* B, int naux, const double* mu, int o, int v, int ntraj,
                           int prec, rtcc_handle_t* out) {
+  return rtcc_create_frozen_core(f, B, naux, mu, o, v, 0, ntraj, prec, out);
+}
+
+rtcc_status_t rtcc_create_frozen_core(const double* f_all, const double* B_all, int naux, const double* mu_all,
+                                      int o_all, int v, int nfc, int ntraj, int prec, rtcc_handle_t* out) {
   if (!out) return fail(RTCC_ERR_INVALID_ARG, "out is null");
   *out = nullptr;
-  if (!f || !B || !mu) return fail(RTCC_ERR_INVALID_ARG, "null input pointer");
+  if (!f_all || !B_all || !mu_all) return fail(RTCC_ERR_INVALID_ARG, "null input pointer");
+  if (nfc < 0 || nfc >= o_all) return fail(RTCC_ERR_INVALID_ARG, "frozen-core count must be in [0, o)");
+  if (o_all < 1 || v < 1 || naux < 1) return fail(RTCC_ERR_INVALID_ARG, "bad sizes");
+  // Frozen core: the lowest nfc occupied orbitals stay doubly occupied and uncorrelated.  The
+  // active problem uses the active blocks of f (which already carries the core's mean field),
+  // of the factors B and of mu; the core's constant dipole 2 sum_c mu_cc joins the reference term.
+  const int na = o_all + v, nact = na - nfc;
+  std::vector<double> fa, Ba, mua;
+  const double *f = f_all, *B = B_all, *mu = mu_all;
+  double core_ref[3] = {0, 0, 0};
+  if (nfc > 0) {
+    fa.resize((size_t)nact * nact);
+    Ba.resize((size_t)naux * nact * nact);
+    mua.resize((size_t)3 * nact * nact);
+    for (int p = 0; p < nact; ++p)
+      for (int q = 0; q < nact; ++q) {
+        const size_t src = (size_t)(p + nfc) * na + (q + nfc), dst = (size_t)p * nact + q;
+        fa[dst] = f_all[src];
+        for (int P = 0; P < naux; ++P) Ba[(size_t)P * nact * nact + dst] = B_all[(size_t)P * na * na + src];
+        for (int x = 0; x < 3; ++x) mua[(size_t)x * nact * nact + dst] = mu_all[(size_t)x * na * na + src];
+      }
+    for (int x = 0; x < 3; ++x)
+      for (int c = 0; c < nfc; ++c) core_ref[x] += 2.0 * mu_all[(size_t)x * na * na + (size_t)c * na + c];
+    f = fa.data();
+    B = Ba.data();
+    mu = mua.data();
+  }
+  const int o = o_all - nfc;
+  *out = nullptr;
   if (o < 1 || v < 1 || naux < 1 || ntraj < 1 || ntraj > 4096) return fail(RTCC_ERR_INVALID_ARG, "bad sizes");
   if (prec < 0 || prec > 3) return fail(RTCC_ERR_INVALID_ARG, "unknown precision");
   const int n = o + v;
@@ -949,7 +983,7 @@ rtcc_status_t rtcc_create(const double* f, const double* B, int naux, const doub
     for (int x = 0; x < 3; ++x) {
       double tr = 0;
       for (int i = 0; i < o; ++i) tr += mu[(size_t)x * n * n + i * n + i];
-      h->mu_ref[x] = 2.0 * tr;
+      h->mu_ref[x] = 2.0 * tr + core_ref[x];
     }
     h->ints = std::make_unique<IntegralStore>();
     build_integrals(*h->ints, h->Bd, naux, o, v, h->stream);

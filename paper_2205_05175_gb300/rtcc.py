@@ -57,6 +57,7 @@ class RtccError(RuntimeError):
 _vp, _dp, _ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
 _sig = {
     "rtcc_create": [_vp, _vp, C.c_int, _vp, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(_vp)],
+    "rtcc_create_frozen_core": [_vp, _vp, C.c_int, _vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(_vp)],
     "rtcc_destroy": [_vp],
     "rtcc_state_size": [_vp, C.POINTER(C.c_size_t)],
     "rtcc_ground_state": [_vp, C.c_double, C.c_int, _dp, _dp],
@@ -131,13 +132,19 @@ def _as_c(a, dtype=np.float64):
 class Handle:
     """Owner of one rtcc_handle_t (rtcc_create ... rtcc_destroy)."""
 
-    def __init__(self, f, B, mu, o, v, ntraj=1, prec=P64):
+    def __init__(self, f, B, mu, o, v, ntraj=1, prec=P64, nfc=0):
+        """nfc > 0 freezes the lowest nfc occupied orbitals (rtcc_create_frozen_core); the handle's
+        state then covers the o - nfc active occupied orbitals."""
         f, B, mu = _as_c(f), _as_c(B), _as_c(mu)
         nmo = o + v
         assert f.shape == (nmo, nmo) and B.shape[1:] == (nmo, nmo) and mu.shape == (3, nmo, nmo)
-        self.o, self.v, self.ntraj = o, v, ntraj
+        self.o, self.v, self.ntraj = o - nfc, v, ntraj
         h = C.c_void_p()
-        _check(_lib.rtcc_create(_ptr(f), _ptr(B), B.shape[0], _ptr(mu), o, v, ntraj, int(prec), C.byref(h)))
+        if nfc:
+            _check(_lib.rtcc_create_frozen_core(_ptr(f), _ptr(B), B.shape[0], _ptr(mu), o, v, nfc, ntraj, int(prec),
+                                                C.byref(h)))
+        else:
+            _check(_lib.rtcc_create(_ptr(f), _ptr(B), B.shape[0], _ptr(mu), o, v, ntraj, int(prec), C.byref(h)))
         self.h = h
         n = C.c_size_t()
         _check(_lib.rtcc_state_size(self.h, C.byref(n)))
