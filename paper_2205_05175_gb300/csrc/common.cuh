@@ -89,6 +89,13 @@ struct PackDesc {
   // rd_src gives the source offset and rd_dst the packed row index of a read-order row
   IndexMap rd_src, rd_dst;
   void* dst;
+  // pair-symmetric gather (plane packs, direct mode only): when ktab is set, packed column k
+  // holds kw[k] * (src[o1] + ksign * src[o2]) with (o1, o2) = ktab[2k], ktab[2k+1] added to the
+  // row offset (kw may be null: weight 1); when rtab is set, row m starts at rtab[m]
+  const long long* ktab;
+  const float* kw;
+  float ksign;
+  const long long* rtab;
 };
 
 // Unpack: C[bt, m, n] += alpha * (value assembled from the GEMM output).
@@ -165,6 +172,11 @@ struct TcEpilogue {
   long long sn;
   int unit_n;          // 1: the output's unit stride runs along n (write through a shared-memory transpose)
   int store;           // 1: the output region is known to be zero: store instead of read-modify-write
+  // pair-symmetric scatter: when ctab1 is set, column n goes to offset ctab1[n] and, when
+  // ctab2[n] >= 0, sign2 times it to ctab2[n] (instead of the cn map)
+  const long long* ctab1;
+  const long long* ctab2;
+  float sign2;
 };
 struct TcGemmParams {
   CUtensorMap tmA, tmB;

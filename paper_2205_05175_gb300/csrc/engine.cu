@@ -97,6 +97,7 @@ struct Compiled {
   int kind = CK_ADD;
   AddDesc add{};
   std::vector<int> add_ops;   // CK_ADD: the program ops whose sources this kernel sums (first = own op)
+  std::shared_ptr<Compiled> twin;   // pair-symmetric contraction: the antisymmetric-part GEMM
   DirectDesc dir{};
   long long splits = 1;
   // GEMM path
@@ -272,8 +273,8 @@ int Engine::temp(int arena, const std::string& name, const std::vector<int>& dim
 }
 
 void Engine::ein(Program& P, int c, const std::string& lc, int a, const std::string& la, int b,
-                 const std::string& lb, cplx alpha) {
-  P.ops.push_back(Op{OP_EIN, c, a, b, lc, la, lb, alpha});
+                 const std::string& lb, cplx alpha, bool pairsym) {
+  P.ops.push_back(Op{OP_EIN, c, a, b, lc, la, lb, alpha, pairsym});
 }
 
 void Engine::add(Program& P, int c, const std::string& lc, int a, const std::string& la, cplx alpha) {
@@ -304,7 +305,8 @@ Program Engine::reverse(const Program& fwd, const std::vector<int>& active_input
     if (!active.count(op.c)) continue;
     const int dc = adj.at(op.c);
     if (op.kind == OP_EIN) {
-      if (active.count(op.a)) ein(R, adj.at(op.a), op.la, dc, op.lc, op.b, op.lb, op.alpha);
+      // the reverse of a pair-symmetric contraction keeps B and its symmetry
+      if (active.count(op.a)) ein(R, adj.at(op.a), op.la, dc, op.lc, op.b, op.lb, op.alpha, op.pairsym);
       if (active.count(op.b)) ein(R, adj.at(op.b), op.lb, op.a, op.la, dc, op.lc, op.alpha);
     } else if (active.count(op.a)) {
       RTCC_REQUIRE(op.la.size() == op.lc.size(), "reverse of a broadcasting add of an active tensor");
@@ -455,7 +457,10 @@ void Engine::plan(Program& P) {
     } else {
       k.kind = CK_GEMM;
     }
-    if (k.kind == CK_GEMM && prec != Prec::P64) {
+    if (k.kind == CK_GEMM && prec != Prec::P64 && op.pairsym &&
+        plan_pairsym(k, op, Lm, Ln, Lk, Lb, d.am, d.cm, prec, c_fresh)) {
+      // planned as two GEMMs over ordered pairs
+    } else if (k.kind == CK_GEMM && prec != Prec::P64) {
       // tensor-core path: operands packed as planes (re/im x hi/lo), segment table per output plane
       const bool x3 = (prec == Prec::TF32X3 || prec == Prec::BF16X3);
       const int npart = x3 ? 2 : 1;
@@ -761,33 +766,203 @@ void Engine::bind(Program& P) {
     k.dir.B = B.ptr;
     k.dir.C = C.ptr;
     if (k.kind != CK_GEMM) continue;
-    k.pa.src = A.ptr;
-    k.pb.src = B.ptr;
-    k.up.C = C.ptr;
-    if (k.a_const) {
-      k.a_pre = dev_alloc(k.a_bytes);
-      allocs_.push_back(k.a_pre);
-      bytes_ += k.a_bytes;
-      k.pa.dst = k.a_pre;
-      launch_pack(k.pa, stream_);
-    } else {
-      k.pa.dst = wsA_;
-    }
-    if (k.b_const) {
-      k.b_pre = dev_alloc(k.b_bytes);
-      allocs_.push_back(k.b_pre);
-      bytes_ += k.b_bytes;
-      k.pb.dst = k.b_pre;
-      launch_pack(k.pb, stream_);
-    } else {
-      k.pb.dst = wsB_;
-    }
-    k.up.gout = wsC_;
-    if (k.tc_kind >= 0) {
-      k.tcp.p.epi.C = C.ptr;
-      tc_gemm_plan(k.tcp, k.tc_kind, k.pa.dst, k.pa.nrb, k.pb.dst, k.pb.nrb, k.pa.R, k.pb.R, k.Kpad, k.NB, dev_err_);
-    }
+    bind_gemm(k, A, B, C);
+    if (k.twin) bind_gemm(*k.twin, A, B, C);
   }
+}
+
+void Engine::bind_gemm(Compiled& k, const Tensor& A, const Tensor& B, const Tensor& C) {
+  k.pa.src = A.ptr;
+  k.pb.src = B.ptr;
+  k.up.C = C.ptr;
+  if (k.a_const) {
+    k.a_pre = dev_alloc(k.a_bytes);
+    allocs_.push_back(k.a_pre);
+    bytes_ += k.a_bytes;
+    k.pa.dst = k.a_pre;
+    launch_pack(k.pa, stream_);
+  } else {
+    k.pa.dst = wsA_;
+  }
+  if (k.b_const) {
+    k.b_pre = dev_alloc(k.b_bytes);
+    allocs_.push_back(k.b_pre);
+    bytes_ += k.b_bytes;
+    k.pb.dst = k.b_pre;
+    launch_pack(k.pb, stream_);
+  } else {
+    k.pb.dst = wsB_;
+  }
+  k.up.gout = wsC_;
+  if (k.tc_kind >= 0) {
+    k.tcp.p.epi.C = C.ptr;
+    tc_gemm_plan(k.tcp, k.tc_kind, k.pa.dst, k.pa.nrb, k.pb.dst, k.pb.nrb, k.pa.R, k.pb.R, k.Kpad, k.NB, dev_err_);
+  }
+}
+
+const long long* Engine::upload(const std::vector<long long>& v) {
+  void* p = dev_alloc(std::max<size_t>(1, v.size()) * sizeof(long long));
+  allocs_.push_back(p);
+  bytes_ += v.size() * sizeof(long long);
+  RTCC_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(long long), cudaMemcpyHostToDevice));
+  return static_cast<const long long*>(p);
+}
+const float* Engine::upload(const std::vector<float>& v) {
+  void* p = dev_alloc(std::max<size_t>(1, v.size()) * sizeof(float));
+  allocs_.push_back(p);
+  bytes_ += v.size() * sizeof(float);
+  RTCC_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(float), cudaMemcpyHostToDevice));
+  return static_cast<const float*>(p);
+}
+
+// Pair-symmetric contraction C[m, n1, n2] += alpha sum_{k1,k2} A[m, k1, k2] V[n1, n2, k1, k2] with
+// V[n1,n2,k1,k2] = V[n2,n1,k2,k1] (the particle-particle ladder with V = (ae|bf) and its reverse).
+// Over ordered pairs p <= q of the contracted labels and x <= y of the kept ones,
+//   A^s[m, pq] = A[m,p,q] + s A[m,q,p],   V^s[xy, pq] = w_pq (V[x,y,p,q] + s V[x,y,q,p]) / 2,
+//   w_pq = 1 - delta_pq / 2,   P^s = A^s V^s^T   (s = +1, -1),
+// and C[m,x,y] += P^+ + P^-, C[m,y,x] += P^+ - P^- (x < y): the sum over all (p, q) regrouped by
+// the symmetry, with half the multiply-adds.  Two GEMMs; the second target of each output column
+// and its sign are applied in the epilogue.  Returns false (generic path) when the shape does not fit.
+bool Engine::plan_pairsym(Compiled& k, const Op& op, const std::string& Lm, const std::string& Ln,
+                          const std::string& Lk, const std::string& Lb, const IndexMap& am, const IndexMap& cm,
+                          Prec prec, bool c_fresh) {
+  const Tensor& A = tensors_[op.a];
+  const Tensor& B = tensors_[op.b];
+  const Tensor& C = tensors_[op.c];
+  const std::string& lb = op.lb;
+  if (!Lb.empty() || Ln.size() != 2 || Lk.size() != 2 || lb.size() != 4 || B.cplx || !B.constant ||
+      op.alpha.imag() != 0.0)
+    return false;
+  auto same_set = [](const std::string& pr, const std::string& L) {
+    return (pr[0] == L[0] && pr[1] == L[1]) || (pr[0] == L[1] && pr[1] == L[0]);
+  };
+  std::string pn, pk;   // the kept and the contracted pair, each in B's label order
+  if (same_set(lb.substr(0, 2), Ln) && same_set(lb.substr(2, 2), Lk)) {
+    pn = lb.substr(0, 2);
+    pk = lb.substr(2, 2);
+  } else if (same_set(lb.substr(0, 2), Lk) && same_set(lb.substr(2, 2), Ln)) {
+    pk = lb.substr(0, 2);
+    pn = lb.substr(2, 2);
+  } else {
+    return false;
+  }
+  auto dimB = [&](char l) { return B.dims[lb.find(l)]; };
+  auto strB = [&](char l) { return B.strides[lb.find(l)]; };
+  const int dn = dimB(pn[0]), dk = dimB(pk[0]);
+  if (dimB(pn[1]) != dn || dimB(pk[1]) != dk) return false;
+  const long long Np = (long long)dn * (dn + 1) / 2, Kt = (long long)dk * (dk + 1) / 2;
+  const long long M = prod_dims(am);
+  const long long sa1 = A.strides[op.la.find(pk[0])], sa2 = A.strides[op.la.find(pk[1])];
+  const long long sc1 = C.strides[op.lc.find(pn[0])], sc2 = C.strides[op.lc.find(pn[1])];
+  const long long sv1 = strB(pn[0]), sv2 = strB(pn[1]), sk1 = strB(pk[0]), sk2 = strB(pk[1]);
+  std::vector<long long> ka(2 * Kt), kv(2 * Kt), rv(Np), c1(Np), c2(Np);
+  std::vector<float> wv(Kt);
+  long long t = 0;
+  for (int x = 0; x < dk; ++x)
+    for (int y = x; y < dk; ++y, ++t) {
+      ka[2 * t] = x * sa1 + y * sa2;
+      ka[2 * t + 1] = y * sa1 + x * sa2;
+      kv[2 * t] = x * sk1 + y * sk2;
+      kv[2 * t + 1] = y * sk1 + x * sk2;
+      wv[t] = (x == y) ? 0.25f : 0.5f;
+    }
+  t = 0;
+  for (int x = 0; x < dn; ++x)
+    for (int y = x; y < dn; ++y, ++t) {
+      rv[t] = x * sv1 + y * sv2;
+      c1[t] = x * sc1 + y * sc2;
+      c2[t] = (x == y) ? -1 : y * sc1 + x * sc2;
+    }
+  const long long* ka_d = upload(ka);
+  const long long* kv_d = upload(kv);
+  const long long* rv_d = upload(rv);
+  const long long* c1_d = upload(c1);
+  const long long* c2_d = upload(c2);
+  const float* wv_d = upload(wv);
+
+  const bool x3 = (prec == Prec::TF32X3 || prec == Prec::BF16X3);
+  const int npart = x3 ? 2 : 1;
+  const int elem = (prec == Prec::BF16X3) ? PE_BF16 : PE_F32;
+  const int esz = (elem == PE_F32) ? 4 : 2;
+  const int kind = (prec == Prec::BF16X3) ? 1 : 0;
+  const long long Kpad = round_up(Kt, tc_kblock_elems(kind));
+  auto planes = [&](PackDesc& pd, const Tensor& T, long long R, int sign) {
+    pd = PackDesc{};
+    pd.src = T.ptr;
+    pd.src_cplx = T.cplx;
+    pd.src_f32 = T.f32;
+    pd.R = R;
+    pd.K = Kt;
+    pd.NB = 1;
+    const int nc = T.cplx ? 2 : 1;
+    pd.nrb = nc * npart;
+    pd.ncs = 1;
+    pd.nss = 1;
+    for (int c = 0; c < nc; ++c)
+      for (int q = 0; q < npart; ++q) {
+        const int rb = c * npart + q;
+        pd.comp[rb][0] = c;
+        pd.sign[rb][0] = 1;
+        pd.rb_part[rb] = (npart == 1) ? SP_FULL : (q == 0 ? SP_HI : SP_LO);
+      }
+    pd.Kpad = Kpad;
+    pd.elem = elem;
+    pd.round_tf32 = 1;
+    pd.transpose = 0;
+    pd.ksign = (float)sign;
+  };
+  auto build = [&](Compiled& g, int sign) {
+    g.kind = CK_GEMM;
+    g.tc_kind = kind;
+    planes(g.pa, A, M, sign);
+    g.pa.rows = am;
+    g.pa.ktab = ka_d;
+    planes(g.pb, B, Np, sign);
+    g.pb.rtab = rv_d;
+    g.pb.ktab = kv_d;
+    g.pb.kw = wv_d;
+    TcGemmParams& gp = g.tcp.p;
+    gp = TcGemmParams{};
+    gp.nrb = A.cplx ? 2 : 1;
+    auto pl = [&](int c, int q) { return c * npart + q; };
+    auto pair = [&](int rb, int ca) {
+      auto push = [&](int pa_, int pb_) { gp.seg[rb][gp.nseg[rb]++] = TcSeg{pa_, pb_, 0}; };
+      if (npart == 1) push(pl(ca, 0), pl(0, 0));
+      else {
+        push(pl(ca, 0), pl(0, 0));
+        push(pl(ca, 0), pl(0, 1));
+        push(pl(ca, 1), pl(0, 0));
+      }
+    };
+    pair(0, 0);
+    if (A.cplx) pair(1, 1);
+    TcEpilogue& ep = gp.epi;
+    ep.c_cplx = C.cplx;
+    ep.c_f32 = C.f32;
+    ep.alpha = op.alpha.real();
+    ep.cm = cm;
+    ep.cb = IndexMap{};
+    ep.flat_n = 0;
+    ep.unit_n = (sc1 == 1 || sc2 == 1) ? 1 : 0;
+    ep.store = (sign > 0 && c_fresh) ? 1 : 0;   // the + part writes every element once
+    ep.ctab1 = c1_d;
+    ep.ctab2 = c2_d;
+    ep.sign2 = (float)sign;
+    g.Kpad = Kpad;
+    g.NB = 1;
+    g.GM = (long long)g.pa.nrb * M;
+    g.GN = (long long)g.pb.nrb * Np;
+    g.a_const = A.constant;
+    g.b_const = true;
+    g.a_bytes = (size_t)(g.GM * Kpad * esz);
+    g.b_bytes = (size_t)(g.GN * Kpad * esz);
+    g.exec_flops = 2 * M * Np * Kt * (long long)(gp.nseg[0] + gp.nseg[1]);
+    if (!g.a_const) wsA_bytes_ = std::max(wsA_bytes_, g.a_bytes);
+  };
+  build(k, +1);
+  k.twin = std::make_shared<Compiled>();
+  build(*k.twin, -1);
+  return true;
 }
 
 void Engine::finalize(std::vector<Program*> progs) {
@@ -859,41 +1034,45 @@ void Engine::run(const Program& P) {
         launch_reduce(k.dir, k.splits, stream_);
         pr.stop(stream_, KC_REDUCE, (double)k.alg_flops, 0.0, tag);
         break;
-      default: {
-        const double esz = (k.pa.elem == PE_F64) ? 8 : (k.pa.elem == PE_F32 ? 4 : 2);
-        if (!k.a_const) {
-          pr.start(stream_);
-          launch_pack(k.pa, stream_);
-          pr.stop(stream_, KC_PACK, 0.0,
-                  (double)k.NB * k.pa.R * k.pa.K * (k.pa.src_cplx ? 2 : 1) * (k.pa.src_f32 ? 4 : 8) + (double)k.NB * k.GM * k.Kpad * esz, tag);
-        }
-        if (!k.b_const) {
-          pr.start(stream_);
-          launch_pack(k.pb, stream_);
-          pr.stop(stream_, KC_PACK, 0.0,
-                  (double)k.NB * k.pb.R * k.pb.K * (k.pb.src_cplx ? 2 : 1) * (k.pb.src_f32 ? 4 : 8) + (double)k.NB * k.GN * k.Kpad * esz, tag);
-        }
-        if (k.tc_kind >= 0) {
-          // kernel-level algorithmic flops: real multiply-adds of all segments, without padding
-          pr.start(stream_);
-          launch_tc_gemm(k.tcp, stream_);
-          pr.stop(stream_, KC_TC_GEMM, (double)k.exec_flops,
-                  (double)k.NB * (k.GM + k.GN) * k.Kpad * esz + 2.0 * k.NB * k.pa.R * k.pb.R * (C_cplx_of(k) ? 2 : 1) * (k.tcp.p.epi.c_f32 ? 4 : 8), tag);
-          break;
-        }
-        const double kflops = 2.0 * k.NB * k.GM * k.GN * (double)(k.pa.nss * k.pa.ncs * k.pa.K);
-        pr.start(stream_);
-        launch_gemm_f64(static_cast<const double*>(k.pa.dst), static_cast<const double*>(k.pb.dst),
-                        static_cast<double*>(wsC_), k.GM, k.GN, k.Kpad, k.NB, stream_);
-        pr.stop(stream_, KC_F64_GEMM, kflops,
-                (double)k.NB * (k.GM + k.GN) * k.Kpad * esz + (double)k.NB * k.GM * k.GN * 8, tag);
-        pr.start(stream_);
-        launch_unpack(k.up, stream_);
-        pr.stop(stream_, KC_UNPACK, 0.0,
-                (double)k.NB * k.GM * k.GN * (k.tc_kind >= 0 ? 4 : 8) + 2.0 * k.NB * k.up.M * k.up.N * (k.up.c_cplx ? 16 : 8), tag);
-      }
+      default:
+        run_gemm(k, pr, tag);
+        if (k.twin) run_gemm(*k.twin, pr, tag);
     }
   }
+}
+
+void Engine::run_gemm(const Compiled& k, Profiler& pr, const char* tag) {
+  const double esz = (k.pa.elem == PE_F64) ? 8 : (k.pa.elem == PE_F32 ? 4 : 2);
+  if (!k.a_const) {
+    pr.start(stream_);
+    launch_pack(k.pa, stream_);
+    pr.stop(stream_, KC_PACK, 0.0,
+            (double)k.NB * k.pa.R * k.pa.K * (k.pa.src_cplx ? 2 : 1) * (k.pa.src_f32 ? 4 : 8) + (double)k.NB * k.GM * k.Kpad * esz, tag);
+  }
+  if (!k.b_const) {
+    pr.start(stream_);
+    launch_pack(k.pb, stream_);
+    pr.stop(stream_, KC_PACK, 0.0,
+            (double)k.NB * k.pb.R * k.pb.K * (k.pb.src_cplx ? 2 : 1) * (k.pb.src_f32 ? 4 : 8) + (double)k.NB * k.GN * k.Kpad * esz, tag);
+  }
+  if (k.tc_kind >= 0) {
+    // kernel-level algorithmic flops: real multiply-adds of all segments, without padding
+    pr.start(stream_);
+    launch_tc_gemm(k.tcp, stream_);
+    pr.stop(stream_, KC_TC_GEMM, (double)k.exec_flops,
+            (double)k.NB * (k.GM + k.GN) * k.Kpad * esz + 2.0 * k.NB * k.pa.R * k.pb.R * (C_cplx_of(k) ? 2 : 1) * (k.tcp.p.epi.c_f32 ? 4 : 8), tag);
+    return;
+  }
+  const double kflops = 2.0 * k.NB * k.GM * k.GN * (double)(k.pa.nss * k.pa.ncs * k.pa.K);
+  pr.start(stream_);
+  launch_gemm_f64(static_cast<const double*>(k.pa.dst), static_cast<const double*>(k.pb.dst),
+                  static_cast<double*>(wsC_), k.GM, k.GN, k.Kpad, k.NB, stream_);
+  pr.stop(stream_, KC_F64_GEMM, kflops,
+          (double)k.NB * (k.GM + k.GN) * k.Kpad * esz + (double)k.NB * k.GM * k.GN * 8, tag);
+  pr.start(stream_);
+  launch_unpack(k.up, stream_);
+  pr.stop(stream_, KC_UNPACK, 0.0,
+          (double)k.NB * k.GM * k.GN * (k.tc_kind >= 0 ? 4 : 8) + 2.0 * k.NB * k.up.M * k.up.N * (k.up.c_cplx ? 16 : 8), tag);
 }
 
 EngineStats Engine::stats_of(const Program& P) const {
@@ -903,7 +1082,8 @@ EngineStats Engine::stats_of(const Program& P) const {
     if (cp->kind == CK_GEMM) {
       s.gemm_flops += cp->alg_flops;
       // packs of non-constant operands, the GEMM, and the unpack of the float64 SIMT path
-      s.launches += (cp->tc_kind >= 0 ? 1 : 2) + (cp->a_const ? 0 : 1) + (cp->b_const ? 0 : 1);
+      for (const Compiled* g = cp.get(); g; g = g->twin.get())
+        s.launches += (g->tc_kind >= 0 ? 1 : 2) + (g->a_const ? 0 : 1) + (g->b_const ? 0 : 1);
     } else {
       s.direct_flops += cp->alg_flops;
       s.launches += 1;

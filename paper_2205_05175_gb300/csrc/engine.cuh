@@ -43,6 +43,10 @@ struct Op {
   int c, a, b;
   std::string lc, la, lb;
   cplx alpha;
+  // EIN only: B is a real constant tensor with two label pairs (its labels 0,1 and 2,3; one pair
+  // contracted, the other kept) and B is unchanged by swapping both pairs at once, e.g.
+  // (ae|bf) = (bf|ae).  The planner may then contract over ordered pairs only (half the work).
+  bool pairsym = false;
 };
 
 struct Compiled;   // defined in engine.cu
@@ -117,7 +121,7 @@ class Engine {
 
   // --- program building ------------------------------------------------------------------
   static void ein(Program& P, int c, const std::string& lc, int a, const std::string& la, int b,
-                  const std::string& lb, cplx alpha = 1.0);
+                  const std::string& lb, cplx alpha = 1.0, bool pairsym = false);
   static void add(Program& P, int c, const std::string& lc, int a, const std::string& la, cplx alpha = 1.0);
 
   // Reverse mode: given the forward program and the ids of its active inputs, return the
@@ -140,6 +144,12 @@ class Engine {
   void plan(Program& P);
   void bind(Program& P);
   bool add_source(Compiled& k, const std::vector<Op>& ops, int oi, const std::string& lc);
+  bool plan_pairsym(Compiled& k, const Op& op, const std::string& Lm, const std::string& Ln, const std::string& Lk,
+                    const std::string& Lb, const IndexMap& am, const IndexMap& cm, Prec prec, bool c_fresh);
+  void bind_gemm(Compiled& k, const Tensor& A, const Tensor& B, const Tensor& C);
+  void run_gemm(const Compiled& k, Profiler& pr, const char* tag);
+  const long long* upload(const std::vector<long long>& v);
+  const float* upload(const std::vector<float>& v);
   void merge_adds(Program& P);
 
   Prec prec_;

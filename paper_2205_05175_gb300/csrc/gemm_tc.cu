@@ -216,7 +216,8 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   uint8_t* sB = base + STAGES * A_BYTES;
   float* etile = reinterpret_cast<float*>(sB + STAGES * B_BYTES);          // EPW x 32 x 33 floats
   long long* coloff_all = reinterpret_cast<long long*>(etile + EPW * 32 * 33);   // EPW x WCOLS entries
-  uint64_t* full = reinterpret_cast<uint64_t*>(coloff_all + EPW * WCOLS);
+  long long* coloff2_all = coloff_all + EPW * WCOLS;                               // second targets
+  uint64_t* full = reinterpret_cast<uint64_t*>(coloff2_all + EPW * WCOLS);
   uint64_t* empty = full + STAGES;
   uint64_t* tfull = empty + STAGES;
   uint64_t* tempty = tfull + 2;
@@ -329,6 +330,9 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     const bool store = e.store && splits == 1;
     float* tile = etile + ew * (32 * 33);
     long long* coloff = coloff_all + ew * WCOLS;   // warp-private: no cross-warp barrier in the epilogue
+    long long* coloff2 = coloff2_all + ew * WCOLS;
+    const bool dual = e.ctab1 != nullptr;          // pair-symmetric scatter to a second column
+    const float s2 = e.sign2;
     int local = 0;
     for (int w = blockIdx.x; w < total_items; w += gridDim.x, ++local) {
       const Item it = decode_item<BN>(p, w, splits);
@@ -337,7 +341,12 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
       __syncwarp();
       for (int c = lane; c < WCOLS; c += 32) {
         const int n = it.n0 + hc + c;
-        coloff[c] = (n < p.N) ? (e.flat_n ? (long long)n * e.sn : imap32(e.cn, (unsigned)n)) : -1;
+        if (dual) {
+          coloff[c] = (n < p.N) ? e.ctab1[n] : -1;
+          coloff2[c] = (n < p.N) ? e.ctab2[n] : -1;
+        } else {
+          coloff[c] = (n < p.N) ? (e.flat_n ? (long long)n * e.sn : imap32(e.cn, (unsigned)n)) : -1;
+        }
       }
       __syncwarp();
       const int row = it.m0 + q * 32 + lane;
@@ -380,11 +389,15 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             for (int j = 0; j < 32; ++j) tim[j] = tile[j * 33 + lane];
             __syncwarp();
             const long long noff = coloff[c + lane];
+            const long long noff2 = dual ? coloff2[c + lane] : -1;
 #pragma unroll
             for (int rr = 0; rr < 32; ++rr) {
               const long long ro = __shfl_sync(0xffffffffu, rowoff, rr);
-              if (noff >= 0 && it.m0 + q * 32 + rr < p.M)
+              if (noff >= 0 && it.m0 + q * 32 + rr < p.M) {
                 put_cplx(e.C, ro + noff, e.c_f32, alpha_f * tre[rr], alpha_f * tim[rr], store);
+                if (noff2 >= 0)
+                  put_cplx(e.C, ro + noff2, e.c_f32, s2 * alpha_f * tre[rr], s2 * alpha_f * tim[rr], store);
+              }
             }
           } else {
             uint32_t rre[32], rim[32];
@@ -394,9 +407,14 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               const long long no = coloff[c + j];
-              if (no >= 0)
+              if (no >= 0) {
                 put_cplx(e.C, rowoff + no, e.c_f32, alpha_f * __uint_as_float(rre[j]),
                          alpha_f * __uint_as_float(rim[j]), store);
+                const long long no2 = dual ? coloff2[c + j] : -1;
+                if (no2 >= 0)
+                  put_cplx(e.C, rowoff + no2, e.c_f32, s2 * alpha_f * __uint_as_float(rre[j]),
+                           s2 * alpha_f * __uint_as_float(rim[j]), store);
+              }
             }
           }
           continue;
@@ -411,12 +429,18 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = __uint_as_float(r[j]);
             __syncwarp();
             const long long noff = coloff[c + lane];
+            const long long noff2 = dual ? coloff2[c + lane] : -1;
 #pragma unroll
             for (int rr = 0; rr < 32; ++rr) {
               const long long ro = __shfl_sync(0xffffffffu, rowoff, rr);
               if (noff >= 0 && it.m0 + q * 32 + rr < p.M) {
+                const float val = alpha_f * tile[rr * 33 + lane];
                 const long long off = ro + noff;
-                put_real(e.C, e.c_cplx ? 2 * off + comp : off, e.c_f32, alpha_f * tile[rr * 33 + lane], store);
+                put_real(e.C, e.c_cplx ? 2 * off + comp : off, e.c_f32, val, store);
+                if (noff2 >= 0) {
+                  const long long off2 = ro + noff2;
+                  put_real(e.C, e.c_cplx ? 2 * off2 + comp : off2, e.c_f32, s2 * val, store);
+                }
               }
             }
             __syncwarp();
@@ -425,8 +449,14 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             for (int j = 0; j < 32; ++j) {
               const long long no = coloff[c + j];
               if (no >= 0) {
+                const float val = alpha_f * __uint_as_float(r[j]);
                 const long long off = rowoff + no;
-                put_real(e.C, e.c_cplx ? 2 * off + comp : off, e.c_f32, alpha_f * __uint_as_float(r[j]), store);
+                put_real(e.C, e.c_cplx ? 2 * off + comp : off, e.c_f32, val, store);
+                const long long no2 = dual ? coloff2[c + j] : -1;
+                if (no2 >= 0) {
+                  const long long off2 = rowoff + no2;
+                  put_real(e.C, e.c_cplx ? 2 * off2 + comp : off2, e.c_f32, s2 * val, store);
+                }
               }
             }
           }
@@ -446,7 +476,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
 
 template <int BN, int KIND, int STAGES, int EPW>
 constexpr size_t smem_bytes() {
-  return 1024 + (size_t)STAGES * (BM * 128 + BN * 128) + (size_t)EPW * 32 * 33 * 4 + (size_t)4 * BN * 8 +
+  return 1024 + (size_t)STAGES * (BM * 128 + BN * 128) + (size_t)EPW * 32 * 33 * 4 + (size_t)2 * 4 * BN * 8 +
          (2 * STAGES + 4) * 8 + 16;
 }
 

@@ -273,12 +273,24 @@ __global__ void __launch_bounds__(256) pack_planes_direct_kernel(PackDesc d) {
   const unsigned tid = threadIdx.y * blockDim.x + threadIdx.x;
   const unsigned k4 = 4u * (blockIdx.x * blockDim.x + threadIdx.x);
   const bool kok = k4 < Kp;
-  long long coff[4];
+  long long coff[4], coff2[4];
+  float kwt[4];
   bool kv[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     kv[j] = k4 + j < K;
-    coff[j] = kv[j] ? imap32(d.cols, k4 + j) : 0;
+    coff[j] = 0;
+    coff2[j] = -1;
+    kwt[j] = 1.f;
+    if (kv[j]) {
+      if (d.ktab) {
+        coff[j] = d.ktab[2 * (k4 + j)];
+        coff2[j] = d.ktab[2 * (k4 + j) + 1];
+        if (d.kw) kwt[j] = d.kw[k4 + j];
+      } else {
+        coff[j] = imap32(d.cols, k4 + j);
+      }
+    }
   }
   const int np = d.nrb;
   const unsigned long long pstride = (unsigned long long)R * Kp;   // plane stride in elements
@@ -288,7 +300,7 @@ __global__ void __launch_bounds__(256) pack_planes_direct_kernel(PackDesc d) {
       const unsigned row = rt * RT + tid;
       if (row < NR) {
         const unsigned bt = row / R, m = row - bt * R;
-        s_src[tid] = imap32(d.bat, bt) + imap32(d.rows, m);
+        s_src[tid] = imap32(d.bat, bt) + (d.rtab ? d.rtab[m] : imap32(d.rows, m));
         s_dst[tid] = ((unsigned long long)bt * np * R + m) * Kp;
       }
     }
@@ -302,7 +314,15 @@ __global__ void __launch_bounds__(256) pack_planes_direct_kernel(PackDesc d) {
       for (int j = 0; j < 4; ++j) {
         xr[j] = 0.f;
         xi[j] = 0.f;
-        if (kv[j]) ld_elem<float>(d.src, base + coff[j], d.src_cplx, d.src_f32, xr[j], xi[j]);
+        if (kv[j]) {
+          ld_elem<float>(d.src, base + coff[j], d.src_cplx, d.src_f32, xr[j], xi[j]);
+          if (coff2[j] >= 0) {
+            float yr, yi;
+            ld_elem<float>(d.src, base + coff2[j], d.src_cplx, d.src_f32, yr, yi);
+            xr[j] = kwt[j] * (xr[j] + d.ksign * yr);
+            xi[j] = kwt[j] * (xi[j] + d.ksign * yi);
+          }
+        }
       }
       const unsigned long long drow = s_dst[r] + k4;
       for (int pl = 0; pl < np; ++pl) {
@@ -726,6 +746,8 @@ void launch_pack(const PackDesc& d, cudaStream_t s) {
   const long long NR = d.NB * d.R;
   if (NR == 0) return;
   RTCC_REQUIRE(NR < (1ll << 31) && d.K < (1ll << 31), "pack extents exceed 32-bit indexing");
+  RTCC_REQUIRE(!(d.ktab || d.rtab) || (d.ncs == 1 && d.nss == 1 && d.elem != PE_F64 && d.Kpad % 4 == 0 && !d.transpose),
+               "pair-symmetric gathers are tensor-core plane packs in direct mode");
   if (d.ncs == 1 && d.nss == 1 && d.elem != PE_F64 && d.Kpad % 4 == 0) {
     // tensor-core operand planes
     if (d.transpose) {

@@ -157,6 +157,11 @@ struct Builder {
   void add(int c, const std::string& lc, int a, const std::string& la, cplx alpha = 1.0) {
     Engine::add(P, c, lc, a, la, alpha);
   }
+  // b's label pairs (0,1) and (2,3) swap together without changing it
+  void ein_pairsym(int c, const std::string& lc, int a, const std::string& la, int bb, const std::string& lb,
+                   cplx alpha = 1.0) {
+    Engine::ein(P, c, lc, a, la, bb, lb, alpha, true);
+  }
 };
 
 // Closed-shell CCSD ket residual into views (r1 "zia", r2 "zijab").
@@ -222,7 +227,8 @@ int residual_ops(Builder& b, const IntIds* I, int t1, int t2, const OneBody& f, 
   if (two) {
     b.add(S, Q + "ijab", V(B::OOVV), "ijab", 0.5);
     // particle-particle ladder (half: the symmetrisation doubles it)
-    b.ein(S, Q + "ijab", tau, "zijef", V(B::VVVV), "abef", 0.5);
+    // (vvvv[a][b][e][f] = (ae|bf) is unchanged by a<->b together with e<->f)
+    b.ein_pairsym(S, Q + "ijab", tau, "zijef", V(B::VVVV), "abef", 0.5);
     // hole-hole ladder with W_mnij = <mn|ij> + P t1 terms + tau <mn|ef>
     const int Wmnij = b.tmp("Wmnij", {o, o, o, o});
     b.add(Wmnij, "zmnij", V(B::OOOO), "mnij");
