@@ -98,6 +98,12 @@ struct Compiled {
   AddDesc add{};
   std::vector<int> add_ops;   // CK_ADD: the program ops whose sources this kernel sums (first = own op)
   std::shared_ptr<Compiled> twin;   // pair-symmetric contraction: the antisymmetric-part GEMM
+  // pack sharing within a program: an operand packed identically by an earlier GEMM (source
+  // unchanged in between) reuses that GEMM's planes; the earlier one then packs into its own buffer
+  bool pa_keep = false, pb_keep = false;
+  const Compiled* pa_from = nullptr;
+  const Compiled* pb_from = nullptr;
+  bool pa_from_b = false, pb_from_b = false;   // the provider's B (true) or A (false) planes
   DirectDesc dir{};
   long long splits = 1;
   // GEMM path
@@ -662,6 +668,98 @@ void Engine::plan(Program& P) {
     P.comp.push_back(cp);
   }
   merge_adds(P);
+  share_packs(P);
+}
+
+namespace {
+// Byte image of every field of a pack that decides its output (not the destination).
+std::string pack_key(const PackDesc& d) {
+  std::string k;
+  auto put = [&](const void* p, size_t n) { k.append(static_cast<const char*>(p), n); };
+  auto put_map = [&](const IndexMap& m) {
+    put(&m.n, sizeof m.n);
+    put(m.dims, sizeof(int) * m.n);
+    put(m.strides, sizeof(long long) * m.n);
+  };
+  put(&d.src, sizeof d.src);
+  put(&d.src_cplx, sizeof d.src_cplx);
+  put(&d.src_f32, sizeof d.src_f32);
+  put_map(d.rows);
+  put_map(d.cols);
+  put_map(d.bat);
+  put(&d.R, sizeof d.R);
+  put(&d.K, sizeof d.K);
+  put(&d.NB, sizeof d.NB);
+  put(&d.nrb, sizeof d.nrb);
+  put(&d.ncs, sizeof d.ncs);
+  put(&d.nss, sizeof d.nss);
+  put(d.comp, sizeof d.comp);
+  put(d.sign, sizeof d.sign);
+  put(d.part, sizeof d.part);
+  put(d.rb_part, sizeof d.rb_part);
+  put(&d.Kpad, sizeof d.Kpad);
+  put(&d.elem, sizeof d.elem);
+  put(&d.round_tf32, sizeof d.round_tf32);
+  put(&d.transpose, sizeof d.transpose);
+  if (d.transpose) {
+    put_map(d.rd_src);
+    put_map(d.rd_dst);
+  }
+  put(&d.ktab, sizeof d.ktab);
+  put(&d.kw, sizeof d.kw);
+  put(&d.ksign, sizeof d.ksign);
+  put(&d.rtab, sizeof d.rtab);
+  return k;
+}
+}  // namespace
+
+// A non-constant tensor-core operand packed by an earlier GEMM of the same program with an
+// identical pack, whose source no op in between (nor that GEMM itself) has written, is not
+// packed again: the later GEMM reads the earlier one's planes.
+void Engine::share_packs(Program& P) {
+  const size_t n = P.ops.size();
+  auto range = [&](int id) {
+    const Tensor& t = tensors_[id];
+    long long hi = 1;
+    for (size_t q = 0; q < t.dims.size(); ++q) hi += (long long)(t.dims[q] - 1) * std::llabs(t.strides[q]);
+    const char* b = reinterpret_cast<const char*>(t.ptr);
+    return std::make_pair(b, b + hi * (long long)t.esz());
+  };
+  auto overlaps = [&](int x, int y) {
+    const auto a = range(x), b = range(y);
+    return a.first < b.second && b.first < a.second;
+  };
+  for (size_t i = 0; i < n; ++i) {
+    Compiled& k = *P.comp[i];
+    if (k.kind != CK_GEMM || k.tc_kind < 0 || k.twin) continue;
+    for (int side = 0; side < 2; ++side) {
+      const bool cst = side ? k.b_const : k.a_const;
+      if (cst) continue;
+      const PackDesc& pd = side ? k.pb : k.pa;
+      const int src = side ? P.ops[i].b : P.ops[i].a;
+      const std::string key = pack_key(pd);
+      for (size_t j = i; j-- > 0;) {
+        // the source must not change between the provider's pack and this one
+        if (P.comp[j]->kind != CK_MERGED && overlaps(P.ops[j].c, src)) break;
+        Compiled& g = *P.comp[j];
+        if (g.kind != CK_GEMM || g.tc_kind < 0 || g.twin) continue;
+        bool hit = false, from_b = false;
+        if (!g.a_const && !g.pa_from && pack_key(g.pa) == key) hit = true;
+        else if (!g.b_const && !g.pb_from && pack_key(g.pb) == key) hit = from_b = true;
+        if (!hit) continue;
+        if (from_b) g.pb_keep = true;
+        else g.pa_keep = true;
+        if (side) {
+          k.pb_from = &g;
+          k.pb_from_b = from_b;
+        } else {
+          k.pa_from = &g;
+          k.pa_from_b = from_b;
+        }
+        break;
+      }
+    }
+  }
 }
 
 // Source `oi` (an add into the output of kernel k) expressed in the labels `lc` that k uses for
@@ -775,23 +873,29 @@ void Engine::bind_gemm(Compiled& k, const Tensor& A, const Tensor& B, const Tens
   k.pa.src = A.ptr;
   k.pb.src = B.ptr;
   k.up.C = C.ptr;
+  auto own = [&](size_t bytes) {
+    void* p = dev_alloc(bytes);
+    allocs_.push_back(p);
+    bytes_ += bytes;
+    return p;
+  };
   if (k.a_const) {
-    k.a_pre = dev_alloc(k.a_bytes);
-    allocs_.push_back(k.a_pre);
-    bytes_ += k.a_bytes;
+    k.a_pre = own(k.a_bytes);
     k.pa.dst = k.a_pre;
     launch_pack(k.pa, stream_);
+  } else if (k.pa_from) {
+    k.pa.dst = k.pa_from_b ? k.pa_from->pb.dst : k.pa_from->pa.dst;
   } else {
-    k.pa.dst = wsA_;
+    k.pa.dst = k.pa_keep ? own(k.a_bytes) : wsA_;
   }
   if (k.b_const) {
-    k.b_pre = dev_alloc(k.b_bytes);
-    allocs_.push_back(k.b_pre);
-    bytes_ += k.b_bytes;
+    k.b_pre = own(k.b_bytes);
     k.pb.dst = k.b_pre;
     launch_pack(k.pb, stream_);
+  } else if (k.pb_from) {
+    k.pb.dst = k.pb_from_b ? k.pb_from->pb.dst : k.pb_from->pa.dst;
   } else {
-    k.pb.dst = wsB_;
+    k.pb.dst = k.pb_keep ? own(k.b_bytes) : wsB_;
   }
   k.up.gout = wsC_;
   if (k.tc_kind >= 0) {
@@ -1043,13 +1147,13 @@ void Engine::run(const Program& P) {
 
 void Engine::run_gemm(const Compiled& k, Profiler& pr, const char* tag) {
   const double esz = (k.pa.elem == PE_F64) ? 8 : (k.pa.elem == PE_F32 ? 4 : 2);
-  if (!k.a_const) {
+  if (!k.a_const && !k.pa_from) {
     pr.start(stream_);
     launch_pack(k.pa, stream_);
     pr.stop(stream_, KC_PACK, 0.0,
             (double)k.NB * k.pa.R * k.pa.K * (k.pa.src_cplx ? 2 : 1) * (k.pa.src_f32 ? 4 : 8) + (double)k.NB * k.GM * k.Kpad * esz, tag);
   }
-  if (!k.b_const) {
+  if (!k.b_const && !k.pb_from) {
     pr.start(stream_);
     launch_pack(k.pb, stream_);
     pr.stop(stream_, KC_PACK, 0.0,
@@ -1083,7 +1187,7 @@ EngineStats Engine::stats_of(const Program& P) const {
       s.gemm_flops += cp->alg_flops;
       // packs of non-constant operands, the GEMM, and the unpack of the float64 SIMT path
       for (const Compiled* g = cp.get(); g; g = g->twin.get())
-        s.launches += (g->tc_kind >= 0 ? 1 : 2) + (g->a_const ? 0 : 1) + (g->b_const ? 0 : 1);
+        s.launches += (g->tc_kind >= 0 ? 1 : 2) + (g->a_const || g->pa_from ? 0 : 1) + (g->b_const || g->pb_from ? 0 : 1);
     } else {
       s.direct_flops += cp->alg_flops;
       s.launches += 1;

@@ -151,6 +151,7 @@ class Engine {
   const long long* upload(const std::vector<long long>& v);
   const float* upload(const std::vector<float>& v);
   void merge_adds(Program& P);
+  void share_packs(Program& P);
 
   Prec prec_;
   cudaStream_t stream_;
