@@ -687,6 +687,88 @@ __global__ void reduce_kernel(DirectDesc d, long long chunk) {
   }
 }
 
+// Few outputs, long K (M, N <= 32 per batch entry; reduced-precision programs): a block owns one
+// batch entry and one K range; per 64-wide K chunk it stages A[m][k] and B[n][k] (float32,
+// complex) in shared memory with the chunk's k offsets decoded once, every thread accumulates up
+// to four of the M x N outputs, and the block adds its partial sums atomically at the end.
+constexpr int kSmallMN = 32, kSmallKC = 64;
+__global__ void __launch_bounds__(256) smallmn_kernel(DirectDesc d, long long kper) {
+  __shared__ float2 sA[kSmallMN][kSmallKC + 1], sB[kSmallMN][kSmallKC + 1];
+  __shared__ long long s_ka[kSmallKC], s_kb[kSmallKC], s_am[kSmallMN], s_bn[kSmallMN];
+  const unsigned M = (unsigned)d.M, N = (unsigned)d.N, tid = threadIdx.x;
+  const unsigned bt = blockIdx.y;
+  const long long k0 = (long long)blockIdx.x * kper, k1 = min(d.K, k0 + kper);
+  if (tid < M) s_am[tid] = imap32(d.ab, bt) + imap32(d.am, tid);
+  if (tid >= 64 && tid - 64 < N) s_bn[tid - 64] = imap32(d.bb, bt) + imap32(d.bn, tid - 64);
+  float accr[4] = {0.f, 0.f, 0.f, 0.f}, acci[4] = {0.f, 0.f, 0.f, 0.f};
+  const unsigned nout = M * N;
+  for (long long kc = k0; kc < k1; kc += kSmallKC) {
+    __syncthreads();
+    if (tid < kSmallKC) {
+      const long long k = kc + tid;
+      s_ka[tid] = k < k1 ? imap32(d.ak, (unsigned)k) : -1;
+    } else if (tid < 2 * kSmallKC) {
+      const long long k = kc + tid - kSmallKC;
+      s_kb[tid - kSmallKC] = k < k1 ? imap32(d.bk, (unsigned)k) : -1;
+    }
+    __syncthreads();
+    for (unsigned idx = tid; idx < M * kSmallKC; idx += blockDim.x) {
+      const unsigned m = idx / kSmallKC, kk = idx % kSmallKC;
+      float xr = 0.f, xi = 0.f;
+      if (s_ka[kk] >= 0) ld_elem<float>(d.A, s_am[m] + s_ka[kk], d.a_cplx, d.a_f32, xr, xi);
+      sA[m][kk] = make_float2(xr, xi);
+    }
+    for (unsigned idx = tid; idx < N * kSmallKC; idx += blockDim.x) {
+      const unsigned n = idx / kSmallKC, kk = idx % kSmallKC;
+      float xr = 0.f, xi = 0.f;
+      if (s_kb[kk] >= 0) ld_elem<float>(d.B, s_bn[n] + s_kb[kk], d.b_cplx, d.b_f32, xr, xi);
+      sB[n][kk] = make_float2(xr, xi);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const unsigned o = tid + q * blockDim.x;
+      if (o >= nout) break;
+      const unsigned m = o / N, n = o - m * N;
+      float sr = accr[q], si = acci[q];
+#pragma unroll 8
+      for (int kk = 0; kk < kSmallKC; ++kk) {
+        const float2 a = sA[m][kk], b = sB[n][kk];
+        sr = fmaf(a.x, b.x, fmaf(-a.y, b.y, sr));
+        si = fmaf(a.x, b.y, fmaf(a.y, b.x, si));
+      }
+      accr[q] = sr;
+      acci[q] = si;
+    }
+  }
+  const float ar = (float)d.ar, ai = (float)d.ai;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const unsigned o = tid + q * blockDim.x;
+    if (o >= nout) break;
+    const unsigned m = o / N, n = o - m * N;
+    const long long off = imap32(d.cb, bt) + imap32(d.cm, m) + imap32(d.cn, n);
+    const float vr = ar * accr[q] - ai * acci[q], vi = ar * acci[q] + ai * accr[q];
+    if (d.c_f32) {
+      float* C = static_cast<float*>(d.C);
+      if (d.c_cplx) {
+        atomicAdd(&C[2 * off], vr);
+        atomicAdd(&C[2 * off + 1], vi);
+      } else {
+        atomicAdd(&C[off], vr);
+      }
+    } else {
+      double* C = static_cast<double*>(d.C);
+      if (d.c_cplx) {
+        atomicAdd(&C[2 * off], f32_to_f64_bits(vr));
+        atomicAdd(&C[2 * off + 1], f32_to_f64_bits(vi));
+      } else {
+        atomicAdd(&C[off], f32_to_f64_bits(vr));
+      }
+    }
+  }
+}
+
 // float64 SIMT GEMM: 64x64 tile, 16-deep K slices, 256 threads with 4x4 outputs each.
 __global__ void __launch_bounds__(256) dgemm_kernel(const double* __restrict__ A, const double* __restrict__ B,
                                                     double* __restrict__ C, int M, int N, int K, int splits,
@@ -823,6 +905,19 @@ void launch_direct(const DirectDesc& d, cudaStream_t s) {
   dim3 grid((N + bx - 1) / bx, (unsigned)std::min((NR + 31) / 32, 65535ll));
   if (d.f32) direct_kernel<true><<<grid, blk, 0, s>>>(d);
   else direct_kernel<false><<<grid, blk, 0, s>>>(d);
+  RTCC_CUDA(cudaGetLastError());
+}
+void launch_smallmn(const DirectDesc& d, cudaStream_t s) {
+  RTCC_REQUIRE(d.M <= kSmallMN && d.N <= kSmallMN && d.M * d.N <= 1024 && d.NB < 65536 && d.K < (1ll << 31),
+               "small-output reduction extents");
+  if (d.NB * d.M * d.N == 0 || d.K == 0) return;
+  // about four blocks per SM in total, whole 64-wide chunks per block
+  long long splits = std::max(1ll, std::min((152ll * 4 + d.NB - 1) / d.NB, (d.K + kSmallKC - 1) / kSmallKC));
+  long long kper = (d.K + splits - 1) / splits;
+  kper = (kper + kSmallKC - 1) / kSmallKC * kSmallKC;
+  splits = (d.K + kper - 1) / kper;
+  dim3 grid((unsigned)splits, (unsigned)d.NB);
+  smallmn_kernel<<<grid, 256, 0, s>>>(d, kper);
   RTCC_CUDA(cudaGetLastError());
 }
 void launch_reduce(const DirectDesc& d, long long splits, cudaStream_t s) {

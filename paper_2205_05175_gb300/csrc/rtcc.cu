@@ -4,6 +4,7 @@
 #include <vector>
 #include "../../include/rtcc.h"
 #include <cmath>
+#include <type_traits>
 #include <cstring>
 #include <memory>
 #include <cstdio>
@@ -93,55 +94,93 @@ struct StageArgs {
 
 // y_out = y + h_z * sum_j coef_j * D R_j, with D = -i on the T part and +i on the Lambda part
 // (dt/dt = -i Omega, dl/dt = +i R).  Optionally saves the newest right-hand side.
+// F32 (reduced-precision handles, whose right-hand sides resolve far less than float32): the
+// weighted sum of the right-hand sides is formed in float32 from integer-rounded values and only
+// y + h * increment is float64, which keeps the kernel off the float64 pipe; otherwise float64.
+template <bool F32>
 __global__ void k_stage(double* __restrict__ yout, const double* __restrict__ y, StageArgs A, const double* hz,
                         long long ns, long long nT) {
+  using R = typename std::conditional<F32, float, double>::type;
   const int z = blockIdx.y;
   const double h = hz[z];
   const size_t base = (size_t)z * ns;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ns; k += (long long)gridDim.x * blockDim.x) {
-    const size_t q = 2 * (base + k);
-    double sr = 0.0, si = 0.0;
+    const size_t e = base + k;
+    R sr = 0, si = 0;
     for (int j = 0; j < A.nterms; ++j) {
-      sr += A.coef[j] * A.R[j][q];
-      si += A.coef[j] * A.R[j][q + 1];
+      const double2 rv = reinterpret_cast<const double2*>(A.R[j])[e];
+      const R c = (R)A.coef[j];
+      if constexpr (F32) {
+        sr = fmaf(c, f64_to_f32_bits(rv.x), sr);
+        si = fmaf(c, f64_to_f32_bits(rv.y), si);
+      } else {
+        sr += c * rv.x;
+        si += c * rv.y;
+      }
     }
-    if (A.copy_dst) {
-      A.copy_dst[q] = A.copy_src[q];
-      A.copy_dst[q + 1] = A.copy_src[q + 1];
-    }
+    if (A.copy_dst) reinterpret_cast<double2*>(A.copy_dst)[e] = reinterpret_cast<const double2*>(A.copy_src)[e];
     // D * s: -i (sr + i si) = si - i sr ; +i (sr + i si) = -si + i sr
-    const double dr = (k < nT) ? si : -si;
-    const double di = (k < nT) ? -sr : sr;
-    yout[q] = y[q] + h * dr;
-    yout[q + 1] = y[q + 1] + h * di;
+    double dr, di;
+    if constexpr (F32) {
+      dr = f32_to_f64_bits((k < nT) ? si : -si);
+      di = f32_to_f64_bits((k < nT) ? -sr : sr);
+    } else {
+      dr = (k < nT) ? si : -si;
+      di = (k < nT) ? -sr : sr;
+    }
+    const double2 yv = reinterpret_cast<const double2*>(y)[e];
+    reinterpret_cast<double2*>(yout)[e] = make_double2(yv.x + h * dr, yv.y + h * di);
   }
 }
 
 // Final combination: ynew = y + h sum b_j D R_j; err_z = max |h sum e_j R_j|; non-finite -> +inf.
+// F32 as in k_stage; the error estimate then also sums in float32 (it only steers the step size).
+template <bool F32>
 __global__ void k_final(double* __restrict__ ynew, const double* __restrict__ y, StageArgs B, StageArgs Ew,
                         const double* hz, long long ns, long long nT, unsigned long long* err_bits, int adaptive) {
+  using R = typename std::conditional<F32, float, double>::type;
   const int z = blockIdx.y;
   const double h = hz[z];
   const size_t base = (size_t)z * ns;
   double emax = 0.0;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ns; k += (long long)gridDim.x * blockDim.x) {
-    const size_t q = 2 * (base + k);
-    double sr = 0.0, si = 0.0, er = 0.0, ei = 0.0;
+    const size_t e = base + k;
+    R sr = 0, si = 0, er = 0, ei = 0;
     for (int j = 0; j < B.nterms; ++j) {
-      const double rr = B.R[j][q], ri = B.R[j][q + 1];
-      sr += B.coef[j] * rr;
-      si += B.coef[j] * ri;
+      const double2 rv = reinterpret_cast<const double2*>(B.R[j])[e];
+      R rr, ri;
+      if constexpr (F32) {
+        rr = f64_to_f32_bits(rv.x);
+        ri = f64_to_f32_bits(rv.y);
+      } else {
+        rr = rv.x;
+        ri = rv.y;
+      }
+      const R bc = (R)B.coef[j];
+      sr += bc * rr;
+      si += bc * ri;
       if (adaptive) {
-        er += Ew.coef[j] * rr;
-        ei += Ew.coef[j] * ri;
+        const R ec = (R)Ew.coef[j];
+        er += ec * rr;
+        ei += ec * ri;
       }
     }
-    const double dr = (k < nT) ? si : -si;
-    const double di = (k < nT) ? -sr : sr;
-    const double yr = y[q] + h * dr, yi = y[q + 1] + h * di;
-    ynew[q] = yr;
-    ynew[q + 1] = yi;
-    double ek = adaptive ? h * sqrt(er * er + ei * ei) : 0.0;
+    double dr, di;
+    if constexpr (F32) {
+      dr = f32_to_f64_bits((k < nT) ? si : -si);
+      di = f32_to_f64_bits((k < nT) ? -sr : sr);
+    } else {
+      dr = (k < nT) ? si : -si;
+      di = (k < nT) ? -sr : sr;
+    }
+    const double2 yv = reinterpret_cast<const double2*>(y)[e];
+    const double yr = yv.x + h * dr, yi = yv.y + h * di;
+    reinterpret_cast<double2*>(ynew)[e] = make_double2(yr, yi);
+    double ek = 0.0;
+    if (adaptive) {
+      if constexpr (F32) ek = (double)((float)h * sqrtf(er * er + ei * ei));
+      else ek = h * sqrt(er * er + ei * ei);
+    }
     if (!isfinite(yr) || !isfinite(yi) || !isfinite(ek)) ek = INFINITY;
     emax = fmax(emax, ek);
   }
@@ -618,7 +657,8 @@ void run_attempt(rtcc_ctx* h, const Tableau& tb, const rtcc_integrator_t& in, do
       A.copy_dst = h->Rk[st - 1];
     }
     pr.start(s);
-    k_stage<<<gst, 256, 0, s>>>(h->Ys, h->Y, A, h->ctl.htry, ns, nT);
+    if (h->prec != Prec::P64) k_stage<true><<<gst, 256, 0, s>>>(h->Ys, h->Y, A, h->ctl.htry, ns, nT);
+    else k_stage<false><<<gst, 256, 0, s>>>(h->Ys, h->Y, A, h->ctl.htry, ns, nT);
     pr.stop(s, KC_RK, 0, sb * (A.nterms + 2 + (st > 0 ? 1 : 0)));
     pr.start(s);
     k_fock<<<dim3(blocks_for((long long)h->nmo * h->nmo), nz), 256, 0, s>>>(h->F, h->f0, h->mu, h->d_fields, h->ctl.t,
@@ -635,7 +675,10 @@ void run_attempt(rtcc_ctx* h, const Tableau& tb, const rtcc_integrator_t& in, do
   }
   B.nterms = tb.s;
   pr.start(s);
-  k_final<<<gst, 256, 0, s>>>(h->Ynew, h->Y, B, Ew, h->ctl.htry, ns, nT, h->ctl.err_bits, tb.adaptive ? 1 : 0);
+  if (h->prec != Prec::P64)
+    k_final<true><<<gst, 256, 0, s>>>(h->Ynew, h->Y, B, Ew, h->ctl.htry, ns, nT, h->ctl.err_bits, tb.adaptive ? 1 : 0);
+  else
+    k_final<false><<<gst, 256, 0, s>>>(h->Ynew, h->Y, B, Ew, h->ctl.htry, ns, nT, h->ctl.err_bits, tb.adaptive ? 1 : 0);
   pr.stop(s, KC_RK, 0, sb * (tb.s + 2));
   pr.start(s);
   k_controller<<<(nz + 127) / 128, 128, 0, s>>>(h->ctl, in, nz);
@@ -848,7 +891,7 @@ void adj_stage(rtcc_ctx* h, AdjointEngine* a, const Tableau& tb, const double* y
     A.coef[A.nterms] = tb.a[st][j];
     ++A.nterms;
   }
-  k_stage<<<gst, 256, 0, s>>>(a->Ys, y, A, a->hdev, ns, nT);
+  k_stage<false><<<gst, 256, 0, s>>>(a->Ys, y, A, a->hdev, ns, nT);
   k_fock<<<dim3(blocks_for((long long)h->nmo * h->nmo), nz), 256, 0, s>>>(a->F, h->f0, h->mu, h->d_fields, a->tdev,
                                                                          a->hdev, tb.c[st], nz, h->nmo * h->nmo);
   a->E->run(a->rhs.fwd);
@@ -871,7 +914,7 @@ void adj_step(rtcc_ctx* h, AdjointEngine* a, const Tableau& tb, const double* y,
   }
   B.nterms = 4;
   const dim3 gst(blocks_for(h->ns) / h->nz + 1 > 4096 ? 4096 : blocks_for(h->ns) / h->nz + 1, h->nz);
-  k_final<<<gst, 256, 0, s>>>(ynew, y, B, Ew, a->hdev, h->ns, h->nT, h->ctl.err_bits, 0);
+  k_final<false><<<gst, 256, 0, s>>>(ynew, y, B, Ew, a->hdev, h->ns, h->nT, h->ctl.err_bits, 0);
   RTCC_CUDA(cudaGetLastError());
 }
 
