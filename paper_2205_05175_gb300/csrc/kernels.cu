@@ -689,8 +689,8 @@ __global__ void reduce_kernel(DirectDesc d, long long chunk) {
 
 // Few outputs, long K (M, N <= 32 per batch entry; reduced-precision programs): a block owns one
 // batch entry and one K range; per 64-wide K chunk it stages A[m][k] and B[n][k] (float32,
-// complex) in shared memory with the chunk's k offsets decoded once, every thread accumulates up
-// to four of the M x N outputs, and the block adds its partial sums atomically at the end.
+// complex) in shared memory with the chunk's k offsets decoded once, every thread accumulates a
+// 2 x 2 block of the M x N outputs, and the block adds its partial sums atomically at the end.
 constexpr int kSmallMN = 32, kSmallKC = 64;
 __global__ void __launch_bounds__(256) smallmn_kernel(DirectDesc d, long long kper) {
   __shared__ float2 sA[kSmallMN][kSmallKC + 1], sB[kSmallMN][kSmallKC + 1];
@@ -700,8 +700,13 @@ __global__ void __launch_bounds__(256) smallmn_kernel(DirectDesc d, long long kp
   const long long k0 = (long long)blockIdx.x * kper, k1 = min(d.K, k0 + kper);
   if (tid < M) s_am[tid] = imap32(d.ab, bt) + imap32(d.am, tid);
   if (tid >= 64 && tid - 64 < N) s_bn[tid - 64] = imap32(d.bb, bt) + imap32(d.bn, tid - 64);
-  float accr[4] = {0.f, 0.f, 0.f, 0.f}, acci[4] = {0.f, 0.f, 0.f, 0.f};
-  const unsigned nout = M * N;
+  // each thread owns a 2 x 2 block of outputs (rows 2*mb, 2*mb+1; columns 2*nb, 2*nb+1), so every
+  // shared-memory operand it reads feeds two products
+  const unsigned nbn = (N + 1) / 2, mb = tid / nbn, nb = tid - mb * nbn;
+  const bool active = mb < (M + 1) / 2;
+  const unsigned m0 = 2 * mb, n0 = 2 * nb;
+  const unsigned m1 = min(m0 + 1, M - 1), n1 = min(n0 + 1, N - 1);   // clamped reads; writes masked
+  float cr[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, ci[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
   for (long long kc = k0; kc < k1; kc += kSmallKC) {
     __syncthreads();
     if (tid < kSmallKC) {
@@ -725,48 +730,48 @@ __global__ void __launch_bounds__(256) smallmn_kernel(DirectDesc d, long long kp
       sB[n][kk] = make_float2(xr, xi);
     }
     __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const unsigned o = tid + q * blockDim.x;
-      if (o >= nout) break;
-      const unsigned m = o / N, n = o - m * N;
-      float sr = accr[q], si = acci[q];
+    if (active) {
 #pragma unroll 8
       for (int kk = 0; kk < kSmallKC; ++kk) {
-        const float2 a = sA[m][kk], b = sB[n][kk];
-        sr = fmaf(a.x, b.x, fmaf(-a.y, b.y, sr));
-        si = fmaf(a.x, b.y, fmaf(a.y, b.x, si));
+        const float2 a[2] = {sA[m0][kk], sA[m1][kk]}, b[2] = {sB[n0][kk], sB[n1][kk]};
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            cr[i][j] = fmaf(a[i].x, b[j].x, fmaf(-a[i].y, b[j].y, cr[i][j]));
+            ci[i][j] = fmaf(a[i].x, b[j].y, fmaf(a[i].y, b[j].x, ci[i][j]));
+          }
       }
-      accr[q] = sr;
-      acci[q] = si;
     }
   }
+  if (!active) return;
   const float ar = (float)d.ar, ai = (float)d.ai;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const unsigned o = tid + q * blockDim.x;
-    if (o >= nout) break;
-    const unsigned m = o / N, n = o - m * N;
-    const long long off = imap32(d.cb, bt) + imap32(d.cm, m) + imap32(d.cn, n);
-    const float vr = ar * accr[q] - ai * acci[q], vi = ar * acci[q] + ai * accr[q];
-    if (d.c_f32) {
-      float* C = static_cast<float*>(d.C);
-      if (d.c_cplx) {
-        atomicAdd(&C[2 * off], vr);
-        atomicAdd(&C[2 * off + 1], vi);
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const unsigned m = m0 + i, n = n0 + j;
+      if (m >= M || n >= N) continue;
+      const long long off = imap32(d.cb, bt) + imap32(d.cm, m) + imap32(d.cn, n);
+      const float vr = ar * cr[i][j] - ai * ci[i][j], vi = ar * ci[i][j] + ai * cr[i][j];
+      if (d.c_f32) {
+        float* C = static_cast<float*>(d.C);
+        if (d.c_cplx) {
+          atomicAdd(&C[2 * off], vr);
+          atomicAdd(&C[2 * off + 1], vi);
+        } else {
+          atomicAdd(&C[off], vr);
+        }
       } else {
-        atomicAdd(&C[off], vr);
-      }
-    } else {
-      double* C = static_cast<double*>(d.C);
-      if (d.c_cplx) {
-        atomicAdd(&C[2 * off], f32_to_f64_bits(vr));
-        atomicAdd(&C[2 * off + 1], f32_to_f64_bits(vi));
-      } else {
-        atomicAdd(&C[off], f32_to_f64_bits(vr));
+        double* C = static_cast<double*>(d.C);
+        if (d.c_cplx) {
+          atomicAdd(&C[2 * off], f32_to_f64_bits(vr));
+          atomicAdd(&C[2 * off + 1], f32_to_f64_bits(vi));
+        } else {
+          atomicAdd(&C[off], f32_to_f64_bits(vr));
+        }
       }
     }
-  }
 }
 
 // float64 SIMT GEMM: 64x64 tile, 16-deep K slices, 256 threads with 4x4 outputs each.
