@@ -53,9 +53,12 @@ typedef enum {
     RTCC_ERR_UNSUPPORTED = 8    /* option not available in this build */
 } rtcc_status_t;
 
-/* Arithmetic of the residual contractions.  The propagated state, the RK
- * combinations, the error estimate, the controller and the dipole reduction are
- * float64 in every mode (Sec. 4.1 studies single vs double precision). */
+/* Arithmetic of the residual contractions.  The propagated state, the controller and the
+ * dipole reduction are float64 in every mode (Sec. 4.1 studies single vs double precision).
+ * In the three reduced modes the intermediates of the residual are stored as float32
+ * (complex64), small contractions and sums run in float32, and the RK stage combinations form
+ * the weighted sum of the right-hand sides (and the error estimate) in float32 before adding
+ * h times it to the float64 state; all of these resolve far more than the split products do. */
 typedef enum {
     RTCC_P64 = 0,         /* float64 contractions (SIMT DFMA) */
     RTCC_P32_TF32 = 1,    /* one TF32 tcgen05 pass, float32 accumulate */
