@@ -300,3 +300,43 @@ def test_matrix_pencil_recovers_frequencies():
     y = 0.3 * np.exp(-1j * 0.81 * k * dt) + 0.1 * np.exp(-1j * 1.37 * k * dt) + 0.05 * np.exp(1j * 0.81 * k * dt)
     w = np.sort(spectrum.matrix_pencil(y, dt, 3).real)
     assert np.allclose(w, [-0.81, 0.81, 1.37], atol=1e-9)
+
+
+# --- real-time spectrum peaks = EOM-CCSD excitation energies (Sec. 3: EOM-CCSD stick spectra) ----
+
+def _rt_modes(o, v, h, T):
+    """Strongest response frequencies of Re mu_z(t) after a weak kick, by matrix pencil, and the
+    eigenvalues of the CC Jacobian dOmega/dt (EOM-CCSD excitation energies) carried through the
+    RK4 map: a mode exp(-i w t) advances by R(-i w h) per step, R the RK4 stability polynomial."""
+    f, B, mu = synth.make_system(o, v, seed=7)
+    s = rk.RTCC(f, B, mu, o)
+    y0, _, _ = s.ground_state(tol=1e-12)
+    t1, t2, _, _ = rk.unpack(y0, o, v)
+    ev = np.linalg.eigvals(fci.jacobian(t1, t2, s.f, s.V)).real
+    z = -1j * ev * h
+    w_rk = 1j * np.log(1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24) / h
+    kick = rk.Field(E0=1e-4, omega=0.0, sigma=0.02, t0=0.1, carrier="cos")
+    tt, mm, _, _ = rk.propagate(s, y0, kick, rk.Integrator(method="rk4", h=h, nsteps=int(round(T / h))))
+    tt, mm = np.asarray(tt), np.asarray(mm)
+    y = mm[tt > 0.4, 2].real - mm[0, 2].real
+    N, L = len(y), len(y) // 2
+    sv = np.linalg.svd(np.array([y[i:i + L + 1] for i in range(N - L)]), compute_uv=False)
+    w = spectrum.matrix_pencil(y, h, int(np.sum(sv > 1e-6 * sv[0])))
+    c, *_ = np.linalg.lstsq(np.exp(-1j * np.outer(h * np.arange(N), w)), y.astype(complex), rcond=None)
+    strongest = [w[k] for k in np.argsort(-np.abs(c)) if w[k].real > 0]
+    return strongest, w_rk
+
+
+def test_rt_peaks_are_eom_ccsd_energies_two_electrons():
+    """Linear response of RT-CCSD oscillates at the Jacobian eigenvalues (for two electrons
+    these are the FCI excitation energies, pinned above)."""
+    strongest, w_rk = _rt_modes(1, 3, 0.05, 20.0)
+    for w in strongest[:4]:
+        assert np.min(np.abs(w_rk - w)) < 1e-6, w
+
+
+def test_rt_peaks_are_eom_ccsd_energies_four_electrons():
+    """Four electrons, where CCSD is not FCI: the strongest RT modes sit at EOM-CCSD energies."""
+    strongest, w_rk = _rt_modes(2, 3, 0.05, 40.0)
+    for w in strongest[:3]:
+        assert np.min(np.abs(w_rk - w)) < 2e-5, w
