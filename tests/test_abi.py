@@ -62,3 +62,16 @@ def test_no_cpu_fallback_in_product_package():
         if fn.endswith(".py"):
             src = open(os.path.join(pkg, fn)).read()
             assert "import oracle" not in src and "from oracle" not in src, fn
+
+
+def test_frozen_core_count_is_checked_before_any_device_work(lib):
+    import numpy as np
+    o, v = 2, 2
+    f = np.diag([-1.0, -0.5, 0.5, 1.0])
+    B = np.zeros((2, 4, 4))
+    mu = np.zeros((3, 4, 4))
+    for nfc in (-1, o, o + 3):
+        with pytest.raises(lib.RtccError) as e:
+            lib.Handle(f, B, mu, o, v, nfc=nfc)
+        assert e.value.status == "INVALID_ARG"
+        assert "frozen-core" in lib.rtcc_last_error()
