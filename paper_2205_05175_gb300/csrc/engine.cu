@@ -9,10 +9,11 @@ namespace rtcc {
 
 void launch_reduce(const DirectDesc& d, long long splits, cudaStream_t s);
 void launch_smallmn(const DirectDesc& d, cudaStream_t s);
+void launch_skinny(const DirectDesc& d, cudaStream_t s);
 
 namespace {
 
-enum CompKind : int { CK_ADD = 0, CK_DIRECT = 1, CK_REDUCE = 2, CK_GEMM = 3, CK_MERGED = 4, CK_SMALLMN = 5 };   // CK_MERGED: folded into an earlier add
+enum CompKind : int { CK_ADD = 0, CK_DIRECT = 1, CK_REDUCE = 2, CK_GEMM = 3, CK_MERGED = 4, CK_SMALLMN = 5, CK_SKINNY = 6 };   // CK_MERGED: folded into an earlier add
 
 constexpr long long kDirectMaxWork = 1ll << 21;   // real multiply-adds below which a term runs direct
 constexpr long long kReduceMaxOut = 2048;         // outputs up to which a long-K term is split-K reduced
@@ -454,6 +455,10 @@ void Engine::plan(Program& P) {
       d.store = c_fresh ? 1 : 0;
     } else if (force_gemm_) {
       k.kind = CK_GEMM;
+    } else if (prec != Prec::P64 && K <= 32 && N <= 32 && M >= 4096 && !Lm.empty() &&
+               A.strides[op.la.find(Lm.back())] == 1 && C.strides[op.lc.find(Lm.back())] == 1) {
+      k.kind = CK_SKINNY;   // short K, few columns, many unit-stride rows: one thread per row
+      d.store = c_fresh ? 1 : 0;
     } else if (prec != Prec::P64 && M <= 32 && N <= 32 && M * N <= 1024 && K >= 2048) {
       k.kind = CK_SMALLMN;   // few outputs per batch entry, long K: staged SIMT reduction
     } else if (nout <= kReduceMaxOut && K >= 256) {
@@ -1145,6 +1150,11 @@ void Engine::run(const Program& P) {
         pr.start(stream_);
         launch_smallmn(k.dir, stream_);
         pr.stop(stream_, KC_REDUCE, (double)k.alg_flops, 0.0, tag);
+        break;
+      case CK_SKINNY:
+        pr.start(stream_);
+        launch_skinny(k.dir, stream_);
+        pr.stop(stream_, KC_DIRECT, (double)k.alg_flops, 0.0, tag);
         break;
       default:
         run_gemm(k, pr, tag);

@@ -774,6 +774,81 @@ __global__ void __launch_bounds__(256) smallmn_kernel(DirectDesc d, long long kp
     }
 }
 
+// Short K and few columns (K, N <= 32; reduced-precision programs), many rows: one thread per
+// row m keeps A[m][0..K) in registers and forms its N outputs against B[n][k] staged in shared
+// memory (read as broadcasts); consecutive threads hold consecutive rows, so loads and the
+// atomic adds into C are coalesced along m.
+constexpr int kSkinny = 32;
+__global__ void __launch_bounds__(256) skinny_kernel(DirectDesc d) {
+  __shared__ __align__(16) float2 sB[kSkinny][kSkinny];
+  __shared__ long long s_ak[kSkinny], s_cn[kSkinny];
+  const unsigned bt = blockIdx.y, tid = threadIdx.x;
+  const int K = (int)d.K, N = (int)d.N;
+  for (unsigned idx = tid; idx < (unsigned)(N * kSkinny); idx += blockDim.x) {
+    const unsigned n = idx / kSkinny, k = idx - n * kSkinny;
+    float xr = 0.f, xi = 0.f;
+    if (k < (unsigned)K)
+      ld_elem<float>(d.B, imap32(d.bb, bt) + imap32(d.bn, n) + imap32(d.bk, k), d.b_cplx, d.b_f32, xr, xi);
+    sB[n][k] = make_float2(xr, xi);
+  }
+  if (tid < (unsigned)K) s_ak[tid] = imap32(d.ak, tid);
+  if (tid >= 64 && tid - 64 < (unsigned)N) s_cn[tid - 64] = imap32(d.cn, tid - 64);
+  __syncthreads();
+  const unsigned long long m = (unsigned long long)blockIdx.x * blockDim.x + tid;
+  if (m >= (unsigned long long)d.M) return;
+  const long long a0 = imap32(d.ab, bt) + imap32(d.am, (unsigned)m);
+  const long long c0 = imap32(d.cb, bt) + imap32(d.cm, (unsigned)m);
+  float2 a[kSkinny];
+#pragma unroll
+  for (int k = 0; k < kSkinny; ++k) {
+    a[k] = make_float2(0.f, 0.f);
+    if (k < K) ld_elem<float>(d.A, a0 + s_ak[k], d.a_cplx, d.a_f32, a[k].x, a[k].y);
+  }
+  const float ar = (float)d.ar, ai = (float)d.ai;
+  for (int n = 0; n < N; ++n) {
+    float sr = 0.f, si = 0.f;
+    // two complex B values per 16-byte shared-memory read (rows are zero-padded past K)
+    const float4* brow = reinterpret_cast<const float4*>(&sB[n][0]);
+#pragma unroll
+    for (int k2 = 0; k2 < kSkinny / 2; ++k2) {
+      if (2 * k2 < K) {
+        const float4 b = brow[k2];
+        sr = fmaf(a[2 * k2].x, b.x, fmaf(-a[2 * k2].y, b.y, sr));
+        si = fmaf(a[2 * k2].x, b.y, fmaf(a[2 * k2].y, b.x, si));
+        sr = fmaf(a[2 * k2 + 1].x, b.z, fmaf(-a[2 * k2 + 1].y, b.w, sr));
+        si = fmaf(a[2 * k2 + 1].x, b.w, fmaf(a[2 * k2 + 1].y, b.z, si));
+      }
+    }
+    const float vr = ar * sr - ai * si, vi = ar * si + ai * sr;
+    const long long off = c0 + s_cn[n];
+    if (d.c_f32) {
+      if (d.c_cplx) {
+        float2* c = static_cast<float2*>(d.C) + off;
+        if (d.store) *c = make_float2(vr, vi);
+        else atomicAdd(c, make_float2(vr, vi));
+      } else {
+        float* c = static_cast<float*>(d.C) + off;
+        if (d.store) *c = vr;
+        else atomicAdd(c, vr);
+      }
+    } else {
+      if (d.c_cplx) {
+        double2* c = static_cast<double2*>(d.C) + off;
+        if (d.store) {
+          *c = make_double2(f32_to_f64_bits(vr), f32_to_f64_bits(vi));
+        } else {
+          atomicAdd(&c->x, f32_to_f64_bits(vr));
+          atomicAdd(&c->y, f32_to_f64_bits(vi));
+        }
+      } else {
+        double* c = static_cast<double*>(d.C) + off;
+        if (d.store) *c = f32_to_f64_bits(vr);
+        else atomicAdd(c, f32_to_f64_bits(vr));
+      }
+    }
+  }
+}
+
 // float64 SIMT GEMM: 64x64 tile, 16-deep K slices, 256 threads with 4x4 outputs each.
 __global__ void __launch_bounds__(256) dgemm_kernel(const double* __restrict__ A, const double* __restrict__ B,
                                                     double* __restrict__ C, int M, int N, int K, int splits,
@@ -910,6 +985,14 @@ void launch_direct(const DirectDesc& d, cudaStream_t s) {
   dim3 grid((N + bx - 1) / bx, (unsigned)std::min((NR + 31) / 32, 65535ll));
   if (d.f32) direct_kernel<true><<<grid, blk, 0, s>>>(d);
   else direct_kernel<false><<<grid, blk, 0, s>>>(d);
+  RTCC_CUDA(cudaGetLastError());
+}
+void launch_skinny(const DirectDesc& d, cudaStream_t s) {
+  RTCC_REQUIRE(d.K >= 1 && d.K <= kSkinny && d.N >= 1 && d.N <= kSkinny && d.M < (1ll << 31) && d.NB < 65536,
+               "short-K contraction extents");
+  if (d.M == 0) return;
+  dim3 grid((unsigned)((d.M + 255) / 256), (unsigned)d.NB);
+  skinny_kernel<<<grid, 256, 0, s>>>(d);
   RTCC_CUDA(cudaGetLastError());
 }
 void launch_smallmn(const DirectDesc& d, cudaStream_t s) {

@@ -18,11 +18,12 @@ def _oracle_rhs(f, B, mu, o, y, fld, t):
     return s.rhs(t, y, fld)
 
 
-@pytest.mark.parametrize("o,v,ntraj", [(2, 5, 1), (3, 7, 2), (5, 19, 1), (3, 30, 2)])
+@pytest.mark.parametrize("o,v,ntraj", [(2, 5, 1), (3, 7, 2), (5, 19, 1), (3, 30, 2), (5, 30, 1)])
 @pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_rhs_parity(o, v, ntraj, prec):
     """(3, 30): contractions over o*v*v >= 2048 indices into o x o outputs take the staged
-    small-output reduction in the reduced-precision modes."""
+    small-output reduction in the reduced-precision modes; (5, 30): products with K = N = o over
+    o*v*v >= 4096 rows take the one-thread-per-row kernel."""
     from paper_2205_05175_gb300 import rtcc
     f, B, mu = system(o, v)
     fields, times, ys, refs = [], [], [], []
