@@ -1,10 +1,16 @@
-// Layout and small-contraction kernels of the contraction engine:
-//   pack    : strided float64 tensor (real or complex) -> K-major GEMM operand
-//             (float32 rounded to TF32, bf16, or float64), with re/im stacking, the
-//             [[Ar,-Ai],[Ai,Ar]] complex embedding and hi/lo precision splits
-//   unpack  : GEMM output -> C[...] += alpha * (re + i im) at strided positions
-//   direct  : C[...] += alpha * sum_k A B for small contractions, float64 throughout
-//   add     : C[...] += alpha * A[...] (permute / broadcast)
+// Layout and small-contraction kernels of the contraction engine.  Tensors hold float64
+// (complex128) or, for the temporaries of reduced-precision engines, float32 (complex64)
+// elements; reduced-precision programs compute in float32 with integer-rounded operands.
+//   pack    : strided tensor (real or complex) -> K-major GEMM operand (float32 rounded to
+//             TF32, bf16, or float64), with re/im planes, hi/lo precision splits, the
+//             [[Ar,-Ai],[Ai,Ar]] complex embedding of the float64 path, and gather tables for
+//             the pair-symmetric contraction
+//   unpack  : float64 GEMM output -> C[...] += alpha * (re + i im) at strided positions
+//   direct  : C[...] (+)= alpha * sum_k A B for small contractions and outer products
+//   reduce  : few outputs, long K: split-K block reduction (float64) or the staged
+//             shared-memory reduction (float32, 2 x 2 outputs per thread)
+//   skinny  : short K and few columns over many rows: one thread per row
+//   add     : C[...] (+)= sum_s alpha_s * A_s[...] (permute / broadcast, up to four sources)
 //   dgemm   : float64 SIMT GEMM for the float64 precision mode
 #include "common.cuh"
 #include <cuda_bf16.h>
