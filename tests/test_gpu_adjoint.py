@@ -1,6 +1,7 @@
 """Adjoint gradients dJ/d(E0, omega, sigma) of J = sum_n w_n . Re mu(t_n) through RK4
 (rtcc_propagate_vjp) against central finite differences (delta = 1e-5) of the float64 forward
-propagation, on the GPU and with the CPU oracle, and through torch.autograd."""
+propagation, on the GPU and with the CPU oracle, against the oracle's forward-mode tangent, and
+through torch.autograd."""
 import numpy as np
 import pytest
 
@@ -75,6 +76,10 @@ def test_vjp_matches_oracle_finite_differences():
                                ckpt_every=25)
     assert abs(J[0] - J_oracle(theta)) < 1e-11
     assert np.abs(g[0] - fd).max() < 2e-6 * np.abs(fd).max()
+    # the oracle's forward tangent differentiates the same discrete RK4 map exactly
+    from oracle import tangent
+    _, gt = tangent.tangent_gradient(s, y0, rk.Field(E0=theta[0], omega=theta[1], sigma=theta[2], t0=1.0), h, nsteps, w)
+    assert np.abs(g[0] - gt).max() < 1e-7 * np.abs(gt).max()
 
 
 def test_autograd_function_backward():

@@ -340,3 +340,30 @@ def test_rt_peaks_are_eom_ccsd_energies_four_electrons():
     strongest, w_rk = _rt_modes(2, 3, 0.05, 40.0)
     for w in strongest[:3]:
         assert np.min(np.abs(w_rk - w)) < 2e-5, w
+
+
+# --- adjoint reference: forward-mode tangent of the RK4 propagation -------------------------
+
+def test_tangent_gradient_matches_central_differences():
+    """The oracle's forward tangent (exact five-point JVPs, analytic dA/dtheta) against central
+    differences (delta 1e-5) of its own RK4 propagation; J itself must coincide."""
+    from oracle import tangent
+    o, v = 2, 5
+    f, B, mu = synth.make_system(o, v)
+    h, nsteps = 0.05, 20
+    t = h * np.arange(nsteps + 1)
+    w = np.zeros((nsteps + 1, 3))
+    w[:, 0] = np.exp(-0.5 * (t - 0.6) ** 2 / 0.3 ** 2)
+    theta = np.array([0.08, 0.7, 0.4])
+    s = rk.RTCC(f, B, mu, o)
+    y0, _, _ = s.ground_state(tol=1e-12)
+
+    def J(th):
+        fld = rk.Field(E0=th[0], omega=th[1], sigma=th[2], t0=1.0)
+        _, m, _, _ = rk.propagate(s, y0, fld, rk.Integrator(method="rk4", h=h, nsteps=nsteps))
+        return float(np.sum(w * m.real))
+
+    fd = np.array([(J(theta + d) - J(theta - d)) / 2e-5 for d in 1e-5 * np.eye(3)])
+    Jt, g = tangent.tangent_gradient(s, y0, rk.Field(E0=theta[0], omega=theta[1], sigma=theta[2], t0=1.0), h, nsteps, w)
+    assert abs(Jt - J(theta)) < 1e-12 * abs(Jt)
+    assert np.abs(g - fd).max() < 1e-7 * np.abs(fd).max()
