@@ -100,7 +100,7 @@ typedef struct {
 
 typedef struct rtcc_ctx* rtcc_handle_t;
 
-/* Create a handle (Sec. 3; Sec. 4.3 integral residency).
+/* Create a handle (Sec. 3; Sec. 4.1 describes the per-term integral uploads this replaces with residency).
  *  f   : host, nmo*nmo float64, symmetric field-free Fock matrix.
  *  B   : host, naux*nmo*nmo float64, density-fitting factors symmetric in the last two
  *        indices; the library forms (pq|rs) = sum_P B[P][p][q] B[P][r][s] on the device
@@ -191,7 +191,7 @@ rtcc_status_t rtcc_propagate_vjp(rtcc_handle_t h, const rtcc_field_t* fields, do
 rtcc_status_t rtcc_last_stats(rtcc_handle_t h, long long* accepted, long long* rejected,
                               long long* rhs_evals, long long* launches);
 
-/* Launch profile (Sec. 4.3 reports time per step; this splits it by kernel class).
+/* Launch profile (Sec. 4.1 reports time per step; this splits it by kernel class).
  * Class index: 0 tcgen05 GEMM, 1 float64 GEMM, 2 pack, 3 unpack, 4 direct contraction,
  * 5 split-K reduction, 6 add/permute, 7 Runge-Kutta/field/controller kernels.
  * flops: algorithmic real flops of the launches (GEMMs: 2 x rows x cols x unpadded K of the
