@@ -192,8 +192,9 @@ rtcc_status_t rtcc_last_stats(rtcc_handle_t h, long long* accepted, long long* r
                               long long* rhs_evals, long long* launches);
 
 /* Launch profile (Sec. 4.1 reports time per step; this splits it by kernel class).
- * Class index: 0 tcgen05 GEMM, 1 float64 GEMM, 2 pack, 3 unpack, 4 direct contraction,
- * 5 split-K reduction, 6 add/permute, 7 Runge-Kutta/field/controller kernels.
+ * Class index: 0 tcgen05 GEMM, 1 float64 GEMM, 2 pack, 3 unpack, 4 direct contraction
+ * (small terms, outer products, short-K row kernel), 5 reductions over a long K (split-K and
+ * staged few-output kernels), 6 add/permute, 7 Runge-Kutta/field/controller kernels.
  * flops: algorithmic real flops of the launches (GEMMs: 2 x rows x cols x unpadded K of the
  * packed product); bytes: algorithmic bytes moved (memory-bound classes). */
 typedef struct {
