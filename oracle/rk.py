@@ -20,6 +20,9 @@ Test infrastructure only: nothing on the product path imports this module.
   land on t_end.
 * Mixed-step RK4 (Sec. 4.2): h1 while t < t_switch (the step that would cross
   t_switch is cut to land on it), h2 afterwards.
+* Implicit Gauss-Legendre RK (two stages, order 4; Sec. 1 lists implicit and symplectic
+  methods among the integrators for RT-CC without giving coefficients): the Gauss points and
+  collocation matrix of [0, 1]; the coupled stage equations are solved by fixed-point iteration.
 * Ground state: Jacobi updates t <- t + Omega/D, l <- l + R/D with
   D = f_ii(+f_jj) - f_aa(-f_bb) of the field-free Fock matrix, plus DIIS.
 """
@@ -50,6 +53,18 @@ CK_TABLE = {
           [Fr(1631, 55296), Fr(175, 512), Fr(575, 13824), Fr(44275, 110592), Fr(253, 4096)]],
     "b5": [Fr(37, 378), Fr(0), Fr(250, 621), Fr(125, 594), Fr(0), Fr(512, 1771)],
     "b4": [Fr(2825, 27648), Fr(0), Fr(18575, 48384), Fr(13525, 55296), Fr(277, 14336), Fr(1, 4)],
+}
+
+
+# Two-stage Gauss-Legendre collocation (implicit, order 4, A-stable and symplectic: the paper's
+# "library of integrators", Sec. 1, names implicit and symplectic Runge-Kutta methods without
+# coefficients).  Nodes are the Gauss points of [0, 1], c = 1/2 -+ sqrt(3)/6; A is the
+# collocation matrix; b = (1/2, 1/2).  Irrational, so kept in floating point.
+_SQ3_6 = np.sqrt(3.0) / 6.0
+GL2_TABLE = {
+    "c": [0.5 - _SQ3_6, 0.5 + _SQ3_6],
+    "a": [[0.25, 0.25 - _SQ3_6], [0.25 + _SQ3_6, 0.25]],
+    "b": [0.5, 0.5],
 }
 
 
@@ -192,6 +207,22 @@ class RTCC:
         ks = self.stages(tab, tt, y, h, fld)
         return y + h * sum(b * k for b, k in zip(tab["b"], ks))
 
+    def gl2_step(self, tt, y, h, fld, tol=1e-14, maxiter=200):
+        """One Gauss-Legendre step: the stage derivatives K_i = f(t + c_i h, y + h sum_j a_ij K_j)
+        (a fully implicit system) solved by fixed-point iteration from K_i = f(t, y)."""
+        c, a, b = GL2_TABLE["c"], GL2_TABLE["a"], GL2_TABLE["b"]
+        k0 = self.rhs(tt, y, fld)
+        K = [k0.copy(), k0.copy()]
+        for _ in range(maxiter):
+            Kn = [self.rhs(tt + c[i] * h, y + h * (a[i][0] * K[0] + a[i][1] * K[1]), fld) for i in range(2)]
+            delta = max(float(np.abs(Kn[i] - K[i]).max()) for i in range(2))
+            K = Kn
+            if delta <= tol * max(1.0, max(float(np.abs(k).max()) for k in K)):
+                break
+        else:
+            raise RuntimeError("implicit stages did not converge")
+        return y + h * (b[0] * K[0] + b[1] * K[1])
+
     def ck_attempt(self, tt, y, h, fld):
         tab = as_float(CK_TABLE)
         ks = self.stages(tab, tt, y, h, fld)
@@ -202,7 +233,7 @@ class RTCC:
 
 @dataclass
 class Integrator:
-    method: str = "rk4"          # "rk4", "ck", "mixed"
+    method: str = "rk4"          # "rk4", "ck", "mixed", "gl2" (implicit Gauss-Legendre)
     h: float = 0.05
     h1: float = 0.005
     h2: float = 0.05
@@ -233,14 +264,14 @@ def propagate(sys: RTCC, y0, fld: Field, integ: Integrator, t_start=0.0):
     times, mus = [tt], [sys.dipole(y)]
     stats = {"accepted": 0, "rejected": 0, "rhs_evals": 0}
     eps = 1e-12
-    if integ.method in ("rk4", "mixed"):
+    if integ.method in ("rk4", "mixed", "gl2"):
         step = 0
         while True:
             if integ.nsteps > 0 and step >= integ.nsteps:
                 break
             if integ.nsteps <= 0 and tt >= integ.t_end - eps:
                 break
-            if integ.method == "rk4":
+            if integ.method in ("rk4", "gl2"):
                 h = integ.h
             else:
                 h = integ.h1 if tt < integ.t_switch - eps else integ.h2
@@ -248,7 +279,7 @@ def propagate(sys: RTCC, y0, fld: Field, integ: Integrator, t_start=0.0):
                     h = min(h, integ.t_switch - tt)
             if integ.nsteps <= 0:
                 h = min(h, integ.t_end - tt)
-            y = sys.rk4_step(tt, y, h, fld)
+            y = sys.rk4_step(tt, y, h, fld) if integ.method != "gl2" else sys.gl2_step(tt, y, h, fld)
             tt = tt + h
             step += 1
             stats["accepted"] += 1

@@ -407,3 +407,78 @@ def test_pade_spectrum_resolves_peaks_from_a_short_record():
     Id = spectrum.spectrum(t, mu, om, (0, 0, 1), kappa=1.0, gamma=0.01)
     pd = [om[k] for k in range(1, len(om) - 1) if Id[k] > Id[k - 1] and Id[k] > Id[k + 1] and Id[k] > 0.2 * Id.max()]
     assert len(pd) < 2   # the plain transform of the same record does not separate them
+
+
+# --- implicit Gauss-Legendre RK (the paper's integrator library names implicit/symplectic RK) ---
+
+def test_gauss_legendre_tableau_is_the_exact_order_four_collocation():
+    sp = pytest.importorskip("sympy")
+    r = sp.sqrt(3) / 6
+    c = [sp.Rational(1, 2) - r, sp.Rational(1, 2) + r]
+    A = [[sp.Rational(1, 4), sp.Rational(1, 4) - r], [sp.Rational(1, 4) + r, sp.Rational(1, 4)]]
+    b = [sp.Rational(1, 2), sp.Rational(1, 2)]
+    tab = rk.GL2_TABLE
+    for i in range(2):
+        assert abs(tab["c"][i] - float(c[i])) < 1e-16 and abs(tab["b"][i] - float(b[i])) < 1e-16
+        for j in range(2):
+            assert abs(tab["a"][i][j] - float(A[i][j])) < 1e-16
+    # collocation: sum_j a_ij c_j^(k-1) = c_i^k / k (k = 1, 2); Gauss nodes: sum_i b_i c_i^(k-1) = 1/k, k <= 4
+    for i in range(2):
+        for k in (1, 2):
+            assert sp.simplify(sum(A[i][j] * c[j] ** (k - 1) for j in range(2)) - c[i] ** k / k) == 0
+    rng = range(2)
+    conds = [sum(b) - 1, sum(b[i] * c[i] for i in rng) - sp.Rational(1, 2),
+             sum(b[i] * c[i] ** 2 for i in rng) - sp.Rational(1, 3),
+             sum(b[i] * A[i][j] * c[j] for i in rng for j in rng) - sp.Rational(1, 6),
+             sum(b[i] * c[i] ** 3 for i in rng) - sp.Rational(1, 4),
+             sum(b[i] * c[i] * A[i][j] * c[j] for i in rng for j in rng) - sp.Rational(1, 8),
+             sum(b[i] * A[i][j] * c[j] ** 2 for i in rng for j in rng) - sp.Rational(1, 12),
+             sum(b[i] * A[i][j] * A[j][k] * c[k] for i in rng for j in rng for k in rng) - sp.Rational(1, 24)]
+    assert all(sp.simplify(x) == 0 for x in conds)
+    assert sp.simplify(sum(b[i] * c[i] ** 4 for i in rng) - sp.Rational(1, 5)) != 0   # not fifth order
+
+
+def test_gauss_legendre_is_unitary_for_hermitian_dynamics_and_fourth_order():
+    """For y' = -i H y with H Hermitian the Gauss-Legendre stability function (the diagonal Pade
+    approximant of exp) has modulus one on the imaginary axis: the norm is kept exactly, which
+    RK4 does not; the global error falls as h^4."""
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((6, 6)) + 1j * rng.standard_normal((6, 6))
+    H = (X + X.conj().T) / 2
+
+    class Lin(rk.RTCC):
+        def __init__(self):
+            pass
+
+        def rhs(self, tt, y, fld):
+            return -1j * (H @ y)
+
+    s = Lin()
+    y0 = rng.standard_normal(6) + 1j * rng.standard_normal(6)
+    w, U = np.linalg.eigh(H)
+    exact = U @ (np.exp(-1j * w * 2.0) * (U.conj().T @ y0))
+    errs = []
+    for h in (0.05, 0.025):
+        y, z = y0.copy(), y0.copy()
+        for n in range(int(round(2.0 / h))):
+            y = s.gl2_step(n * h, y, h, None)
+            z = s.rk4_step(n * h, z, h, None)
+        assert abs(np.linalg.norm(y) - np.linalg.norm(y0)) < 1e-12 * np.linalg.norm(y0)
+        assert abs(np.linalg.norm(z) - np.linalg.norm(y0)) > 1e-9 * np.linalg.norm(y0)
+        errs.append(np.abs(y - exact).max())
+    assert 14.0 < errs[0] / errs[1] < 18.0
+
+
+def test_gauss_legendre_rtcc_follows_fci_with_h4_error(two_electron):
+    """The implicit integrator on the RT-CC equations of motion: mu(t) -> FCI mu(t) (CCSD is
+    exact for two electrons) with the order-4 error ratio, like RK4."""
+    s, y0, _, F, _, psi0, _ = two_electron
+    fld = rk.Field(E0=0.05, omega=0.5, sigma=0.5, t0=1.0)
+    T = 2.0
+    _, mf = F.propagate(psi0, fld, T, 1e-4, 1000)
+    errs = []
+    for h in (0.1, 0.05):
+        _, mm, _, _ = rk.propagate(s, y0, fld, rk.Integrator(method="gl2", h=h, nsteps=int(round(T / h))))
+        errs.append(np.abs(mm[-1] - mf[-1]).max())
+    assert errs[1] < 1e-6
+    assert 10.0 < errs[0] / errs[1] < 25.0
