@@ -78,7 +78,7 @@ typedef struct {
     double sign;    /* +1 or -1 */
 } rtcc_field_t;
 
-typedef enum { RTCC_RK4 = 0, RTCC_CK = 1, RTCC_MIXED_RK4 = 2 } rtcc_method_t;
+typedef enum { RTCC_RK4 = 0, RTCC_CK = 1, RTCC_MIXED_RK4 = 2, RTCC_GL2 = 3 } rtcc_method_t;
 
 /* Integrator settings (Sec. 2.1, Sec. 4.2).
  *   RK4:        fixed step h.
@@ -88,6 +88,12 @@ typedef enum { RTCC_RK4 = 0, RTCC_CK = 1, RTCC_MIXED_RK4 = 2 } rtcc_method_t;
  *               clamped to [0.2h, 5h] and [h_min, h_max]; h is the first trial step.
  *   MIXED_RK4:  RK4 with h1 while t < t_switch (the crossing step is cut to land on
  *               t_switch), h2 afterwards.
+ *   GL2:        implicit two-stage Gauss-Legendre collocation (order 4, A-stable; Sec. 1
+ *               lists implicit RK among the integrators, without coefficients) with fixed
+ *               step h: c = 1/2 -+ sqrt(3)/6, the collocation matrix of [0, 1], b = (1/2, 1/2).
+ *               The stage equations K_i = f(t + c_i h, y + h sum_j a_ij K_j) are solved by
+ *               `sweeps` Gauss-Seidel fixed-point sweeps from K_i = f(t, y) (0: 20 sweeps;
+ *               each sweep costs two right-hand sides).
  * Stop after nsteps accepted steps if nsteps > 0, else at t_end (last step cut to land). */
 typedef struct {
     int method;        /* rtcc_method_t */
@@ -96,6 +102,7 @@ typedef struct {
     int max_rejects;
     int nsteps;
     double t_end;
+    int sweeps;        /* GL2 only */
 } rtcc_integrator_t;
 
 typedef struct rtcc_ctx* rtcc_handle_t;

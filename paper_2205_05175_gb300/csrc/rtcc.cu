@@ -27,6 +27,8 @@ struct Tableau {
   double b[kMaxStages];    // propagated solution
   double e[kMaxStages];    // b - b_embedded (error weights), zero for RK4
   bool adaptive;
+  bool implicit = false;   // full A: stages solved by fixed-point sweeps
+  int sweeps = 0;
 };
 
 Tableau rk4_tableau() {
@@ -38,6 +40,22 @@ Tableau rk4_tableau() {
   t.a[3][2] = 1.0;
   t.b[0] = 1.0 / 6; t.b[1] = 1.0 / 3; t.b[2] = 1.0 / 3; t.b[3] = 1.0 / 6;
   t.adaptive = false;
+  return t;
+}
+
+// Two-stage Gauss-Legendre collocation (implicit, order 4): Gauss points of [0, 1] and the
+// collocation matrix; the stage system is solved by Gauss-Seidel fixed-point sweeps.
+Tableau gl2_tableau(int sweeps) {
+  Tableau t{};
+  const double r = std::sqrt(3.0) / 6.0;
+  t.s = 2;
+  t.c[0] = 0.5 - r; t.c[1] = 0.5 + r;
+  t.a[0][0] = 0.25; t.a[0][1] = 0.25 - r;
+  t.a[1][0] = 0.25 + r; t.a[1][1] = 0.25;
+  t.b[0] = 0.5; t.b[1] = 0.5;
+  t.adaptive = false;
+  t.implicit = true;
+  t.sweeps = sweeps > 0 ? sweeps : 20;
   return t;
 }
 
@@ -213,7 +231,7 @@ __global__ void k_prestep(Ctl c, rtcc_integrator_t in, int nz) {
   const double t = c.t[z];
   const double eps = 1e-12;
   double hs;
-  if (in.method == RTCC_RK4) hs = in.h;
+  if (in.method == RTCC_RK4 || in.method == RTCC_GL2) hs = in.h;
   else if (in.method == RTCC_MIXED_RK4) hs = (t < in.t_switch - eps) ? fmin(in.h1, in.t_switch - t) : in.h2;
   else hs = c.h[z];
   if (in.nsteps <= 0) hs = fmin(hs, in.t_end - t);
@@ -643,7 +661,38 @@ void run_attempt(rtcc_ctx* h, const Tableau& tb, const rtcc_integrator_t& in, do
   pr.start(s);
   k_prestep<<<(nz + 127) / 128, 128, 0, s>>>(h->ctl, in, nz);
   pr.stop(s, KC_RK, 0, 0);
-  for (int st = 0; st < tb.s; ++st) {
+  auto stage_rhs = [&](const StageArgs& A, double c) {
+    pr.start(s);
+    if (h->prec != Prec::P64) k_stage<true><<<gst, 256, 0, s>>>(h->Ys, h->Y, A, h->ctl.htry, ns, nT);
+    else k_stage<false><<<gst, 256, 0, s>>>(h->Ys, h->Y, A, h->ctl.htry, ns, nT);
+    pr.stop(s, KC_RK, 0, sb * (A.nterms + 2));
+    pr.start(s);
+    k_fock<<<dim3(blocks_for((long long)h->nmo * h->nmo), nz), 256, 0, s>>>(h->F, h->f0, h->mu, h->d_fields, h->ctl.t,
+                                                                           h->ctl.htry, c, nz, h->nmo * h->nmo);
+    pr.stop(s, KC_RK, 0, 8.0 * h->nmo * h->nmo * (4 + nz));
+    h->E->run(h->rhs.fwd);
+    h->E->run(h->rhs.rev);
+  };
+  const size_t rbytes = sizeof(double) * 2 * (size_t)ns * nz;
+  if (tb.implicit) {
+    // K_1 = K_2 = f(t, y), then Gauss-Seidel sweeps K_i <- f(t + c_i h, y + h sum_j a_ij D K_j)
+    StageArgs A0{};
+    stage_rhs(A0, 0.0);
+    RTCC_CUDA(cudaMemcpyAsync(h->Rk[0], h->Rout, rbytes, cudaMemcpyDeviceToDevice, s));
+    RTCC_CUDA(cudaMemcpyAsync(h->Rk[1], h->Rout, rbytes, cudaMemcpyDeviceToDevice, s));
+    for (int sw = 0; sw < tb.sweeps; ++sw)
+      for (int st = 0; st < tb.s; ++st) {
+        StageArgs A{};
+        A.nterms = tb.s;
+        for (int j = 0; j < tb.s; ++j) {
+          A.R[j] = h->Rk[j];
+          A.coef[j] = tb.a[st][j];
+        }
+        stage_rhs(A, tb.c[st]);
+        RTCC_CUDA(cudaMemcpyAsync(h->Rk[st], h->Rout, rbytes, cudaMemcpyDeviceToDevice, s));
+      }
+  }
+  for (int st = 0; st < (tb.implicit ? 0 : tb.s); ++st) {
     StageArgs A{};
     A.nterms = 0;
     for (int j = 0; j < st; ++j) {
@@ -669,7 +718,7 @@ void run_attempt(rtcc_ctx* h, const Tableau& tb, const rtcc_integrator_t& in, do
   }
   StageArgs B{}, Ew{};
   for (int j = 0; j < tb.s; ++j) {
-    B.R[j] = (j == tb.s - 1) ? h->Rout : h->Rk[j];
+    B.R[j] = (j == tb.s - 1 && !tb.implicit) ? h->Rout : h->Rk[j];
     B.coef[j] = tb.b[j];
     Ew.coef[j] = tb.e[j];
   }
@@ -1182,7 +1231,9 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
   if (!h || !fields || !integ || max_out < 1 || !t_out || !mu_out || !n_out)
     return fail(RTCC_ERR_INVALID_ARG, "null argument or max_out < 1");
   const rtcc_integrator_t in = *integ;
-  if (in.method < 0 || in.method > 2) return fail(RTCC_ERR_INVALID_ARG, "unknown integrator");
+  if (in.method < 0 || in.method > 3) return fail(RTCC_ERR_INVALID_ARG, "unknown integrator");
+  if (in.method == RTCC_GL2 && (!(in.h > 0) || in.sweeps < 0 || in.sweeps > 1000))
+    return fail(RTCC_ERR_INVALID_ARG, "Gauss-Legendre needs h > 0 and 0 <= sweeps <= 1000");
   if (in.nsteps <= 0 && !(in.t_end > 0)) return fail(RTCC_ERR_INVALID_ARG, "need nsteps > 0 or t_end > 0");
   if (in.method == RTCC_RK4 && !(in.h > 0)) return fail(RTCC_ERR_INVALID_ARG, "h must be positive");
   if (in.method == RTCC_MIXED_RK4 && !(in.h1 > 0 && in.h2 > 0)) return fail(RTCC_ERR_INVALID_ARG, "h1, h2 must be positive");
@@ -1204,7 +1255,7 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
       std::vector<double> h0(nz, in.h);
       RTCC_CUDA(cudaMemcpyAsync(h->ctl.h, h0.data(), sizeof(double) * nz, cudaMemcpyHostToDevice, s));
     }
-    const Tableau tb = (in.method == RTCC_CK) ? ck_tableau() : rk4_tableau();
+    const Tableau tb = (in.method == RTCC_CK) ? ck_tableau() : (in.method == RTCC_GL2 ? gl2_tableau(in.sweeps) : rk4_tableau());
     run_dipole(h);
     k_record<<<(nz + 127) / 128, 128, 0, s>>>(h->ctl, h->DIP, h->mu_ref[0], h->mu_ref[1], h->mu_ref[2], tout, muout,
                                              max_out, nz, 1);
@@ -1259,7 +1310,8 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
         long long nz_need;
         if (in.nsteps > 0) nz_need = in.nsteps - stp[z];
         else {
-          const double hstep = (in.method == RTCC_CK) ? hz[z] * 5.0 : (in.method == RTCC_RK4 ? in.h : std::max(in.h1, in.h2));
+          const double hstep = (in.method == RTCC_CK) ? hz[z] * 5.0
+                               : ((in.method == RTCC_RK4 || in.method == RTCC_GL2) ? in.h : std::max(in.h1, in.h2));
           nz_need = (long long)std::floor((in.t_end - tz[z]) / hstep);
         }
         need = std::min(need, nz_need);
@@ -1285,7 +1337,7 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
     for (int z = 0; z < nz; ++z) n_out[z] = nout[z];
     h->last_stats[0] = cnt[0];
     h->last_stats[1] = cnt[1];
-    h->last_stats[2] = (cnt[0] + cnt[1]) * tb.s;
+    h->last_stats[2] = (cnt[0] + cnt[1]) * (tb.implicit ? 1 + (long long)tb.s * tb.sweeps : tb.s);
     h->last_stats[3] = per_attempt * attempts;
     if (!dev_out) {
       // temporary device output buffers are released with the handle's allocation list

@@ -1,4 +1,4 @@
-"""Trajectory parity (RK4, Cash-Karp, mixed-step RK4) of the CUDA path against the oracle, the
+"""Trajectory parity (RK4, Cash-Karp, mixed-step RK4, Gauss-Legendre) of the CUDA path against the oracle, the
 zero-field fixed point, two-electron exactness against FCI, and batched-trajectory independence."""
 import numpy as np
 import pytest
@@ -90,6 +90,24 @@ def test_mixed_step_matches_oracle():
     assert n[0] == len(tt)
     assert np.abs(t[0, :n[0]] - tt).max() < 1e-12
     assert np.abs(m[0, :n[0]] - mm).max() < 1e-10
+
+
+def test_gauss_legendre_matches_oracle():
+    """Implicit two-stage Gauss-Legendre: the device's Gauss-Seidel sweeps and the oracle's
+    fixed-point iteration converge to the same collocation solution."""
+    from paper_2205_05175_gb300 import rtcc
+    o, v = 3, 7
+    f, B, mu = system(o, v)
+    s = rk.RTCC(f, B, mu, o)
+    y0, _, _ = s.ground_state(tol=1e-11)
+    fld = rk.Field(E0=0.05, omega=0.5, sigma=0.5, t0=0.5)
+    tt, mm, _, _ = rk.propagate(s, y0, fld, rk.Integrator(method="gl2", h=0.05, nsteps=20))
+    t, m, n, stats = _gpu_traj(o, v, f, B, mu, [rtcc.make_field(E0=0.05, t0=0.5)],
+                               rtcc.make_integrator(rtcc.GL2, h=0.05, nsteps=20, sweeps=20), 64, prec=0, y0=y0)
+    assert n[0] == 21
+    assert stats[2] == 20 * (1 + 2 * 20)
+    assert np.abs(t[0, :21] - tt).max() < 1e-12
+    assert np.abs(m[0, :21] - mm).max() < 1e-10
 
 
 def test_zero_field_fixed_point_on_device():
