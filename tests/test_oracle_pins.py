@@ -302,6 +302,52 @@ def test_matrix_pencil_recovers_frequencies():
     assert np.allclose(w, [-0.81, 0.81, 1.37], atol=1e-9)
 
 
+def _fci_kick_dipole(o, v, kappa, dt, T):
+    """Exact mu_z(t) after a delta kick E(t) = kappa delta(t) z: psi(0+) = exp(i kappa M_z) psi_0,
+    then free evolution in the eigenbasis of the field-free Hamiltonian (two electrons, FCI)."""
+    f, B, mu = synth.make_system(o, v)
+    F = fci.FCI(f, B, mu, o)
+    e0, psi0, w, U = F.ground()
+    lam, Q = np.linalg.eigh(F.M[2])
+    c = U.conj().T @ (Q @ (np.exp(1j * kappa * lam) * (Q.conj().T @ psi0)))
+    Mp = U.conj().T @ F.M[2] @ U
+    t = dt * np.arange(int(round(T / dt)) + 1)
+    A = np.exp(-1j * np.outer(t, w)) * c[None, :]
+    mus = np.zeros((len(t), 3))
+    mus[:, 2] = np.real(np.einsum("ti,ij,tj->t", A.conj(), Mp, A))
+    k0 = int(np.argmin(np.abs(w - e0)))
+    strength = np.abs(Mp[k0, :]) ** 2
+    strength[k0] = 0.0
+    return t, mus, w - e0, strength
+
+
+def test_kick_spectrum_line_strength_and_noise_floor():
+    """Sec. 2.2 (polarisability from the induced dipole) and the noise study of Sec. 4.1
+    (Fig. sp-noise).  After a weak delta kick of area kappa the induced dipole is, to first order,
+    2 kappa sum_k |<0|mu_z|k>|^2 sin(w_k t), so the damped transform gives a line at each
+    excitation energy w_k of height |<0|mu_z|k>|^2 (1 - exp(-gamma T)) / gamma.  Uniform noise of
+    amplitude eps on the samples after t = 0 adds Im[dt sum_n eta_n exp((i w - gamma) t_n)] / kappa,
+    whose root-mean-square over w is dt eps sqrt(sum_n exp(-2 gamma t_n) / 6) / kappa.  A dropped dt,
+    a missing factor of the damping or a kappa in the wrong place fails one of these."""
+    kappa = 0.01 * 0.01 * np.sqrt(2 * np.pi)    # area of the Sec. 4.1 noise-study pulse (E0 = 0.01, sigma = 0.01)
+    dt, T, gamma = 0.05, 300.0, 0.01
+    t, mus, exc, strength = _fci_kick_dipole(1, 4, kappa, dt, T)
+    om = np.linspace(0.5, 3.0, 2501)
+    I0 = spectrum.spectrum(t, mus, om, (0, 0, 1), kappa=kappa, gamma=gamma)
+    k = int(np.argmax(strength))
+    j = int(np.argmax(I0))
+    assert abs(om[j] - exc[k]) < 1e-3
+    assert abs(I0[j] / (strength[k] * (1 - np.exp(-gamma * T)) / gamma) - 1) < 2e-3
+    rng = np.random.Generator(np.random.PCG64(2205_05175))
+    floor = dt * np.sqrt(np.sum(np.exp(-2 * gamma * t[1:])) / 6) / kappa
+    for eps in (1e-6, 1e-5, 1e-4):
+        noisy = mus.copy()
+        noisy[1:, 2] += rng.uniform(-eps, eps, len(t) - 1)
+        dI = spectrum.spectrum(t, noisy, om, (0, 0, 1), kappa=kappa, gamma=gamma) - I0
+        assert 0.75 < np.sqrt(np.mean(dI ** 2)) / (eps * floor) < 1.25
+        assert abs(om[int(np.argmax(I0 + dI))] - exc[k]) < 1e-3
+
+
 # --- real-time spectrum peaks = EOM-CCSD excitation energies (Sec. 3: EOM-CCSD stick spectra) ----
 
 def _rt_modes(o, v, h, T):
