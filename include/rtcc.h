@@ -93,7 +93,12 @@ typedef enum { RTCC_RK4 = 0, RTCC_CK = 1, RTCC_MIXED_RK4 = 2, RTCC_GL2 = 3 } rtc
  *               step h: c = 1/2 -+ sqrt(3)/6, the collocation matrix of [0, 1], b = (1/2, 1/2).
  *               The stage equations K_i = f(t + c_i h, y + h sum_j a_ij K_j) are solved by
  *               `sweeps` Gauss-Seidel fixed-point sweeps from K_i = f(t, y) (0: 20 sweeps;
- *               each sweep costs two right-hand sides).
+ *               each sweep costs two right-hand sides).  A step whose last sweep still moves
+ *               h K_2 by more than tol (max over components) stops the call with
+ *               RTCC_ERR_NOCONV.  The sweeps contract only for steps of the order of RK4's
+ *               stability limit, so they do not lengthen the usable step; what GL2 adds is
+ *               that it conserves quadratic invariants (the norm, for Hermitian linear
+ *               dynamics), which RK4 does not.
  * Stop after nsteps accepted steps if nsteps > 0, else at t_end (last step cut to land). */
 typedef struct {
     int method;        /* rtcc_method_t */
@@ -174,7 +179,7 @@ rtcc_status_t rtcc_dipole(rtcc_handle_t h, double* mu_out);
  * n_out  : host, ntraj ints: samples written per trajectory.
  * Each trajectory carries its own step size (Cash-Karp) and time; all trajectories
  * share every GEMM.  Sampling stops silently when max_out is reached; propagation
- * continues to the end.  Errors: DIVERGED, STEP_UNDERFLOW, TIMEOUT, CUDA. */
+ * continues to the end.  Errors: DIVERGED, STEP_UNDERFLOW, NOCONV (GL2 stages), TIMEOUT, CUDA. */
 rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields,
                              const rtcc_integrator_t* integ, int max_out,
                              double* t_out, double* mu_out, int* n_out);

@@ -16,7 +16,7 @@ namespace {
 thread_local std::string g_last_error = "no error";
 
 constexpr int kMaxStages = 6;
-enum TrajStatus : int { TS_RUN = 0, TS_DONE = 1, TS_DIVERGED = 2, TS_UNDERFLOW = 3 };
+enum TrajStatus : int { TS_RUN = 0, TS_DONE = 1, TS_DIVERGED = 2, TS_UNDERFLOW = 3, TS_NOCONV = 4 };
 
 // Butcher tableaus (Sec. 2.1 Eqs. rk_y/rk_k; Sec. 4.2 Eq. rk4truncation, Eqs. ck-k/ck-y with
 // the row sums sum_j a_ij = c_i restored: a42 = -9/10, a63 = +575/13824, c4 = 3/5, c5 = 1).
@@ -246,6 +246,11 @@ __global__ void k_controller(Ctl c, rtcc_integrator_t in, int nz) {
   const double eps = 1e-12;
   if (!isfinite(delta)) {
     c.status[z] = TS_DIVERGED;
+    return;
+  }
+  if (in.method == RTCC_GL2 && delta > in.tol) {
+    // the last Gauss-Seidel sweep still moved h K_2 by more than tol: the stages have not converged
+    c.status[z] = TS_NOCONV;
     return;
   }
   bool acc = true;
@@ -689,7 +694,10 @@ void run_attempt(rtcc_ctx* h, const Tableau& tb, const rtcc_integrator_t& in, do
           A.coef[j] = tb.a[st][j];
         }
         stage_rhs(A, tb.c[st]);
-        RTCC_CUDA(cudaMemcpyAsync(h->Rk[st], h->Rout, rbytes, cudaMemcpyDeviceToDevice, s));
+        // the last evaluation stays in Rout, so Rk[1] keeps the previous sweep's K_2 for the
+        // convergence measure h max |K_2(new) - K_2(old)| formed by the final combination
+        if (sw < tb.sweeps - 1 || st < tb.s - 1)
+          RTCC_CUDA(cudaMemcpyAsync(h->Rk[st], h->Rout, rbytes, cudaMemcpyDeviceToDevice, s));
       }
   }
   for (int st = 0; st < (tb.implicit ? 0 : tb.s); ++st) {
@@ -718,17 +726,26 @@ void run_attempt(rtcc_ctx* h, const Tableau& tb, const rtcc_integrator_t& in, do
   }
   StageArgs B{}, Ew{};
   for (int j = 0; j < tb.s; ++j) {
-    B.R[j] = (j == tb.s - 1 && !tb.implicit) ? h->Rout : h->Rk[j];
+    B.R[j] = (j == tb.s - 1) ? h->Rout : h->Rk[j];
     B.coef[j] = tb.b[j];
     Ew.coef[j] = tb.e[j];
   }
   B.nterms = tb.s;
+  if (tb.implicit) {
+    // error slot: +1 on the newest K_2 (Rout), -1 on the previous sweep's K_2 (Rk[1], weight 0 in y)
+    for (int j = 0; j < tb.s; ++j) Ew.coef[j] = (j == tb.s - 1) ? 1.0 : 0.0;
+    B.R[tb.s] = h->Rk[tb.s - 1];
+    B.coef[tb.s] = 0.0;
+    Ew.coef[tb.s] = -1.0;
+    B.nterms = tb.s + 1;
+  }
+  const int measure = (tb.adaptive || tb.implicit) ? 1 : 0;
   pr.start(s);
   if (h->prec != Prec::P64)
-    k_final<true><<<gst, 256, 0, s>>>(h->Ynew, h->Y, B, Ew, h->ctl.htry, ns, nT, h->ctl.err_bits, tb.adaptive ? 1 : 0);
+    k_final<true><<<gst, 256, 0, s>>>(h->Ynew, h->Y, B, Ew, h->ctl.htry, ns, nT, h->ctl.err_bits, measure);
   else
-    k_final<false><<<gst, 256, 0, s>>>(h->Ynew, h->Y, B, Ew, h->ctl.htry, ns, nT, h->ctl.err_bits, tb.adaptive ? 1 : 0);
-  pr.stop(s, KC_RK, 0, sb * (tb.s + 2));
+    k_final<false><<<gst, 256, 0, s>>>(h->Ynew, h->Y, B, Ew, h->ctl.htry, ns, nT, h->ctl.err_bits, measure);
+  pr.stop(s, KC_RK, 0, sb * (B.nterms + 2));
   pr.start(s);
   k_controller<<<(nz + 127) / 128, 128, 0, s>>>(h->ctl, in, nz);
   pr.stop(s, KC_RK, 0, 0);
@@ -1232,8 +1249,8 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
     return fail(RTCC_ERR_INVALID_ARG, "null argument or max_out < 1");
   const rtcc_integrator_t in = *integ;
   if (in.method < 0 || in.method > 3) return fail(RTCC_ERR_INVALID_ARG, "unknown integrator");
-  if (in.method == RTCC_GL2 && (!(in.h > 0) || in.sweeps < 0 || in.sweeps > 1000))
-    return fail(RTCC_ERR_INVALID_ARG, "Gauss-Legendre needs h > 0 and 0 <= sweeps <= 1000");
+  if (in.method == RTCC_GL2 && (!(in.h > 0) || !(in.tol > 0) || in.sweeps < 0 || in.sweeps > 1000))
+    return fail(RTCC_ERR_INVALID_ARG, "Gauss-Legendre needs h > 0, tol > 0 and 0 <= sweeps <= 1000");
   if (in.nsteps <= 0 && !(in.t_end > 0)) return fail(RTCC_ERR_INVALID_ARG, "need nsteps > 0 or t_end > 0");
   if (in.method == RTCC_RK4 && !(in.h > 0)) return fail(RTCC_ERR_INVALID_ARG, "h must be positive");
   if (in.method == RTCC_MIXED_RK4 && !(in.h1 > 0 && in.h2 > 0)) return fail(RTCC_ERR_INVALID_ARG, "h1, h2 must be positive");
@@ -1267,7 +1284,14 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
     const long long c0 = total_count(h->prof);
     run_attempt(h, tb, in, tout, muout, max_out);
     const long long per_attempt = total_count(h->prof) - c0;
-    cudaGraphExec_t exec = nullptr;
+    // owns the replayed graph, so every error thrown below also releases it
+    struct GraphExec {
+      cudaGraphExec_t e = nullptr;
+      ~GraphExec() {
+        if (e) cudaGraphExecDestroy(e);
+      }
+    } ge;
+    cudaGraphExec_t& exec = ge.e;
     if (use_graph) {
       cudaGraph_t graph = nullptr;
       RTCC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -1279,8 +1303,9 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
         throw;
       }
       RTCC_CUDA(cudaStreamEndCapture(s, &graph));
-      RTCC_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+      const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
       cudaGraphDestroy(graph);
+      RTCC_CUDA(ie);
     }
     std::vector<int> stat(nz), stp(nz);
     std::vector<double> tz(nz), hz(nz);
@@ -1297,6 +1322,8 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
       bool running = false;
       for (int z = 0; z < nz; ++z) {
         if (stat[z] == TS_DIVERGED) throw Error(RTCC_ERR_DIVERGED, "trajectory " + std::to_string(z) + " diverged");
+        if (stat[z] == TS_NOCONV)
+          throw Error(RTCC_ERR_NOCONV, "trajectory " + std::to_string(z) + ": implicit stages did not converge");
         if (stat[z] == TS_UNDERFLOW)
           throw Error(RTCC_ERR_STEP_UNDERFLOW, "trajectory " + std::to_string(z) + ": step size underflow");
         running |= (stat[z] == TS_RUN);
@@ -1324,7 +1351,6 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
       attempts += k;
       check_every = std::min(check_every * 2, 64);
     }
-    if (exec) cudaGraphExecDestroy(exec);
     std::vector<int> nout(nz);
     long long cnt[4];
     RTCC_CUDA(cudaMemcpyAsync(nout.data(), h->ctl.nout, sizeof(int) * nz, cudaMemcpyDeviceToHost, s));

@@ -54,3 +54,21 @@ def test_ground_state_nonconvergence_is_reported():
         with pytest.raises(rtcc.RtccError) as e:
             H.ground_state(tol=1e-12, maxiter=2)
         assert e.value.status == "NOCONV"
+
+
+def test_unconverged_implicit_stages_are_reported():
+    """Gauss-Legendre stages solved by fixed-point sweeps: at o=2, v=6 the sweeps stop contracting
+    between h = 0.3 and 0.4 (the same sweeps run on the oracle leave h |dK_2| near 4 after 20
+    sweeps at h = 0.4, finite), so the step is refused with NOCONV instead of being taken."""
+    from paper_2205_05175_gb300 import rtcc
+    o, v = 2, 6
+    f, B, mu = synth.make_system(o, v)
+    fld = [rtcc.make_field(E0=0.05, t0=0.5)]
+    with rtcc.Handle(f, B, mu, o, v, ntraj=1, prec=0) as H:
+        H.ground_state(tol=1e-11)
+        with pytest.raises(rtcc.RtccError) as e:
+            H.propagate(fld, rtcc.make_integrator(rtcc.GL2, h=0.4, nsteps=1, tol=1e-6, sweeps=20), 4)
+        assert e.value.status == "NOCONV" and "implicit stages" in rtcc.rtcc_last_error()
+        H.ground_state(tol=1e-11)                 # the handle recovers
+        _, m, n = H.propagate(fld, rtcc.make_integrator(rtcc.GL2, h=0.05, nsteps=2, tol=1e-6), 4)
+        assert n[0] == 3 and np.isfinite(m[0, :3]).all()
