@@ -365,6 +365,37 @@ def config_f1():
     return out
 
 
+def config_f3():
+    """Implicit Gauss-Legendre against RK4 at the same step: accuracy against a float64 RK4 run at a
+    quarter of the step, right-hand-side evaluations and wall time (dimer shape, 5 au)."""
+    import numpy as np
+
+    from paper_2205_05175_gb300 import rtcc, synth
+    o, v, h, T = 10, 38, 0.05, 5.0
+    f, B, mu = synth.make_system(o, v)
+    fld = rtcc.make_field(E0=0.01, omega=0.5, sigma=0.5, t0=1.0, pol=(0.0, 0.0, 1.0))
+    n = int(round(T / h))
+    with rtcc.Handle(f, B, mu, o, v, ntraj=1, prec=rtcc.P64) as H:
+        H.ground_state(tol=1e-10)
+        _, mref, k = H.propagate([fld], rtcc.make_integrator(rtcc.RK4, h=h / 4, nsteps=4 * n), 4 * n + 1)
+    mref = mref[0, :k[0]:4]
+    out = {"config": "f3", "workload": f"o={o} v={v}, E0=0.01 z sine pulse, {T} au at h={h}; reference float64 RK4 h={h / 4}",
+           "runs": {}}
+    for prec in ("p64", "bf16x3"):
+        with rtcc.Handle(f, B, mu, o, v, ntraj=1, prec=rtcc.PRECISIONS[prec]) as H:
+            H.ground_state(tol=1e-10)
+            y0 = H.get_state(0)[0]
+            for name, integ in (("rk4", rtcc.make_integrator(rtcc.RK4, h=h, nsteps=n)),
+                                ("gl2", rtcc.make_integrator(rtcc.GL2, h=h, nsteps=n, tol=1e-6, sweeps=20))):
+                H.set_state(0, y0, 0.0, 0.0)
+                t0 = time.perf_counter()
+                _, m, k = H.propagate([fld], integ, n + 1)
+                wall = time.perf_counter() - t0
+                out["runs"][f"{name}_{prec}"] = {"max_abs_dmu": float(np.abs(m[0, :k[0]] - mref).max()),
+                                                 "rhs": H.last_stats()[2], "wall_s": round(wall, 3)}
+    return out
+
+
 def run_gpu(args, rank, world, local):
     import numpy as np
     import torch
@@ -482,7 +513,7 @@ def main(argv=None):
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-dipole-error", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
-    ap.add_argument("--config", default=None, choices=["c2", "c3", "c5", "f1"],
+    ap.add_argument("--config", default=None, choices=["c2", "c3", "c5", "f1", "f3"],
                     help="run an accuracy / integrator / adjoint measurement instead of the throughput line")
     args = ap.parse_args(argv)
     if args.config is not None:
@@ -490,7 +521,7 @@ def main(argv=None):
             print(json.dumps({"impl": "reference", "config": args.config,
                               "unavailable": "configuration runs compare the library's own precision modes"}))
             return 0
-        line = {"c2": config_c2, "c3": config_c3, "c5": config_c5, "f1": config_f1}[args.config]()
+        line = {"c2": config_c2, "c3": config_c3, "c5": config_c5, "f1": config_f1, "f3": config_f3}[args.config]()
         print(json.dumps(line), flush=True)
         return 0
     rank, world, local = dist_env()
