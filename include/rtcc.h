@@ -46,7 +46,7 @@ typedef enum {
     RTCC_ERR_INVALID_ARG = 1,   /* bad size, null pointer, asymmetric input, unknown enum */
     RTCC_ERR_OOM = 2,           /* device allocation failed */
     RTCC_ERR_CUDA = 3,          /* CUDA runtime/driver error (no device, launch failure) */
-    RTCC_ERR_NOCONV = 4,        /* ground-state iterations did not converge */
+    RTCC_ERR_NOCONV = 4,        /* ground-state iterations or implicit stage sweeps did not converge */
     RTCC_ERR_DIVERGED = 5,      /* NaN/Inf or norm blow-up in a propagated state */
     RTCC_ERR_STEP_UNDERFLOW = 6,/* Cash-Karp step fell below h_min or too many rejects */
     RTCC_ERR_TIMEOUT = 7,       /* a bounded device-side wait expired (kernel returned early) */

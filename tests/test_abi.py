@@ -1,4 +1,5 @@
 """The C-ABI library builds, loads and exports every entry point include/rtcc.h declares."""
+import ctypes
 import os
 import re
 import subprocess
@@ -75,3 +76,56 @@ def test_frozen_core_count_is_checked_before_any_device_work(lib):
             lib.Handle(f, B, mu, o, v, nfc=nfc)
         assert e.value.status == "INVALID_ARG"
         assert "frozen-core" in lib.rtcc_last_error()
+
+
+LAYOUT_C = r"""
+#include <stdio.h>
+#include "rtcc.h"
+#define F(S, m) printf(#S " " #m " %zu %zu\n", offsetof(S, m), sizeof(((S*)0)->m))
+int main(void) {
+  F(rtcc_field_t, E0); F(rtcc_field_t, omega); F(rtcc_field_t, sigma); F(rtcc_field_t, t0);
+  F(rtcc_field_t, pol); F(rtcc_field_t, carrier); F(rtcc_field_t, sign);
+  F(rtcc_integrator_t, method); F(rtcc_integrator_t, h); F(rtcc_integrator_t, h1); F(rtcc_integrator_t, h2);
+  F(rtcc_integrator_t, t_switch); F(rtcc_integrator_t, tol); F(rtcc_integrator_t, safety);
+  F(rtcc_integrator_t, h_min); F(rtcc_integrator_t, h_max); F(rtcc_integrator_t, max_rejects);
+  F(rtcc_integrator_t, nsteps); F(rtcc_integrator_t, t_end); F(rtcc_integrator_t, sweeps);
+  F(rtcc_profile_t, launches); F(rtcc_profile_t, ms); F(rtcc_profile_t, flops); F(rtcc_profile_t, bytes);
+  printf("sizeof rtcc_field_t %zu\nsizeof rtcc_integrator_t %zu\nsizeof rtcc_profile_t %zu\n",
+         sizeof(rtcc_field_t), sizeof(rtcc_integrator_t), sizeof(rtcc_profile_t));
+  printf("enum %d %d %d %d %d %d %d %d %d %d\n", RTCC_RK4, RTCC_CK, RTCC_MIXED_RK4, RTCC_GL2, RTCC_P64,
+         RTCC_P32_TF32, RTCC_P32_3XTF32, RTCC_P32_BF16X3, RTCC_CARRIER_SIN, RTCC_CARRIER_COS);
+  printf("status %d %d %d %d %d %d %d %d %d\n", RTCC_OK, RTCC_ERR_INVALID_ARG, RTCC_ERR_OOM, RTCC_ERR_CUDA,
+         RTCC_ERR_NOCONV, RTCC_ERR_DIVERGED, RTCC_ERR_STEP_UNDERFLOW, RTCC_ERR_TIMEOUT, RTCC_ERR_UNSUPPORTED);
+  return 0;
+}
+"""
+
+
+def test_struct_layouts_and_enums_match_the_header(lib, tmp_path):
+    """The ctypes mirrors of the header's structs have the C compiler's offsets and sizes, and the
+    binding's constants the header's enum values (a field added on one side only fails here)."""
+    src = tmp_path / "layout.c"
+    exe = tmp_path / "layout"
+    src.write_text(LAYOUT_C)
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()
+    mirrors = {"rtcc_field_t": lib.rtcc_field_t, "rtcc_integrator_t": lib.rtcc_integrator_t,
+               "rtcc_profile_t": lib.rtcc_profile_t}
+    seen = {k: [] for k in mirrors}
+    for line in out:
+        w = line.split()
+        if w[0] == "sizeof":
+            assert int(w[2]) == ctypes.sizeof(mirrors[w[1]]), line
+        elif w[0] == "enum":
+            assert [int(x) for x in w[1:]] == [lib.RK4, lib.CK, lib.MIXED_RK4, lib.GL2, lib.P64, lib.P32_TF32,
+                                               lib.P32_3XTF32, lib.P32_BF16X3, lib.CARRIER_SIN, lib.CARRIER_COS]
+        elif w[0] == "status":
+            names = ["OK", "INVALID_ARG", "OOM", "CUDA", "NOCONV", "DIVERGED", "STEP_UNDERFLOW", "TIMEOUT", "UNSUPPORTED"]
+            assert {int(x): n for x, n in zip(w[1:], names)} == lib.STATUS
+        else:
+            S, m, off, size = w[0], w[1], int(w[2]), int(w[3])
+            field = getattr(mirrors[S], m)
+            assert (field.offset, field.size) == (off, size), line
+            seen[S].append(m)
+    for S, cls in mirrors.items():
+        assert seen[S] == [f[0] for f in cls._fields_], S
