@@ -248,13 +248,45 @@ def test_ck_local_error_orders_on_linear_ode():
     assert 25 < e4[0] / e4[1] < 40     # h^5 local error
 
 
-def test_ck_controller_formula():
-    acc, hn = rk.ck_controller(0.01, 1e-7, 1e-6)
-    assert acc and abs(hn - 0.01 * 0.84 * 10 ** 0.2) < 1e-15
-    acc, hn = rk.ck_controller(0.01, 1e-5, 1e-6)
-    assert (not acc) and abs(hn - 0.01 * 0.84 * 0.1 ** 0.25) < 1e-15
-    assert rk.ck_controller(0.01, 0.0, 1e-6) == (True, 0.05)
-    assert rk.ck_controller(0.01, 1.0, 1e-6)[1] == pytest.approx(0.002)
+def _embedded_attempt(tab, y, h, lam):
+    """One Cash-Karp attempt on y' = lam y: (fifth-order solution, |y5 - y4|)."""
+    ks = []
+    for i in range(len(tab["c"])):
+        ks.append(lam * (y + h * sum(tab["a"][i][j] * ks[j] for j in range(i))))
+    y5 = y + h * sum(b * k for b, k in zip(tab["b5"], ks))
+    y4 = y + h * sum(b * k for b, k in zip(tab["b4"], ks))
+    return y5, abs(y5 - y4)
+
+
+def test_ck_controller_drives_the_error_estimate_to_its_target():
+    """Eq. ck-h-final on an undamped oscillator y' = i y, where the estimate grows as h^5 and |y|
+    stays 1: from a tiny first step h grows by the 5x clamp, then settles where the estimate is
+    safety^5 tol (an exponent other than 1/5 settles at safety^(1/p) tol instead, a wrong safety
+    elsewhere); a step far too long is rejected and the 1/4-exponent retry lands at
+    safety^5 tol (tol/Delta)^(1/4) and is accepted."""
+    tab = rk.as_float(rk.CK_TABLE)
+    tol, safety = 1e-10, 0.84
+    y, h, hs, ratios = 1.0 + 0j, 1e-4, [], []
+    for _ in range(30):
+        y5, d = _embedded_attempt(tab, y, h, 1j)
+        acc, hn = rk.ck_controller(h, d, tol, safety)
+        assert acc
+        hs.append(h)
+        ratios.append(d / tol)
+        y, h = y5, hn
+    grow = [b / a for a, b in zip(hs, hs[1:])]
+    assert grow[0] == pytest.approx(5.0, rel=1e-14) and grow[1] == pytest.approx(5.0, rel=1e-14)
+    assert max(abs(r / safety ** 5 - 1) for r in ratios[12:]) < 1e-4
+    h_eq = hs[-1]
+    _, d = _embedded_attempt(tab, 1.0 + 0j, 2.0 * h_eq, 1j)
+    acc, hn = rk.ck_controller(2.0 * h_eq, d, tol, safety)
+    assert not acc and 0.2 * 2.0 * h_eq < hn < 2.0 * h_eq
+    _, d2 = _embedded_attempt(tab, 1.0 + 0j, hn, 1j)
+    assert rk.ck_controller(hn, d2, tol, safety)[0]
+    assert d2 / tol == pytest.approx(safety ** 5 * (tol / d) ** 0.25, rel=0.05)
+    # the clamps of the reading: [0.2 h, 5 h] and [h_min, h_max]
+    assert rk.ck_controller(0.01, 1.0, tol)[1] == pytest.approx(0.002)
+    assert rk.ck_controller(0.5, 0.0, tol, h_max=1.0)[1] == 1.0
 
 
 def test_field_matches_printed_values():
