@@ -313,6 +313,31 @@ def test_spline_reproduces_cubic_with_natural_ends_and_line():
     assert np.abs(spectrum.natural_cubic_spline(x, yv, x) - yv).max() < 1e-14
 
 
+def test_spline_reproduces_a_natural_spline_in_the_truncated_power_basis():
+    """Sec. 4.2 interpolation: a C2 piecewise cubic with knots at the samples and zero second
+    derivative at both ends is the unique natural cubic spline through its own values, so the
+    interpolant must reproduce it between the knots.  Built independently of the tridiagonal
+    solve: s(x) = a + b x + sum_j c_j (x - x_j)_+^3 over the interior knots, with
+    sum_j c_j (x_end - x_j) = 0 so that s''(x_end) = 0 (s'' vanishes left of the first knot)."""
+    rng = np.random.default_rng(3)
+    x = np.sort(rng.uniform(0.0, 5.0, 15))
+    x[0], x[-1] = 0.0, 5.0
+    c = rng.standard_normal(13)
+    c[-1] = -np.sum(c[:-1] * (x[-1] - x[1:-2])) / (x[-1] - x[-2])
+
+    def s_true(z):
+        z = np.asarray(z, float)
+        return 0.4 - 0.7 * z + np.sum(c[:, None] * np.maximum(z[None, :] - x[1:-1, None], 0.0) ** 3, axis=0)
+
+    xn = np.linspace(0.0, 5.0, 997)
+    got = spectrum.natural_cubic_spline(x, s_true(x), xn)
+    assert np.abs(got - s_true(xn)).max() < 1e-10 * max(1.0, np.abs(s_true(xn)).max())
+    # the same data with one interior value moved is not reproduced (the test can fail)
+    y = s_true(x)
+    y[7] += 1e-3
+    assert np.abs(spectrum.natural_cubic_spline(x, y, xn) - s_true(xn)).max() > 1e-4
+
+
 def test_delta_pulse_spectrum_peaks_at_oscillation_frequencies():
     dt = 0.05
     t = dt * np.arange(4000)
