@@ -244,6 +244,11 @@ def test_ck_local_error_orders_on_linear_ode():
         ex = np.exp(lam * h)
         e5.append(abs(y5[0] - ex))
         e4.append(abs(y4[0] - ex))
+        # the attempt propagates the fifth-order solution and estimates with |y5 - y4|, which is
+        # the fourth-order solution's own error up to the much smaller fifth-order one
+        ya, delta = s.ck_attempt(0.0, np.array([1.0 + 0j]), h, None)
+        assert abs(ya[0] - ex) == pytest.approx(e5[-1], rel=1e-6)
+        assert abs(delta / e4[-1] - 1) < 2 * e5[-1] / e4[-1] + 1e-12
     assert 50 < e5[0] / e5[1] < 80     # h^6 local error
     assert 25 < e4[0] / e4[1] < 40     # h^5 local error
 
