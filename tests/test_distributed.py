@@ -9,6 +9,7 @@ import sys
 
 import pytest
 
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -65,3 +66,19 @@ def test_reference_arm_runs_on_rank_zero_only():
             "sys.exit(bench.run_reference(a, rank=1, world=2))" % ROOT)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_reference_arm_line_carries_the_contract_keys(capsys):
+    """bench.py --impl reference on one rank: the oracle timed on a bounded sample (here a small
+    shape so the test stays short), printed as one JSON line with the keys the contract names."""
+    import bench
+    assert bench.main(["--impl", "reference", "--steps", "1", "--warmup", "1", "--o", "2", "--v", "6"]) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0 and line["warmup"] == 1 and line["steps"] == 1
+    assert line["ms_per_step"] == 1e3 / line["value"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert "o=2 v=6" in line["config"]["workload"]
