@@ -1,6 +1,7 @@
 """Parity at the full benchmark shape (o=30, v=114, naux=576) in the launch configuration the
 benchmark times: 12 trajectories batched in one handle, BF16x3 contractions, one right-hand side
-(Eqs. derivT/derivL) for every trajectory in one call, states and results resident on the device.
+(Eqs. derivT/derivL) for every trajectory in one call, states and results resident on the device,
+and the dipole (Eq. dipole) of the last trajectory.
 
 The oracle evaluates the last trajectory of the batch in full (about a minute of CPU and 20 GB of
 host memory); the first slot is given the same state, field and time, so its output must equal
@@ -14,7 +15,7 @@ between terms while any indexing error gives O(1)."""
 import numpy as np
 import pytest
 
-from oracle import rk
+from oracle import closed, rk
 from paper_2205_05175_gb300 import synth
 from tests.gpu_common import rel_err, state_from, system
 
@@ -33,7 +34,6 @@ def test_rhs_parity_hexamer_shape_twelve_trajectories():
     t1, t2 = synth.random_amplitudes(O, V, seed=301, s1=0.01, s2=0.005)
     l1, l2 = synth.random_amplitudes(O, V, seed=302, s1=0.01, s2=0.005)
     base = state_from(t1, t2, l1, l2)
-    del t2, l2
     last = NTRAJ - 1
     slot = [last] + list(range(1, NTRAJ))          # slot 0 repeats the inputs of slot 11
     scale = [1.0 + 0.02 * z for z in slot]
@@ -45,6 +45,8 @@ def test_rhs_parity_hexamer_shape_twelve_trajectories():
     ys = torch.stack([base_d * s for s in scale])
     with rtcc.Handle(f, B, mu, O, V, ntraj=NTRAJ, prec=rtcc.P32_BF16X3) as h:
         out = h.rhs(ys, fields, times)
+        h.set_state(last, base * scale[last])
+        dip = h.dipole()[last]
     torch.cuda.synchronize()
     assert bool(torch.isfinite(out).all())
     got = out[last].cpu().numpy().view(np.complex128)
@@ -55,3 +57,8 @@ def test_rhs_parity_hexamer_shape_twelve_trajectories():
     assert float((out[0] - out[last]).abs().max()) < 1e-5 * peak
     for k in range(1, last):
         assert float((out[k] - out[last]).abs().max()) > 1e-3 * peak, k
+    # Eq. dipole through the density program; these random amplitudes put |mu| near 5 au, so the
+    # bound is relative (same error model as above)
+    sc = scale[last]
+    ref_mu = closed.dipole(t1 * sc, t2 * sc, l1 * sc, l2 * sc, mu, O)
+    assert np.abs(dip - ref_mu).max() < 1e-4 * np.abs(ref_mu).max(), np.abs(dip - ref_mu).max()
