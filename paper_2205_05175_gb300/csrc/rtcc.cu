@@ -1568,9 +1568,11 @@ rtcc_status_t rtcc_selftest_timeout(double seconds) {
   if (!(seconds >= 0.0) || seconds > 10.0) return fail(RTCC_ERR_INVALID_ARG, "seconds must be in [0, 10]");
   return guarded([&] {
     int* d = static_cast<int*>(dev_alloc(2 * sizeof(int)));
-    RTCC_CUDA(cudaMemset(d, 0, 2 * sizeof(int)));
-    k_wait_flag<<<1, 1>>>(d, (unsigned long long)(seconds * 1e9), d + 1);
-    cudaError_t e = cudaDeviceSynchronize();
+    cudaError_t e = cudaMemset(d, 0, 2 * sizeof(int));
+    if (e == cudaSuccess) {
+      k_wait_flag<<<1, 1>>>(d, (unsigned long long)(seconds * 1e9), d + 1);
+      e = cudaDeviceSynchronize();
+    }
     int st = -1;
     if (e == cudaSuccess) e = cudaMemcpy(&st, d + 1, sizeof(int), cudaMemcpyDeviceToHost);
     cudaFree(d);
