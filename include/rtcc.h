@@ -236,6 +236,24 @@ rtcc_status_t rtcc_spectrum(const double* t, const double* mu, int n, const rtcc
                             double kappa, double gamma, double dt, const double* omega,
                             int n_omega, double* I);
 
+/* Pade-accelerated absorption spectrum (Sec. 1 cites Pade approximants for spectra from short
+ * propagations): as rtcc_spectrum, but each Fourier sum dt sum_k d_k e^{i w t_k} over the
+ * samples is replaced by dt e^{i w t_0} P(z)/Q(z), z = e^{i w dt}, the diagonal [M/M] Pade
+ * approximant of the power series sum_k d_k z^k built from 2M + 1 samples (all samples when n is
+ * odd, the first n - 1 otherwise).  The denominator solves its Toeplitz system in the
+ * least-squares sense with the minimum-norm solution (singular values at or below
+ * 2.2e-16 * M * sigma_max are dropped), by a one-sided Jacobi SVD on the device.  The pulse's
+ * samples E(t_k) get the same treatment unless kappa > 0 (delta pulse: alpha = D(w)/kappa).
+ *  t      : host, n sample times, increasing and uniformly spaced (relative 1e-9); 3 <= n <= 1025.
+ *  mu     : host, n*3 float64 real parts of the dipole.
+ *  field  : host; its pol projects the dipole, its amplitude is the pulse (kappa <= 0).
+ *  gamma  : damping exp(-gamma (t - t_0)) applied to mu(t) - mu(t_0).
+ *  omega  : host, n_omega frequencies;  I : host, n_omega outputs I(w) = Im[ D(w) / E(w) ].
+ * Errors: INVALID_ARG (sizes, non-uniform samples), NOCONV (Jacobi sweeps did not converge),
+ * CUDA. */
+rtcc_status_t rtcc_spectrum_pade(const double* t, const double* mu, int n, const rtcc_field_t* field,
+                                 double kappa, double gamma, const double* omega, int n_omega, double* I);
+
 /* Thread-local description of the most recent error (never null). */
 const char* rtcc_last_error(void);
 

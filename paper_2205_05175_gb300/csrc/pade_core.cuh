@@ -83,9 +83,26 @@ PADE_HD void pair_dots(const double* U, int M, int p, int q, int lane, int nl, d
   }
 }
 
+// This thread's share of |G|_F^2 = sum_k (M - |k - M|) c_k^2 (c_k fills M - |k - M| entries).
+PADE_HD double fro2_partial(const double* c, int M, long long tid, long long nt) {
+  double s = 0.0;
+  for (long long k = 1 + tid; k <= 2LL * M - 1; k += nt) {
+    const double m = (double)(M - (k > M ? k - M : M - k));
+    s += m * c[k] * c[k];
+  }
+  return s;
+}
+
+// Columns with norm^2 at or below eps^2 |G|_F^2 take part in no rotation: they end below the
+// least-squares cut (whose square is at least eps^2 M^2 |G|_F^2 / (M + 1)) and stay there.
+// Without this floor, columns of negligible size (a pulse record that has decayed to
+// underflow) keep rotating among themselves for many sweeps.
+PADE_HD double floor2(double fro2) { return kEps * kEps * fro2; }
+
 // The rotation that makes columns p and q orthogonal, from the full a, b, g; false when they
-// already are (cosine below kOrthTol, a zero column, or a non-finite value).
-PADE_HD bool rotation(double a, double b, double g, double& cs, double& sn) {
+// already are (cosine below kOrthTol), when either is below the floor, or for non-finite input.
+PADE_HD bool rotation(double a, double b, double g, double fl, double& cs, double& sn) {
+  if (!(a > fl && b > fl)) return false;
   if (!(fabs(g) > kOrthTol * sqrt(a * b))) return false;
   const double zeta = (b - a) / (2.0 * g);
   const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));

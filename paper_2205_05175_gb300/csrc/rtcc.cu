@@ -1,6 +1,7 @@
 // C-ABI of the RT-CCSD library (include/rtcc.h): handle, ground state, Runge-Kutta
 // propagation with a device-side step controller, dipole recording, spectrum.
 #include "model.cuh"
+#include "pade_core.cuh"
 #include <vector>
 #include "../../include/rtcc.h"
 #include <cmath>
@@ -476,6 +477,145 @@ __global__ void k_dft(const double* t, const double* y, int n, double dt, rtcc_f
     else { er *= dt; ei *= dt; }
     // Im[(dr + i di) / (er + i ei)] = (di er - dr ei) / |E|^2
     I[w] = (di * er - dr * ei) / (er * er + ei * ei);
+  }
+}
+
+// Pade-accelerated spectrum (Sec. 1 cites Pade approximants among the short-time spectral
+// techniques): the Fourier sum dt sum_k d_k e^{i w t_k} over uniform samples is replaced by
+// dt e^{i w t_0} P(z)/Q(z), z = e^{i w dt}, the diagonal Pade approximant of sum_k d_k z^k
+// (arithmetic in pade_core.cuh).
+// series[0][k] = (pol . (mu_k - mu_0)) e^{-gamma (t_k - t_0)}; series[1][k] = E(t_k) when the
+// pulse's own transform is divided out.
+__global__ void k_pade_series(const double* t, const double* y, int N, rtcc_field_t fld, double gamma, int with_field,
+                              double* series) {
+  const double t0 = t[0];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    const double tk = t[k];
+    const double damp = exp(-gamma * (tk - t0));
+    series[k] = ((y[(size_t)k * 3] - y[0]) * fld.pol[0] + (y[(size_t)k * 3 + 1] - y[1]) * fld.pol[1] +
+                 (y[(size_t)k * 3 + 2] - y[2]) * fld.pol[2]) * damp;
+    if (with_field) series[N + k] = field_amp(fld, tk);
+  }
+}
+
+// Sum over a warp, the same value on every lane (shuffle-down tree into lane 0, then broadcast).
+struct WarpSum {
+  __device__ double operator()(double x) const {
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+    return __shfl_sync(0xffffffffu, x, 0);
+  }
+};
+
+// One CTA per series (N = 2M + 1 coefficients): one warp per column pair of each tournament
+// round, a block barrier between rounds, sweeps until no pair rotates (at most
+// pade::kMaxSweeps; info = 1 if that bound is reached); then the minimum-norm denominator and
+// the numerator.  coef[s] = a_0 .. a_M, b_0 .. b_M.  work: pade::work_doubles(M) per series.
+constexpr int kPadeThreads = 512, kPadeMaxOrder = 512;
+__global__ void __launch_bounds__(kPadeThreads) k_pade_solve(const double* series, int M, double* work, double* coef,
+                                                             int* info) {
+  using namespace pade;
+  const int sid = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  const int N = 2 * M + 1, M2 = padded(M);
+  const double* c = series + (size_t)sid * N;
+  double* U = work + (size_t)sid * work_doubles(M);
+  double* V = U + (size_t)M * M2;
+  double* rhs = V + (size_t)M2 * M2;
+  double* s2 = rhs + M2;
+  double* w = s2 + M2;
+  __shared__ int s_rot;
+  __shared__ double s_red[32];
+  const WarpSum sum;
+  fill(c, M, U, V, rhs, tid, blockDim.x);
+  {
+    double f = fro2_partial(c, M, tid, blockDim.x);
+    f = sum(f);
+    if (lane == 0) s_red[warp] = f;
+  }
+  __syncthreads();
+  double fro2 = 0.0;
+  for (int i = 0; i < nwarp; ++i) fro2 += s_red[i];
+  const double fl = floor2(fro2);
+  __syncthreads();
+  int sweep = 0;
+  for (; sweep < kMaxSweeps; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int r = 0; r < M2 - 1; ++r) {
+      for (int k = warp; k < M2 / 2; k += nwarp) {
+        int p, q;
+        pair_of(M2, r, k, p, q);
+        double a, b, g;
+        pair_dots(U, M, p, q, lane, 32, a, b, g);
+        a = sum(a);
+        b = sum(b);
+        g = sum(g);
+        double cs, sn;
+        if (rotation(a, b, g, fl, cs, sn)) {
+          pair_apply(U, V, M, M2, p, q, cs, sn, lane, 32);
+          if (lane == 0) s_rot = 1;
+        }
+      }
+      __syncthreads();
+    }
+    const int any = s_rot;
+    __syncthreads();
+    if (!any) break;
+  }
+  if (tid == 0) info[sid] = (sweep >= kMaxSweeps) ? 1 : 0;
+  for (int j = warp; j < M2; j += nwarp) {
+    double x, y;
+    col_dots(U, rhs, M, j, lane, 32, x, y);
+    x = sum(x);
+    y = sum(y);
+    if (lane == 0) {
+      s2[j] = x;
+      w[j] = y;
+    }
+  }
+  __syncthreads();
+  double mx = 0.0;
+  for (int j = tid; j < M2; j += blockDim.x) mx = fmax(mx, s2[j]);
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
+  if (lane == 0) s_red[warp] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int i = 0; i < nwarp; ++i) m = fmax(m, s_red[i]);
+    s_red[0] = m;
+  }
+  __syncthreads();
+  const double cut = cut2(M, s_red[0]);
+  for (int j = tid; j < M2; j += blockDim.x) w[j] = (s2[j] > cut) ? w[j] / s2[j] : 0.0;
+  __syncthreads();
+  double* out = coef + (size_t)sid * 2 * (M + 1);
+  double* bq = out + (M + 1);
+  for (int i = tid; i < M; i += blockDim.x) bq[i + 1] = denominator(V, w, M2, i);
+  if (tid == 0) bq[0] = 1.0;
+  __syncthreads();
+  for (int k = tid; k <= M; k += blockDim.x) out[k] = numerator(bq, c, k);
+}
+
+// I(w) = Im[ D(w) / E(w) ] with D = dt e^{i w t_0} P_0/Q_0 and E = kappa (delta pulse) or the
+// same approximant of the pulse's samples (series 1).
+__global__ void k_pade_eval(const double* coef, int M, double dt, double t0, double kappa, const double* omega, int nw,
+                            double* I) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nw; q += gridDim.x * blockDim.x) {
+    const double om = omega[q];
+    double zs, zc, ss, sc;
+    sincos(om * dt, &zs, &zc);
+    sincos(om * t0, &ss, &sc);
+    double pr, pi;
+    pade::ratio(coef, coef + M + 1, M, zc, zs, pr, pi);
+    const double dr = dt * (sc * pr - ss * pi), di = dt * (sc * pi + ss * pr);
+    double er = kappa, ei = 0.0;
+    if (kappa <= 0.0) {
+      const double* c1 = coef + 2 * (M + 1);
+      double fr, fi;
+      pade::ratio(c1, c1 + M + 1, M, zc, zs, fr, fi);
+      er = dt * (sc * fr - ss * fi);
+      ei = dt * (sc * fi + ss * fr);
+    }
+    I[q] = (di * er - dr * ei) / (er * er + ei * ei);
   }
 }
 
@@ -1561,6 +1701,60 @@ rtcc_status_t rtcc_spectrum(const double* t, const double* mu, int n, const rtcc
     }
     for (void* p : al) cudaFree(p);
     cudaStreamDestroy(s);
+  });
+}
+
+rtcc_status_t rtcc_spectrum_pade(const double* t, const double* mu, int n, const rtcc_field_t* field, double kappa,
+                                 double gamma, const double* omega, int n_omega, double* I) {
+  if (!t || !mu || !field || !omega || !I || n < 3 || n_omega < 1) return fail(RTCC_ERR_INVALID_ARG, "bad argument");
+  const double h0 = t[1] - t[0];
+  for (int k = 1; k < n; ++k) {
+    const double hk = t[k] - t[k - 1];
+    if (!(hk > 0.0) || std::fabs(hk - h0) > 1e-9 * h0)
+      return fail(RTCC_ERR_INVALID_ARG, "Pade spectra need increasing, uniformly spaced sample times");
+  }
+  const int N = (n % 2 == 1) ? n : n - 1;   // 2M + 1 samples
+  const int M = (N - 1) / 2;
+  if (M > kPadeMaxOrder) return fail(RTCC_ERR_INVALID_ARG, "Pade spectra take at most 1025 samples");
+  const int nser = (kappa > 0.0) ? 1 : 2;
+  return guarded([&] {
+    cudaStream_t s;
+    RTCC_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    std::vector<void*> al;
+    auto A = [&](size_t bytes) {
+      void* p = dev_alloc(bytes);
+      al.push_back(p);
+      return p;
+    };
+    std::vector<int> info(nser, 0);
+    try {
+      double* dt_ = static_cast<double*>(A(sizeof(double) * N));
+      double* dy = static_cast<double*>(A(sizeof(double) * 3 * N));
+      double* dw = static_cast<double*>(A(sizeof(double) * n_omega));
+      double* dI = static_cast<double*>(A(sizeof(double) * n_omega));
+      double* ser = static_cast<double*>(A(sizeof(double) * nser * N));
+      double* work = static_cast<double*>(A(sizeof(double) * nser * pade::work_doubles(M)));
+      double* coef = static_cast<double*>(A(sizeof(double) * nser * 2 * (M + 1)));
+      int* dinfo = static_cast<int*>(A(sizeof(int) * nser));
+      RTCC_CUDA(cudaMemcpyAsync(dt_, t, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+      RTCC_CUDA(cudaMemcpyAsync(dy, mu, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, s));
+      RTCC_CUDA(cudaMemcpyAsync(dw, omega, sizeof(double) * n_omega, cudaMemcpyHostToDevice, s));
+      k_pade_series<<<blocks_for(N), 256, 0, s>>>(dt_, dy, N, *field, gamma, nser > 1 ? 1 : 0, ser);
+      k_pade_solve<<<nser, kPadeThreads, 0, s>>>(ser, M, work, coef, dinfo);
+      k_pade_eval<<<blocks_for(n_omega), 256, 0, s>>>(coef, M, h0, t[0], kappa, dw, n_omega, dI);
+      RTCC_CUDA(cudaGetLastError());
+      RTCC_CUDA(cudaMemcpyAsync(I, dI, sizeof(double) * n_omega, cudaMemcpyDeviceToHost, s));
+      RTCC_CUDA(cudaMemcpyAsync(info.data(), dinfo, sizeof(int) * nser, cudaMemcpyDeviceToHost, s));
+      RTCC_CUDA(cudaStreamSynchronize(s));
+    } catch (...) {
+      for (void* p : al) cudaFree(p);
+      cudaStreamDestroy(s);
+      throw;
+    }
+    for (void* p : al) cudaFree(p);
+    cudaStreamDestroy(s);
+    for (int x : info)
+      if (x) throw Error(RTCC_ERR_NOCONV, "Pade denominator: Jacobi sweeps did not converge");
   });
 }
 

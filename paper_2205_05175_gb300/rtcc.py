@@ -72,6 +72,7 @@ _sig = {
     "rtcc_propagate_vjp": [_vp, C.POINTER(rtcc_field_t), C.c_double, C.c_int, _vp, C.c_int, _vp, _vp],
     "rtcc_spectrum": [_vp, _vp, C.c_int, C.POINTER(rtcc_field_t), C.c_double, C.c_double, C.c_double, _vp,
                       C.c_int, _vp],
+    "rtcc_spectrum_pade": [_vp, _vp, C.c_int, C.POINTER(rtcc_field_t), C.c_double, C.c_double, _vp, C.c_int, _vp],
     "rtcc_selftest_gemm": [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp],
     "rtcc_selftest_timeout": [C.c_double],
     "rtcc_gemm_noalloc": [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp],
@@ -240,6 +241,15 @@ def rtcc_spectrum(t, mu_re, field, omegas, kappa=0.0, gamma=0.01, dt=0.0):
     I = np.zeros(len(omegas))
     _check(_lib.rtcc_spectrum(_ptr(t), _ptr(mu_re), len(t), C.byref(field), kappa, gamma, dt, _ptr(omegas),
                               len(omegas), _ptr(I)))
+    return I
+
+
+def rtcc_spectrum_pade(t, mu_re, field, omegas, kappa=0.0, gamma=0.01):
+    """Pade-accelerated spectrum of uniformly spaced samples (at most 1025)."""
+    t, mu_re, omegas = _as_c(t), _as_c(mu_re), _as_c(omegas)
+    I = np.zeros(len(omegas))
+    _check(_lib.rtcc_spectrum_pade(_ptr(t), _ptr(mu_re), len(t), C.byref(field), kappa, gamma, _ptr(omegas),
+                                   len(omegas), _ptr(I)))
     return I
 
 

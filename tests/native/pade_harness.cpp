@@ -50,6 +50,7 @@ int main() {
   double* s2 = rhs + M2;
   double* w = s2 + M2;
   fill(c.data(), M, U, V, rhs, 0, 1);
+  const double fl = floor2(fro2_partial(c.data(), M, 0, 1));
   int sweep = 0;
   for (; sweep < kMaxSweeps; ++sweep) {
     bool rotated = false;
@@ -61,7 +62,7 @@ int main() {
         for (int l = 0; l < 32; ++l) pair_dots(U, M, p, q, l, 32, A[l], B[l], G[l]);
         const double a = warp_sum(A), b = warp_sum(B), g = warp_sum(G);
         double cs, sn;
-        if (rotation(a, b, g, cs, sn)) {
+        if (rotation(a, b, g, fl, cs, sn)) {
           for (int l = 0; l < 32; ++l) pair_apply(U, V, M, M2, p, q, cs, sn, l, 32);
           rotated = true;
         }

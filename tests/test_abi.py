@@ -129,3 +129,21 @@ def test_struct_layouts_and_enums_match_the_header(lib, tmp_path):
             seen[S].append(m)
     for S, cls in mirrors.items():
         assert seen[S] == [f[0] for f in cls._fields_], S
+
+
+def test_pade_spectrum_arguments_are_checked_before_any_device_work(lib):
+    import numpy as np
+    om = np.linspace(0.1, 1.0, 5)
+    fld = lib.make_field()
+    t = 0.1 * np.arange(11)
+    t[5] += 0.01                                   # not uniform
+    with pytest.raises(lib.RtccError) as e:
+        lib.rtcc_spectrum_pade(t, np.zeros((11, 3)), fld, om, kappa=1.0)
+    assert e.value.status == "INVALID_ARG" and "uniformly" in lib.rtcc_last_error()
+    t = 0.1 * np.arange(1027)                      # M = 513, one above the largest order (512)
+    with pytest.raises(lib.RtccError) as e:
+        lib.rtcc_spectrum_pade(t, np.zeros((1027, 3)), fld, om, kappa=1.0)
+    assert e.value.status == "INVALID_ARG" and "1025" in lib.rtcc_last_error()
+    with pytest.raises(lib.RtccError) as e:
+        lib.rtcc_spectrum_pade(t[:2], np.zeros((2, 3)), fld, om, kappa=1.0)
+    assert e.value.status == "INVALID_ARG"

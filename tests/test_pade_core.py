@@ -78,3 +78,18 @@ def test_full_rank_series_match_the_oracle(harness, n):
     _, v = _pade(harness, c, z)
     o = spectrum.pade_transform(c, z)
     assert np.abs(v - o).max() < 1e-11 * np.abs(o).max()
+
+
+def test_pulse_record_that_decays_to_underflow_converges(harness):
+    """The samples of a Gaussian pulse fall to ~1e-300 long before the record ends (1025 samples,
+    the largest accepted): columns of negligible size are left alone, so the sweeps stop early,
+    and the transform still matches the oracle's."""
+    from oracle import rk
+    fld = rk.Field(E0=0.01, omega=0.5, sigma=0.5, t0=1.0)
+    t = 0.1 * np.arange(1025)
+    e = fld.amplitude(t)
+    z = np.exp(1j * np.linspace(0.2, 1.5, 300) * 0.1)
+    sweeps, v = _pade(harness, e, z)
+    assert sweeps < 30
+    o = spectrum.pade_transform(e, z)
+    assert np.abs(v - o).max() < 1e-12 * np.abs(o).max()
