@@ -5,9 +5,11 @@
  *     i dt_mu/dt      = <mu| e^{-T} H(t) e^{T} |0>            (Sec. 2, Eq. derivT)
  *    -i dlambda_mu/dt = <0|(1+Lambda)[Hbar(t), tau_mu]|0>      (Sec. 2, Eq. derivL)
  * with H(t) = H0 - mu.E(t) in frozen molecular orbitals (Sec. 2.2), propagates them
- * with explicit Runge-Kutta integrators (Sec. 2.1 Eqs. rk_y/rk_k; Sec. 4.2 RK4,
- * Cash-Karp Eqs. ck-k/ck-y/ck-h-final, mixed-step RK4) and records the dipole
- * mu_x(t) = <0|(1+Lambda) e^{-T} mu_x e^{T}|0> (Sec. 2.2, Eq. dipole).
+ * with Runge-Kutta integrators (Sec. 2.1 Eqs. rk_y/rk_k; Sec. 4.2 RK4, Cash-Karp
+ * Eqs. ck-k/ck-y/ck-h-final, mixed-step RK4; the implicit two-stage Gauss-Legendre method
+ * from the integrator library of Sec. 1) and records the dipole
+ * mu_x(t) = <0|(1+Lambda) e^{-T} mu_x e^{T}|0> (Sec. 2.2, Eq. dipole), from which it forms
+ * absorption spectra by a direct transform or a Pade-accelerated one (Sec. 2.2; Sec. 1).
  *
  * Conventions shared by every call
  *  - Orbitals are ordered occupied (o) then virtual (v); nmo = o + v.
