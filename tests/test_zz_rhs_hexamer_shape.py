@@ -26,7 +26,20 @@ TOL = 2e-4
 POLS = ((1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0))
 
 
+def _available_host_gb():
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 1e6
+    except OSError:
+        pass
+    return float("inf")
+
+
 def test_rhs_parity_hexamer_shape_twelve_trajectories():
+    if _available_host_gb() < 32:
+        pytest.skip("the oracle's full-shape right-hand side needs about 21 GB of host memory")
     import torch
 
     from paper_2205_05175_gb300 import rtcc
