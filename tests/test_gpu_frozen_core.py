@@ -41,6 +41,31 @@ def test_frozen_core_ground_state_and_trajectory(nfc):
     assert np.abs(mus[0, :7] - (np.asarray(mus_ref) + core)).max() < 1e-9
 
 
+def test_frozen_core_with_the_papers_isotropic_pulse():
+    """The paper's setup in one run: frozen core (Sec. 3) and the pulse of Eq. field as printed,
+    E(t) = -E0 exp(-(t - nu)^2 / (2 sigma^2)) cos(omega (t - nu)) n, along the isotropic
+    direction n = (1, 1, 1)/sqrt(3) of Eq. iso-field, so every dipole component responds."""
+    from paper_2205_05175_gb300 import rtcc
+    o, v, nfc = 5, 19, 1
+    f, B, mu = system(o, v)
+    fa, Ba, mua = _active(f, B, mu, nfc)
+    core = 2.0 * np.array([mu[x, :nfc, :nfc].trace() for x in range(3)])
+    n = tuple(np.ones(3) / np.sqrt(3.0))
+    s = rk.RTCC(fa, Ba, mua, o - nfc)
+    y0, _, _ = s.ground_state(tol=1e-11)
+    fld = rk.Field(E0=0.05, omega=0.5, sigma=0.5, t0=1.0, pol=n, carrier="cos", sign=-1.0)
+    _, mus_ref, _, _ = rk.propagate(s, y0, fld, rk.Integrator(method="rk4", h=0.05, nsteps=8))
+    with rtcc.Handle(f, B, mu, o, v, ntraj=1, prec=rtcc.P64, nfc=nfc) as h:
+        h.set_state(0, y0)
+        _, mus, k = h.propagate([rtcc.make_field(E0=0.05, omega=0.5, sigma=0.5, t0=1.0, pol=n,
+                                                 carrier=rtcc.CARRIER_COS, sign=-1.0)],
+                                rtcc.make_integrator(rtcc.RK4, h=0.05, nsteps=8), 9)
+    ref = np.asarray(mus_ref) + core
+    assert k[0] == 9
+    assert np.abs(mus[0, :9] - ref).max() < 1e-9
+    assert np.all(np.abs(ref[-1].real - ref[0].real) > 1e-6)     # all three components respond
+
+
 def test_frozen_core_zero_is_the_plain_handle():
     from paper_2205_05175_gb300 import rtcc
     o, v = 3, 7
