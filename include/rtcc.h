@@ -87,7 +87,11 @@ typedef enum { RTCC_RK4 = 0, RTCC_CK = 1, RTCC_MIXED_RK4 = 2, RTCC_GL2 = 3 } rtc
  *   CK:         Cash-Karp with the 37/378 (fifth-order) solution propagated, error
  *               Delta = max |y5 - y4| over all complex components, accept if Delta <= tol,
  *               h_new = safety*h*(tol/Delta)^(1/5) (accept) or ^(1/4) (reject, repeat),
- *               clamped to [0.2h, 5h] and [h_min, h_max]; h is the first trial step.
+ *               clamped to [0.2h, 5h] and [h_min, h_max]; h is the first trial step, and
+ *               h = 0 continues every trajectory with its stored trial step (the one the
+ *               previous call ended with, or rtcc_set_state's hstep), so that a run resumed
+ *               from rtcc_get_state takes the same steps as one that never stopped
+ *               (INVALID_ARG if a stored step lies outside [h_min, h_max]).
  *   MIXED_RK4:  RK4 with h1 while t < t_switch (the crossing step is cut to land on
  *               t_switch), h2 afterwards.
  *   GL2:        implicit two-stage Gauss-Legendre collocation (order 4, A-stable; Sec. 1

@@ -1394,14 +1394,29 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
   if (in.nsteps <= 0 && !(in.t_end > 0)) return fail(RTCC_ERR_INVALID_ARG, "need nsteps > 0 or t_end > 0");
   if (in.method == RTCC_RK4 && !(in.h > 0)) return fail(RTCC_ERR_INVALID_ARG, "h must be positive");
   if (in.method == RTCC_MIXED_RK4 && !(in.h1 > 0 && in.h2 > 0)) return fail(RTCC_ERR_INVALID_ARG, "h1, h2 must be positive");
-  if (in.method == RTCC_CK && !(in.h > 0 && in.tol > 0 && in.safety > 0 && in.h_min > 0 && in.h_max >= in.h_min))
+  if (in.method == RTCC_CK && !(in.h >= 0 && in.tol > 0 && in.safety > 0 && in.h_min > 0 && in.h_max >= in.h_min))
     return fail(RTCC_ERR_INVALID_ARG, "bad Cash-Karp settings");
   return guarded([&] {
     cudaStream_t s = h->stream;
     const int nz = h->nz;
     const bool dev_out = is_device_ptr(t_out);
-    double* tout = dev_out ? t_out : h->alloc<double>((size_t)nz * max_out);
-    double* muout = dev_out ? mu_out : h->alloc<double>((size_t)nz * max_out * 6);
+    // device staging of host outputs, released when the call returns (normally or by an error)
+    struct Staging {
+      void* p = nullptr;
+      ~Staging() {
+        if (p) cudaFree(p);
+      }
+    } st_t, st_mu;
+    double* tout = t_out;
+    double* muout = mu_out;
+    if (!dev_out) {
+      st_t.p = dev_alloc(sizeof(double) * nz * max_out);
+      st_mu.p = dev_alloc(sizeof(double) * nz * max_out * 6);
+      tout = static_cast<double*>(st_t.p);
+      muout = static_cast<double*>(st_mu.p);
+      RTCC_CUDA(cudaMemsetAsync(tout, 0, sizeof(double) * nz * max_out, s));
+      RTCC_CUDA(cudaMemsetAsync(muout, 0, sizeof(double) * nz * max_out * 6, s));
+    }
     RTCC_CUDA(cudaMemcpyAsync(h->d_fields, fields, sizeof(rtcc_field_t) * nz, cudaMemcpyHostToDevice, s));
     RTCC_CUDA(cudaMemsetAsync(h->ctl.status, 0, sizeof(int) * nz, s));
     RTCC_CUDA(cudaMemsetAsync(h->ctl.steps, 0, sizeof(int) * nz, s));
@@ -1409,8 +1424,19 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
     RTCC_CUDA(cudaMemsetAsync(h->ctl.nout, 0, sizeof(int) * nz, s));
     RTCC_CUDA(cudaMemsetAsync(h->ctl.counters, 0, sizeof(long long) * 4, s));
     if (in.method == RTCC_CK) {
-      std::vector<double> h0(nz, in.h);
-      RTCC_CUDA(cudaMemcpyAsync(h->ctl.h, h0.data(), sizeof(double) * nz, cudaMemcpyHostToDevice, s));
+      if (in.h > 0) {
+        std::vector<double> h0(nz, in.h);
+        RTCC_CUDA(cudaMemcpyAsync(h->ctl.h, h0.data(), sizeof(double) * nz, cudaMemcpyHostToDevice, s));
+      } else {
+        // h = 0: every trajectory continues with its stored trial step (resume)
+        std::vector<double> hz(nz);
+        RTCC_CUDA(cudaMemcpyAsync(hz.data(), h->ctl.h, sizeof(double) * nz, cudaMemcpyDeviceToHost, s));
+        RTCC_CUDA(cudaStreamSynchronize(s));
+        for (int z = 0; z < nz; ++z)
+          if (!(hz[z] >= in.h_min && hz[z] <= in.h_max))
+            throw Error(RTCC_ERR_INVALID_ARG, "trajectory " + std::to_string(z) +
+                                                  " has no stored Cash-Karp step in [h_min, h_max]; pass h > 0");
+      }
     }
     const Tableau tb = (in.method == RTCC_CK) ? ck_tableau() : (in.method == RTCC_GL2 ? gl2_tableau(in.sweeps) : rk4_tableau());
     run_dipole(h);
@@ -1505,9 +1531,6 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
     h->last_stats[1] = cnt[1];
     h->last_stats[2] = (cnt[0] + cnt[1]) * (tb.implicit ? 1 + (long long)tb.s * tb.sweeps : tb.s);
     h->last_stats[3] = per_attempt * attempts;
-    if (!dev_out) {
-      // temporary device output buffers are released with the handle's allocation list
-    }
   });
 }
 

@@ -149,3 +149,31 @@ def test_batched_trajectories_are_independent():
         _, ms, ns, _ = _gpu_traj(o, v, f, B, mu, [fields[z]], integ, 32, prec=0)
         assert nb[z] == ns[0] == 21
         assert np.abs(mb[z, :21] - ms[0, :21]).max() < 1e-12
+
+
+def test_cash_karp_checkpoint_resume_across_handles():
+    """Checkpoint/resume: the state, time and trial step read from one handle and written into a
+    fresh one continue the Cash-Karp run exactly as the first handle continues it (h = 0 keeps
+    each trajectory's stored step)."""
+    from paper_2205_05175_gb300 import rtcc
+    o, v = 2, 6
+    f, B, mu = system(o, v)
+    fld = [rtcc.make_field(E0=0.5, sigma=0.3, t0=1.0)]
+    first = rtcc.make_integrator(rtcc.CK, h=0.01, tol=1e-6, t_end=1.5)
+    rest = rtcc.make_integrator(rtcc.CK, h=0.0, tol=1e-6, t_end=3.0)
+    with rtcc.Handle(f, B, mu, o, v, ntraj=1, prec=rtcc.P64) as a:
+        a.ground_state(tol=1e-11)
+        a.propagate(fld, first, 4096)
+        y, t, hs = a.get_state(0)
+        ta, ma, na = a.propagate(fld, rest, 4096)
+    assert abs(t - 1.5) < 1e-12 and hs > 0
+    with rtcc.Handle(f, B, mu, o, v, ntraj=1, prec=rtcc.P64) as b:
+        with pytest.raises(rtcc.RtccError) as e:          # nothing stored yet: h = 0 is refused
+            b.propagate(fld, rest, 4096)
+        assert e.value.status == "INVALID_ARG"
+        b.set_state(0, y, t, hs)
+        tb, mb, nb = b.propagate(fld, rest, 4096)
+    assert na[0] == nb[0] > 10
+    assert ta[0, 0] == t and abs(ta[0, na[0] - 1] - 3.0) < 1e-12
+    assert np.abs(ta[0, :na[0]] - tb[0, :nb[0]]).max() < 1e-9
+    assert np.abs(ma[0, :na[0]] - mb[0, :nb[0]]).max() < 1e-9
