@@ -436,6 +436,46 @@ def config_f4():
             "max_peak_error_pade_eh": shift(pp), "max_peak_error_dft_eh": shift(pd), "wall_s_pade": round(wall_pade, 3)}
 
 
+def config_x1():
+    """The noise study of Sec. 4.1 (Fig. sp-noise) on the library's own path: a float64 monomer-
+    shaped trajectory after the paper's noise-study pulse (E0 = 0.01, nu = 0.05, sigma = 0.01, cos
+    carrier factor 1, 300 au), uniform noise of amplitude 10^-k added to mu_z(t), and the spectrum
+    of each against the clean one (mixed-step RK4: h1 = 1e-3 through the pulse, then h2 = 0.05)."""
+    import numpy as np
+
+    from paper_2205_05175_gb300 import rtcc, synth
+    o, v, T = 5, 19, 300.0
+    f, B, mu = synth.make_system(o, v)
+    E0, nu, sigma = 0.01, 0.05, 0.01
+    kick = E0 * sigma * np.sqrt(2.0 * np.pi)
+    fld = rtcc.make_field(E0=E0, omega=0.0, sigma=sigma, t0=nu, pol=(0.0, 0.0, 1.0), carrier=rtcc.CARRIER_COS)
+    integ = rtcc.make_integrator(rtcc.MIXED_RK4, h1=1e-3, h2=0.05, t_switch=0.1, t_end=T)
+    with rtcc.Handle(f, B, mu, o, v, ntraj=1, prec=rtcc.P64) as H:
+        H.ground_state(tol=1e-11)
+        a = time.perf_counter()
+        t, m, k = H.propagate([fld], integ, 8000)
+        wall = time.perf_counter() - a
+    t, m = t[0, :k[0]], m[0, :k[0]].real
+    sel = t >= 0.1 - 1e-12
+    t, m = t[sel], m[sel].copy()
+    om = np.linspace(0.05, 3.0, 6000)
+    I0 = rtcc.rtcc_spectrum(t, m, fld, om, kappa=kick, gamma=0.01)
+    p0 = _peaks(om, I0)
+    rng = np.random.Generator(np.random.PCG64(2205_05175))
+    rows = {}
+    for e in range(3, 9):
+        eps = 10.0 ** -e
+        mn = m.copy()
+        mn[1:, 2] += rng.uniform(-eps, eps, len(t) - 1)
+        I = rtcc.rtcc_spectrum(t, mn, fld, om, kappa=kick, gamma=0.01)
+        pk = _peaks(om, I)
+        shift = max(min(abs(x - y) for x in pk) for y in p0) if pk else None
+        rows[f"1e-{e}"] = {"max_abs_dI_rel": float(np.abs(I - I0).max() / np.abs(I0).max()), "max_peak_shift_eh": shift}
+    return {"config": "x1", "workload": f"o={o} v={v} float64, cos pulse E0={E0} nu={nu} sigma={sigma} (kick {kick:.3e} au), "
+                                        f"{T} au, {len(t)} samples after the pulse",
+            "wall_s": round(wall, 3), "peaks_clean": p0, "noise": rows}
+
+
 def run_gpu(args, rank, world, local):
     import numpy as np
     import torch
@@ -553,7 +593,7 @@ def main(argv=None):
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-dipole-error", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
-    ap.add_argument("--config", default=None, choices=["c2", "c3", "c5", "f1", "f3", "f4"],
+    ap.add_argument("--config", default=None, choices=["c2", "c3", "c5", "f1", "f3", "f4", "x1"],
                     help="run an accuracy / integrator / adjoint measurement instead of the throughput line")
     args = ap.parse_args(argv)
     if args.config is not None:
@@ -562,7 +602,7 @@ def main(argv=None):
                               "unavailable": "configuration runs compare the library's own precision modes"}))
             return 0
         line = {"c2": config_c2, "c3": config_c3, "c5": config_c5, "f1": config_f1, "f3": config_f3,
-                "f4": config_f4}[args.config]()
+                "f4": config_f4, "x1": config_x1}[args.config]()
         print(json.dumps(line), flush=True)
         return 0
     rank, world, local = dist_env()
