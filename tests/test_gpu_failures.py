@@ -56,6 +56,7 @@ def test_ground_state_nonconvergence_is_reported():
         assert e.value.status == "NOCONV"
 
 
+@pytest.mark.last
 def test_unconverged_implicit_stages_are_reported():
     """Gauss-Legendre stages solved by fixed-point sweeps: at o=2, v=6 the sweeps stop contracting
     between h = 0.3 and 0.4 (the same sweeps run on the oracle leave h |dK_2| near 4 after 20

@@ -41,6 +41,7 @@ def test_frozen_core_ground_state_and_trajectory(nfc):
     assert np.abs(mus[0, :7] - (np.asarray(mus_ref) + core)).max() < 1e-9
 
 
+@pytest.mark.last
 def test_frozen_core_with_the_papers_isotropic_pulse():
     """The paper's setup in one run: frozen core (Sec. 3) and the pulse of Eq. field as printed,
     E(t) = -E0 exp(-(t - nu)^2 / (2 sigma^2)) cos(omega (t - nu)) n, along the isotropic

@@ -92,6 +92,7 @@ def test_mixed_step_matches_oracle():
     assert np.abs(m[0, :n[0]] - mm).max() < 1e-10
 
 
+@pytest.mark.last
 def test_gauss_legendre_matches_oracle():
     """Implicit two-stage Gauss-Legendre: the device's Gauss-Seidel sweeps and the oracle's
     fixed-point iteration converge to the same collocation solution."""
@@ -151,6 +152,7 @@ def test_batched_trajectories_are_independent():
         assert np.abs(mb[z, :21] - ms[0, :21]).max() < 1e-12
 
 
+@pytest.mark.last
 def test_cash_karp_checkpoint_resume_across_handles():
     """Checkpoint/resume: the state, time and trial step read from one handle and written into a
     fresh one continue the Cash-Karp run exactly as the first handle continues it (h = 0 keeps

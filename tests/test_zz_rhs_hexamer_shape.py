@@ -19,7 +19,7 @@ from oracle import closed, rk
 from paper_2205_05175_gb300 import synth
 from tests.gpu_common import rel_err, state_from, system
 
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.last]
 
 O, V, NTRAJ = 30, 114, 12
 TOL = 2e-4

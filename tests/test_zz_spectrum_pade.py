@@ -1,13 +1,14 @@
 """rtcc_spectrum_pade (Pade-accelerated spectra: Jacobi-SVD least squares for the denominator,
 numerator convolution, evaluation on the frequency grid, all on the device) against the oracle's
 pade_spectrum.  The same arithmetic built for the host matches the oracle to 1e-10 or better on
-these series (tests/test_pade_core.py); the device only reorders nothing but the lanes' work."""
+these series (tests/test_pade_core.py); the device runs the same functions with the lanes of each
+warp, and the warps of a block, in parallel."""
 import numpy as np
 import pytest
 
 from oracle import rk, spectrum
 
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.last]
 
 
 def _peaks(om, I):
