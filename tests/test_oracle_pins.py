@@ -227,6 +227,32 @@ def test_rk4_global_error_scales_as_h4_on_linear_ode():
     assert 14.0 < errs[0] / errs[1] < 17.0
 
 
+def test_mixed_step_sequence_on_linear_ode_is_the_product_of_rk4_factors():
+    """Sec. 4.2 mixed-step RK4 as read here: h1 while t < t_switch with the crossing step cut to
+    land on t_switch, then h2, the last step cut to land on t_end.  On y' = lam y every RK4 step of
+    size h multiplies y by R(lam h), R(z) = 1 + z + z^2/2 + z^3/6 + z^4/24, so the samples are the
+    running products of R over that exact step sequence."""
+    lam = -0.4 + 2.1j
+
+    class Lin(rk.RTCC):
+        def __init__(self):
+            pass
+
+        def rhs(self, tt, y, fld):
+            return lam * y
+
+        def dipole(self, y):
+            return y.copy()
+
+    integ = rk.Integrator(method="mixed", h1=0.1, h2=0.25, t_switch=0.33, t_end=1.5)
+    tt, mm, _, st = rk.propagate(Lin(), np.array([1.0 + 0j]), None, integ)
+    steps = [0.1, 0.1, 0.1, 0.03, 0.25, 0.25, 0.25, 0.25, 0.17]
+    assert np.allclose(np.diff(tt), steps, rtol=0, atol=1e-12) and st["accepted"] == len(steps)
+    R = lambda z: 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+    want = np.cumprod([1.0 + 0j] + [R(lam * h) for h in np.diff(tt)])
+    assert np.abs(mm[:, 0] - want).max() < 1e-14
+
+
 def test_ck_local_error_orders_on_linear_ode():
     lam = -0.3 + 1.7j
     class Lin(rk.RTCC):
