@@ -26,6 +26,32 @@ def _system(o, v, seed=7, offdiag=0.1):
 
 # --- residual equations ------------------------------------------------------------
 
+def test_brute_force_reduces_to_slater_condon_rules_at_zero_amplitudes():
+    """With T = Lambda = 0 the determinant-space definitions reduce to textbook matrix elements
+    between determinants (Slater-Condon rules), independent of the bit-string machinery:
+    <Phi_i^a|H|Phi_0> = f_ia, <Phi_ij^ab|H|Phi_0> = <ab||ij>, R_mu = <Phi_0|H|Phi_mu>, the
+    reference energy sum_i f_ii - 1/2 sum_ij <ij||ij>, and the reference density."""
+    o, v = 2, 3
+    f, B, _ = _system(o, v)
+    fso, w = spinorb.spin_orbital_operators(f, spinorb.eri_chemist(B))
+    N, nv = 2 * o, 2 * v
+    bc = brute.BruteCC(fso, w, N)
+    z1, z2 = np.zeros((N, nv), complex), np.zeros((N, N, nv, nv), complex)
+    o1, o2, e = bc.omega(z1, z2)
+    occ, vir = np.arange(N), N + np.arange(nv)
+    assert np.abs(o1 - fso[np.ix_(occ, vir)]).max() < 1e-13
+    assert np.abs(o2 - w[np.ix_(vir, vir, occ, occ)].transpose(2, 3, 0, 1)).max() < 1e-13
+    assert abs(e) < 1e-13
+    eref = np.trace(fso[:N, :N]) - 0.5 * np.einsum("ijij->", w[:N, :N, :N, :N])
+    assert abs(bc.Eref - eref) < 1e-12
+    r1, r2 = bc.lambda_residual(z1, z2, z1, z2)
+    assert np.abs(r1 - fso[np.ix_(occ, vir)]).max() < 1e-13
+    assert np.abs(r2 - w[np.ix_(occ, occ, vir, vir)]).max() < 1e-13
+    rho = bc.density(z1, z2, z1, z2)
+    assert np.abs(rho - np.diag([1.0] * N + [0.0] * nv)).max() < 1e-14
+    assert np.abs(o2).max() > 1e-3 and np.abs(o1).max() > 1e-3     # non-trivial values
+
+
 @pytest.mark.parametrize("o,v", [(1, 3), (2, 2), (2, 3)])
 def test_spin_orbital_residual_matches_brute_force(o, v):
     """Eq. derivT: Omega_mu = <mu|e^-T H e^T|0> for general complex spin-orbital amplitudes."""
