@@ -147,3 +147,19 @@ def test_pade_spectrum_arguments_are_checked_before_any_device_work(lib):
     with pytest.raises(lib.RtccError) as e:
         lib.rtcc_spectrum_pade(t[:2], np.zeros((2, 3)), fld, om, kappa=1.0)
     assert e.value.status == "INVALID_ARG"
+
+
+def test_binding_refuses_to_import_without_the_library(tmp_path):
+    """No CPU fallback: a copy of the package without librtcc.so raises ImportError on import."""
+    import shutil
+    import sys
+    pkg = tmp_path / "paper_2205_05175_gb300"
+    pkg.mkdir()
+    src = os.path.join(ROOT, "paper_2205_05175_gb300")
+    for fn in os.listdir(src):
+        if fn.endswith(".py"):
+            shutil.copy(os.path.join(src, fn), pkg / fn)
+    code = "import paper_2205_05175_gb300.rtcc"
+    r = subprocess.run([sys.executable, "-c", code], cwd=str(tmp_path), capture_output=True, text=True,
+                       env=dict(os.environ, PYTHONPATH=str(tmp_path)))
+    assert r.returncode != 0 and "ImportError" in r.stderr and "librtcc.so is missing" in r.stderr
