@@ -50,6 +50,10 @@ WORKLOAD = "water-hexamer-shaped RT-CCSD, o={o} v={v} naux={naux}, 12 Cash-Karp 
 E0S = (0.001, 0.01, 0.05, 0.1)
 POLS = ((1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0))
 NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25      # dense tensor-core rate ratio (nominal)
+PASSES = {0: 1, 1: 1, 2: 3, 3: 3}         # tensor-core passes per algorithmic product, per precision mode
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the same build
+# (the summary and its command are in profiles/); None until such a capture exists for the shape
+TRAFFIC = {}
 
 
 def dist_env():
@@ -82,6 +86,56 @@ def measured_peaks():
         d = json.load(open(p))
         return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("bf16_tflops_sustained", 1700.0), "measured"
     return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+def precision_peak(prec, bf16_sus, src):
+    """Rate of one algorithmic flop in a precision mode, and where it comes from."""
+    if prec == 3:
+        return bf16_sus / 3.0, f"{src}: sustained bf16 cuBLAS rate / 3 (three BF16 passes per product)"
+    if prec in (1, 2):
+        tf = measure_tf32_tflops()
+        if tf is None:
+            tf, how = bf16_sus * NOMINAL_TF32_OVER_BF16, f"{src} sustained bf16 x nominal tf32/bf16 ratio 0.49"
+        else:
+            how = "tf32 cuBLAS rate measured in this run (8192^3, best of 10)"
+        return (tf / 3.0, how + " / 3 (three TF32 passes)") if prec == 2 else (tf, how)
+    f64 = measure_f64_tflops()
+    return f64, "float64 cuBLAS rate measured in this run (8192^3, best of 5)"
+
+
+def _matmul_tflops(dtype, n=8192, reps=10, tf32=False):
+    import torch
+    old = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = tf32
+    try:
+        a = torch.randn(n, n, device="cuda", dtype=dtype)
+        b = torch.randn(n, n, device="cuda", dtype=dtype)
+        torch.matmul(a, b)
+        best = float("inf")
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        del a, b
+        return 2.0 * n ** 3 / best / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
+
+
+def measure_tf32_tflops():
+    try:
+        import torch
+        return _matmul_tflops(torch.float32, tf32=True)
+    except Exception:
+        return None
+
+
+def measure_f64_tflops():
+    import torch
+    return _matmul_tflops(torch.float64, reps=5)
 
 
 class ClockSampler:
@@ -135,27 +189,10 @@ class ClockSampler:
 
 # --- CPU oracle timing (reference arm and cpu_baseline) ------------------------------
 
-def oracle_sample(o=30, v=114, repeats=1, warmup=0):
-    """Time the oracle on a bounded sample of the workload: one T-residual evaluation of one
-    trajectory at the full shape, scaled to a full right-hand side by the RHS / T-residual cost
-    ratio measured at the dimer shape, and to a Cash-Karp step by its six evaluations."""
-    import numpy as np
-
+def _omega_seconds(o, v, repeats, warmup):
+    """Median wall time of the oracle's T-residual (one trajectory) at (o, v) after warm-up runs."""
     from oracle import closed, rk
     from paper_2205_05175_gb300 import synth
-    # ratio at the dimer shape
-    f, B, mu = synth.make_system(10, 38)
-    s = rk.RTCC(f, B, mu, 10)
-    t1, t2 = synth.random_amplitudes(10, 38, seed=1, s1=0.01, s2=0.005)
-    l1, l2 = synth.random_amplitudes(10, 38, seed=2, s1=0.01, s2=0.005)
-    closed.omega(t1, t2, s.f, s.V)
-    a = time.perf_counter()
-    closed.omega(t1, t2, s.f, s.V)
-    tom = time.perf_counter() - a
-    a = time.perf_counter()
-    closed.rhs(t1, t2, l1, l2, s.f, s.V)
-    trhs = time.perf_counter() - a
-    ratio = trhs / tom
     f, B, mu = synth.make_system(o, v)
     s = rk.RTCC(f, B, mu, o)
     t1, t2 = synth.random_amplitudes(o, v, seed=1, s1=0.01, s2=0.005)
@@ -168,29 +205,112 @@ def oracle_sample(o=30, v=114, repeats=1, warmup=0):
         a = time.perf_counter()
         closed.omega(t1, t2, s.f, s.V)
         times.append(time.perf_counter() - a)
-    t_step = min(times) * ratio * 6.0
-    return {"value": 1.0 / t_step, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"one T-residual evaluation of one trajectory at o={o},v={v} ({min(times):.1f} s, "
-                       f"min of {repeats} after {warmup} untimed) x RHS/T-residual ratio {ratio:.2f} (measured at o=10,v=38) x 6 "
-                       f"right-hand sides per Cash-Karp step; numpy float64/complex128, BLAS threads = all cores")}
+    return statistics.median(times), times
+
+
+def _rhs_over_omega(o=10, v=38, repeats=3):
+    """Cost of a full right-hand side (T and Lambda residuals) over a T-residual, measured at
+    the dimer shape (median of `repeats` after one untimed run of each)."""
+    from oracle import closed, rk
+    from paper_2205_05175_gb300 import synth
+    f, B, mu = synth.make_system(o, v)
+    s = rk.RTCC(f, B, mu, o)
+    t1, t2 = synth.random_amplitudes(o, v, seed=1, s1=0.01, s2=0.005)
+    l1, l2 = synth.random_amplitudes(o, v, seed=2, s1=0.01, s2=0.005)
+    closed.omega(t1, t2, s.f, s.V)
+    closed.rhs(t1, t2, l1, l2, s.f, s.V)
+    tom, trhs = [], []
+    for _ in range(repeats):
+        a = time.perf_counter()
+        closed.omega(t1, t2, s.f, s.V)
+        tom.append(time.perf_counter() - a)
+        a = time.perf_counter()
+        closed.rhs(t1, t2, l1, l2, s.f, s.V)
+        trhs.append(time.perf_counter() - a)
+    return statistics.median(trhs) / statistics.median(tom)
+
+
+def _single_thread_omega(o, v, repeats, warmup):
+    """The same T-residual timing in a child process whose BLAS runs one thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", VECLIB_MAXIMUM_THREADS="1")
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "m, t = bench._omega_seconds(%d, %d, %d, %d); print(json.dumps([m, t]))" % (ROOT, o, v, repeats, warmup))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, cwd=ROOT)
+    if r.returncode != 0:
+        return None
+    return json.loads(r.stdout.strip().splitlines()[-1])[0]
+
+
+def oracle_sample(o=30, v=114, repeats=3, warmup=1, single_thread=True):
+    """Time the oracle on a bounded sample of the workload and scale it to trajectory-steps/s:
+    the T-residual of one trajectory at the full shape (median of `repeats` after `warmup`
+    untimed runs, BLAS on all cores) x the RHS / T-residual cost ratio measured at the dimer shape
+    x 6 right-hand sides per Cash-Karp step.  With single_thread, the same T-residual is timed with
+    one BLAS thread at the tetramer shape (o=20, v=76) and scaled to the full shape by the oracle's
+    own flop count (tests/golden/rhs_flops.json)."""
+    ratio = _rhs_over_omega()
+    med, times = _omega_seconds(o, v, repeats, warmup)
+    t_step = med * ratio * 6.0
+    out = {"value": 1.0 / t_step, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": (f"T-residual of one trajectory at o={o},v={v}: median {med:.2f} s of {repeats} runs "
+                      f"({', '.join(f'{x:.2f}' for x in times)}) after {warmup} untimed, x RHS/T-residual cost ratio "
+                      f"{ratio:.2f} (median of 3 at o=10,v=38) x 6 right-hand sides per Cash-Karp step; numpy "
+                      f"complex128, BLAS threads = all {os.cpu_count()} cores"),
+           "sample_seconds": med, "rhs_over_omega": ratio}
+    if single_thread:
+        ot, vt = 20, 76
+        m1 = _single_thread_omega(ot, vt, 3, 1)
+        if m1 is not None:
+            fl = _flop_table()
+            scale = _omega_flops(fl, o, v) / _omega_flops(fl, ot, vt)
+            out["single_thread"] = {"value": 1.0 / (m1 * scale * ratio * 6.0), "unit": UNIT, "cores": 1,
+                                    "sample": (f"T-residual at o={ot},v={vt} with one BLAS thread: median {m1:.2f} s "
+                                               f"of 3 after 1 untimed, x {scale:.1f} (oracle flop ratio of the "
+                                               f"T-residual, o={o},v={v} over o={ot},v={vt}) x {ratio:.2f} x 6")}
+    return out
+
+
+def _flop_table():
+    return json.load(open(os.path.join(ROOT, "tests", "golden", "rhs_flops.json")))["rows"]
+
+
+def _omega_flops(rows, o, v):
+    return sum(c * float(o) ** p * float(v) ** q for _, ph, c, p, q in rows if ph == "omega")
+
+
+def rhs_flops(o, v):
+    """Algorithmic real flops of one right-hand side (T and Lambda residuals) of one trajectory:
+    the oracle's per-term count (tests/golden/rhs_flops.json, written by
+    tests/golden/make_rhs_flops.py) evaluated at (o, v)."""
+    return sum(c * float(o) ** p * float(v) ** q for _, _, c, p, q in _flop_table())
 
 
 def run_reference(args, rank, world):
+    """The oracle as the reference arm.  One full trajectory step of this workload is minutes of
+    CPU time, so each of the K timed steps (and each of the W untimed ones) is one bounded
+    sample: the oracle's T-residual of one trajectory at the full shape.  ms_per_step is that
+    sample's time; value scales it to trajectory-steps/s by the measured RHS / T-residual ratio
+    and the six right-hand sides of a Cash-Karp step."""
     if rank != 0:
         return 0
-    steps = max(1, min(args.steps, 4))
-    warm = max(0, min(getattr(args, "warmup", 0), 3))
     o, v = getattr(args, "o", 30), getattr(args, "v", 114)
     t0 = time.perf_counter()
-    r = oracle_sample(o=o, v=v, repeats=steps, warmup=warm)
+    ratio = _rhs_over_omega()
+    med, times = _omega_seconds(o, v, args.steps, args.warmup)
     wall = time.perf_counter() - t0
-    line = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": args.gpus,
-            "steps": steps, "warmup": warm, "ms_per_step": 1e3 / r["value"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD.format(o=o, v=v, naux=4 * (o + v)), "sample": r["sample"]},
-            "cpu_baseline": {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle",
-                             "sample": r["sample"]},
-            "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    value = 1.0 / (med * ratio * 6.0)
+    sample = (f"each step is one sample: the oracle's T-residual of one trajectory at o={o},v={v} (median "
+              f"{med:.2f} s over {args.steps} timed after {args.warmup} untimed), scaled to trajectory-steps/s by the "
+              f"RHS/T-residual cost ratio {ratio:.2f} (o=10,v=38) and 6 right-hand sides per Cash-Karp step; numpy "
+              f"complex128, BLAS threads = all {os.cpu_count()} cores")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "step_kind": "sample (one T-residual evaluation of one trajectory)",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.format(o=o, v=v, naux=4 * (o + v)), "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
     print(json.dumps(line), flush=True)
     return 0
@@ -522,19 +642,31 @@ def run_gpu(args, rank, world, local):
     dom = max(prof, key=lambda k: prof[k]["ms"])
     d = prof[dom]
     hbm, bf16, bf16_sus, src = measured_peaks()
-    if dom in ("tc_gemm", "f64_gemm"):
-        peak = bf16_sus if prec == rtcc.P32_BF16X3 else bf16_sus * NOMINAL_TF32_OVER_BF16
-        roof = {"bound": "tensor", "achieved": d["flops"] / (d["ms"] / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s"}
-        if dom == "f64_gemm":
-            roof["bound"] = "alu"
+    alg_rhs = rhs_flops(o, v)
+    if dom == "tc_gemm":
+        # algorithmic flops: the oracle's per-term count of one right-hand side x the trajectory
+        # right-hand sides evaluated in the timed region, over the tensor-core GEMM's device time;
+        # the peak is the rate of one algorithmic flop in this precision (a third of the sustained
+        # bf16 rate for the three BF16x3 passes; TF32 measured by cuBLAS on this GPU)
+        peak, psrc = precision_peak(prec, bf16_sus, src)
+        roof = {"bound": "tensor", "achieved": alg_rhs * nrhs / (d["ms"] / 1e3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "algorithmic_flops_per_rhs": alg_rhs, "rhs_evaluations": nrhs,
+                "executed_tflops": d["flops"] / (d["ms"] / 1e3) / 1e12,
+                "executed_frac_of_bf16_sustained": d["flops"] / (d["ms"] / 1e3) / 1e12 / bf16_sus,
+                "executed_over_algorithmic": d["flops"] / max(1.0, alg_rhs * nrhs) / PASSES[prec],
+                "peak_source": psrc}
+    elif dom == "f64_gemm":
+        peak, psrc = precision_peak(prec, bf16_sus, src)
+        roof = {"bound": "alu", "achieved": alg_rhs * nrhs / (d["ms"] / 1e3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "algorithmic_flops_per_rhs": alg_rhs, "rhs_evaluations": nrhs, "peak_source": psrc}
     else:
-        roof = {"bound": "hbm", "achieved": d["bytes"] / (d["ms"] / 1e3) / 1e9, "peak": hbm, "unit": "GB/s"}
+        roof = {"bound": "hbm", "achieved": d["bytes"] / (d["ms"] / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "peak_source": f"{src} copy bandwidth"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = TRAFFIC.get((o, v, nz, args.prec))
     roof["kernel"] = dom
     roof["launches"] = d["launches"]
     roof["avg_launch_ms"] = d["ms"] / max(1, d["launches"])
-    roof["peak_source"] = f"{src} (bf16 sustained{'' if prec == rtcc.P32_BF16X3 else ' x nominal tf32/bf16 ratio 0.49'})"
     share = {k: round(prof[k]["ms"] / max(1e-9, sum(p["ms"] for p in prof.values())), 4) for k in prof}
     if args.skip_e2e:
         acc_e2e, ms_e2e, h2d, d2h = acc, ms_max, 0.0, 0.0
@@ -575,7 +707,7 @@ def run_gpu(args, rank, world, local):
                 "dipole_error_vs_f64": {"value": derr, "unit": "au",
                                         "config": "o=10,v=38, RK4 h=0.02, 50 steps, E0=0.01 z sine pulse"}}
         if not args.skip_cpu_baseline and world == 1:
-            line["cpu_baseline"] = oracle_sample(repeats=1)
+            line["cpu_baseline"] = oracle_sample()
         print(json.dumps(line), flush=True)
     return 0
 

@@ -173,6 +173,15 @@ rtcc_status_t rtcc_set_state(rtcc_handle_t h, int traj, const double* y, double 
 rtcc_status_t rtcc_rhs(rtcc_handle_t h, const double* y, const rtcc_field_t* fields,
                        const double* times, double* dydt);
 
+/* Vector-Jacobian product of the right-hand side rtcc_rhs computes (Eqs. derivT/derivL; the
+ * transposed Jacobian is what the adjoint of the propagation applies at every stage):
+ *   ybar_z = (d dydt_z / d y_z)^T u_z      (holomorphic: no complex conjugation)
+ * at the states y, the fields and the times of rtcc_rhs.  y, u: host or device, ntraj *
+ * state_size complex; ybar: host or device, same size (output).  Uses the handle's adjoint
+ * engine (built on the first call).  Errors: INVALID_ARG, OOM, CUDA, TIMEOUT. */
+rtcc_status_t rtcc_rhs_vjp(rtcc_handle_t h, const double* y, const rtcc_field_t* fields,
+                           const double* times, const double* u, double* ybar);
+
 /* Dipole of every trajectory's current state (Eq. dipole): mu_out host or device,
  * ntraj*3 complex. */
 rtcc_status_t rtcc_dipole(rtcc_handle_t h, double* mu_out);

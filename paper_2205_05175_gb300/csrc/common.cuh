@@ -200,6 +200,9 @@ void tc_gemm_plan(TcGemmPlan& pl, int kind, const void* A, int planesA, const vo
                   long long N, long long Kpad, long long NB, int* err);
 void launch_tc_gemm(const TcGemmPlan& p, cudaStream_t s);
 int tc_kblock_elems(int kind);   // K elements per 128-byte block: 32 (tf32) or 64 (bf16)
+// Streaming multiprocessors of the current device (queried once per device; 152 on GB300).
+// Grid sizes, split-K decisions and wave counts are all taken from this number.
+int device_sm_count();
 
 // 32-bit mixed-radix decode of one index group (extents < 2^31 per group).
 __device__ __forceinline__ long long imap32(const IndexMap& m, unsigned idx) {

@@ -463,7 +463,7 @@ void Engine::plan(Program& P) {
       k.kind = CK_SMALLMN;   // few outputs per batch entry, long K: staged SIMT reduction
     } else if (nout <= kReduceMaxOut && K >= 256) {
       k.kind = CK_REDUCE;
-      long long want = std::max(1ll, (152ll * 8) / std::max(1ll, nout));
+      long long want = std::max(1ll, ((long long)device_sm_count() * 8) / std::max(1ll, nout));
       k.splits = std::max(1ll, std::min(want, (K + 1023) / 1024));
     } else if (work < kDirectMaxWork) {
       k.kind = CK_DIRECT;

@@ -515,14 +515,11 @@ void launch_inst(const TcGemmPlan& pl, cudaStream_t s) {
   constexpr size_t sm = smem_bytes<BN, KIND, STAGES, EPW>();
   static_assert(sm <= 227 * 1024, "shared memory budget");
   static bool attr = false;
-  static int nsm = 0;
   if (!attr) {
     RTCC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    int dev = 0;
-    RTCC_CUDA(cudaGetDevice(&dev));
-    RTCC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     attr = true;
   }
+  const int nsm = device_sm_count();
   const long long tiles = (long long)((pl.p.M + BM - 1) / BM) * ((pl.p.N + BN - 1) / BN);
   const long long items = tiles * (pl.p.fused ? 1 : pl.p.nrb) * pl.splits * pl.NB;
   RTCC_REQUIRE(items < (1ll << 31), "too many GEMM tiles");
@@ -558,7 +555,8 @@ void tc_gemm_plan(TcGemmPlan& pl, int kind, const void* A, int planesA, const vo
   const long long tiles = ((M + BM - 1) / BM) * ((N + pl.bn - 1) / pl.bn) * NB * (pl.p.fused ? 1 : pl.p.nrb);
   const int nv = pl.p.nseg[0] * pl.p.nkb;
   int splits = 1;
-  if (tiles < 152 && nv >= 32) splits = (int)std::max(1ll, std::min<long long>((2 * 152 + tiles - 1) / tiles, nv / 16));
+  const long long nsm = device_sm_count();
+  if (tiles < nsm && nv >= 32) splits = (int)std::max(1ll, std::min<long long>((2 * nsm + tiles - 1) / tiles, nv / 16));
   splits = std::min(splits, 64);
   pl.p.vper = (nv + splits - 1) / splits;
   pl.splits = (nv + pl.p.vper - 1) / pl.p.vper;

@@ -18,13 +18,33 @@
 #include <type_traits>
 
 namespace rtcc {
+
+int device_sm_count() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 152;
+  }
+  if (cache[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      n = 152;
+    }
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
 namespace {
 
 constexpr int kThreads = 256;
 
 inline unsigned grid_for(long long n, int threads = kThreads) {
   long long b = (n + threads - 1) / threads;
-  if (b > 152ll * 64) b = 152ll * 64;   // grid-stride beyond 64 blocks per SM
+  const long long cap = (long long)device_sm_count() * 64;   // grid-stride beyond 64 blocks per SM
+  if (b > cap) b = cap;
   if (b < 1) b = 1;
   return (unsigned)b;
 }
@@ -921,7 +941,7 @@ void launch_pack(const PackDesc& d, cudaStream_t s) {
     if (d.transpose) {
       const long long nkt = (d.Kpad + 63) / 64, nrt = (NR + 31) / 32;
       // each block walks several k tiles of one row tile (the row offsets are decoded once)
-      const long long gx = std::max(1ll, std::min(nkt, (152ll * 32 + nrt - 1) / nrt));
+      const long long gx = std::max(1ll, std::min(nkt, ((long long)device_sm_count() * 32 + nrt - 1) / nrt));
       dim3 grid((unsigned)gx, (unsigned)std::min(nrt, 65535ll));
       dim3 blk(32, 8);
       if (d.elem == PE_F32) pack_planes_transpose_kernel<PE_F32><<<grid, blk, 0, s>>>(d);
@@ -1006,7 +1026,7 @@ void launch_smallmn(const DirectDesc& d, cudaStream_t s) {
                "small-output reduction extents");
   if (d.NB * d.M * d.N == 0 || d.K == 0) return;
   // about four blocks per SM in total, whole 64-wide chunks per block
-  long long splits = std::max(1ll, std::min((152ll * 4 + d.NB - 1) / d.NB, (d.K + kSmallKC - 1) / kSmallKC));
+  long long splits = std::max(1ll, std::min(((long long)device_sm_count() * 4 + d.NB - 1) / d.NB, (d.K + kSmallKC - 1) / kSmallKC));
   long long kper = (d.K + splits - 1) / splits;
   kper = (kper + kSmallKC - 1) / kSmallKC * kSmallKC;
   splits = (d.K + kper - 1) / kper;
@@ -1050,8 +1070,9 @@ void launch_gemm_f64(const double* A, const double* B, double* C, long long M, l
   RTCC_REQUIRE(M < (1ll << 31) && N < (1ll << 31) && Kpad < (1ll << 31) && NB < 65536, "GEMM extents too large");
   const long long tiles = ((N + 63) / 64) * ((M + 63) / 64) * NB;
   int splits = 1;
-  if (tiles < 2 * 152 && Kpad >= 512)
-    splits = (int)std::max(1ll, std::min<long long>((4 * 152 + tiles - 1) / tiles, Kpad / 256));
+  const long long nsm = device_sm_count();
+  if (tiles < 2 * nsm && Kpad >= 512)
+    splits = (int)std::max(1ll, std::min<long long>((4 * nsm + tiles - 1) / tiles, Kpad / 256));
   splits = (int)std::min<long long>(splits, 65535 / NB);
   const int kper = (int)(((Kpad + splits - 1) / splits + 15) / 16 * 16);
   splits = (int)((Kpad + kper - 1) / kper);

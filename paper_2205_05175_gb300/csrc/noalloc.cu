@@ -96,10 +96,8 @@ void plane_desc(rtcc::PackDesc& pd, const double* src, bool cplx, long long rows
   pd.dst = dst;
 }
 
-}  // namespace
-
-extern "C" rtcc_status_t rtcc_gemm_noalloc(int prec, int cplx, int batch, int M, int N, int K, const double* A,
-                                           const double* Bm, double* C, void* stream) {
+rtcc_status_t gemm_noalloc(int prec, int cplx, int batch, int M, int N, int K, const double* A, const double* Bm,
+                           double* C, void* stream) {
   using namespace rtcc;
   if (prec < RTCC_P32_TF32 || prec > RTCC_P32_BF16X3)
     return fail(RTCC_ERR_INVALID_ARG, "rtcc_gemm_noalloc: precision must be TF32, 3xTF32 or BF16x3");
@@ -122,52 +120,65 @@ extern "C" rtcc_status_t rtcc_gemm_noalloc(int prec, int cplx, int batch, int M,
     return fail(RTCC_ERR_INVALID_ARG, "rtcc_gemm_noalloc: packed operands need " + std::to_string(bytesA + bytesB) +
                                           " bytes of scratch, more than the " + std::to_string(kScratchBytes) +
                                           "-byte static limit");
-  try {
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    unsigned char* scr = static_cast<unsigned char*>(ds.scratch);
-    PackDesc pa, pb;
-    plane_desc(pa, A, ac, M, K, batch, npart, elem, Kpad, scr);
-    plane_desc(pb, Bm, bc, N, K, batch, npart, elem, Kpad, scr + bytesA);
-    TcGemmPlan pl{};
-    TcGemmParams& g = pl.p;
-    g.nrb = cc ? 2 : 1;
-    auto plane = [&](int c, int q) { return c * npart + q; };
-    auto pair = [&](int rb, int ca, int cb, int neg) {
-      auto push = [&](int x, int y) { g.seg[rb][g.nseg[rb]++] = TcSeg{x, y, neg}; };
-      if (npart == 1) push(plane(ca, 0), plane(cb, 0));
-      else {
-        push(plane(ca, 0), plane(cb, 0));
-        push(plane(ca, 0), plane(cb, 1));
-        push(plane(ca, 1), plane(cb, 0));
-      }
-    };
-    if (!ac && !bc) pair(0, 0, 0, 0);
-    else if (ac && !bc) { pair(0, 0, 0, 0); pair(1, 1, 0, 0); }
-    else if (!ac && bc) { pair(0, 0, 0, 0); pair(1, 0, 1, 0); }
-    else { pair(0, 0, 0, 0); pair(0, 1, 1, 1); pair(1, 0, 1, 0); pair(1, 1, 0, 0); }
-    TcEpilogue& ep = g.epi;
-    ep.C = C;
-    ep.c_cplx = cc;
-    ep.alpha = 1.0;
-    ep.cm = map1(M, N);
-    ep.cn = map1(N, 1);
-    ep.cb = map1(batch, (long long)M * N);
-    ep.flat_n = 1;
-    ep.sn = 1;
-    ep.unit_n = 1;
-    // the output is overwritten; the error word keeps no state from an earlier call
-    RTCC_CUDA(cudaMemsetAsync(C, 0, sizeof(double) * (size_t)batch * M * N * (cc ? 2 : 1), s));
-    RTCC_CUDA(cudaMemsetAsync(ds.err, 0, sizeof(int) * 4, s));
-    launch_pack(pa, s);
-    launch_pack(pb, s);
-    tc_gemm_plan(pl, kind, pa.dst, planesA, pb.dst, planesB, M, N, Kpad, batch, ds.err);
-    launch_tc_gemm(pl, s);
-    int h = 0;
-    RTCC_CUDA(cudaMemcpyAsync(&h, ds.err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    RTCC_CUDA(cudaStreamSynchronize(s));
-    if (h != DEV_OK) return fail(RTCC_ERR_TIMEOUT, "rtcc_gemm_noalloc: a tensor-core wait expired on the device");
-  } catch (const Error& e) {
-    return fail(e.status, e.what());
-  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned char* scr = static_cast<unsigned char*>(ds.scratch);
+  PackDesc pa, pb;
+  plane_desc(pa, A, ac, M, K, batch, npart, elem, Kpad, scr);
+  plane_desc(pb, Bm, bc, N, K, batch, npart, elem, Kpad, scr + bytesA);
+  TcGemmPlan pl{};
+  TcGemmParams& g = pl.p;
+  g.nrb = cc ? 2 : 1;
+  auto plane = [&](int c, int q) { return c * npart + q; };
+  auto pair = [&](int rb, int ca, int cb, int neg) {
+    auto push = [&](int x, int y) { g.seg[rb][g.nseg[rb]++] = TcSeg{x, y, neg}; };
+    if (npart == 1) push(plane(ca, 0), plane(cb, 0));
+    else {
+      push(plane(ca, 0), plane(cb, 0));
+      push(plane(ca, 0), plane(cb, 1));
+      push(plane(ca, 1), plane(cb, 0));
+    }
+  };
+  if (!ac && !bc) pair(0, 0, 0, 0);
+  else if (ac && !bc) { pair(0, 0, 0, 0); pair(1, 1, 0, 0); }
+  else if (!ac && bc) { pair(0, 0, 0, 0); pair(1, 0, 1, 0); }
+  else { pair(0, 0, 0, 0); pair(0, 1, 1, 1); pair(1, 0, 1, 0); pair(1, 1, 0, 0); }
+  TcEpilogue& ep = g.epi;
+  ep.C = C;
+  ep.c_cplx = cc;
+  ep.alpha = 1.0;
+  ep.cm = map1(M, N);
+  ep.cn = map1(N, 1);
+  ep.cb = map1(batch, (long long)M * N);
+  ep.flat_n = 1;
+  ep.sn = 1;
+  ep.unit_n = 1;
+  // the output is overwritten; the error word keeps no state from an earlier call
+  RTCC_CUDA(cudaMemsetAsync(C, 0, sizeof(double) * (size_t)batch * M * N * (cc ? 2 : 1), s));
+  RTCC_CUDA(cudaMemsetAsync(ds.err, 0, sizeof(int) * 4, s));
+  launch_pack(pa, s);
+  launch_pack(pb, s);
+  tc_gemm_plan(pl, kind, pa.dst, planesA, pb.dst, planesB, M, N, Kpad, batch, ds.err);
+  launch_tc_gemm(pl, s);
+  int h = 0;
+  RTCC_CUDA(cudaMemcpyAsync(&h, ds.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RTCC_CUDA(cudaStreamSynchronize(s));
+  if (h != DEV_OK) return fail(RTCC_ERR_TIMEOUT, "rtcc_gemm_noalloc: a tensor-core wait expired on the device");
   return RTCC_OK;
+}
+
+}  // namespace
+
+// Every exception (the library's own errors, and std::exception from the scratch table or a
+// message string) becomes a status code: nothing leaves this extern "C" function.
+extern "C" rtcc_status_t rtcc_gemm_noalloc(int prec, int cplx, int batch, int M, int N, int K, const double* A,
+                                           const double* Bm, double* C, void* stream) {
+  try {
+    return gemm_noalloc(prec, cplx, batch, M, N, K, A, Bm, C, stream);
+  } catch (const rtcc::Error& e) {
+    return fail(e.status, e.what());
+  } catch (const std::exception& e) {
+    return fail(RTCC_ERR_CUDA, std::string("rtcc_gemm_noalloc: ") + e.what());
+  } catch (...) {
+    return fail(RTCC_ERR_CUDA, "rtcc_gemm_noalloc: unknown exception");
+  }
 }

@@ -684,7 +684,7 @@ __global__ void k_wait_flag(const volatile int* flag, unsigned long long ns, int
 
 inline unsigned blocks_for(long long n, int threads = 256) {
   long long b = (n + threads - 1) / threads;
-  return (unsigned)std::max(1ll, std::min(b, 152ll * 32));
+  return (unsigned)std::max(1ll, std::min(b, (long long)device_sm_count() * 32));
 }
 
 bool is_device_ptr(const void* p) {
@@ -1324,6 +1324,35 @@ rtcc_status_t rtcc_rhs(rtcc_handle_t h, const double* y, const rtcc_field_t* fie
     h->E->check_error();
     copy_out(dydt, h->Ynew, bytes, h->stream);
     RTCC_CUDA(cudaStreamSynchronize(h->stream));
+  });
+}
+
+rtcc_status_t rtcc_rhs_vjp(rtcc_handle_t h, const double* y, const rtcc_field_t* fields, const double* times,
+                           const double* u, double* ybar) {
+  if (!h || !y || !fields || !times || !u || !ybar) return fail(RTCC_ERR_INVALID_ARG, "null argument");
+  return guarded([&] {
+    AdjointEngine* a = adjoint_engine(h);
+    cudaStream_t s = h->stream;
+    const size_t bytes = sizeof(double) * 2 * h->ns * h->nz;
+    copy_in(a->Ys, y, bytes, s);
+    RTCC_CUDA(cudaMemcpyAsync(h->d_fields, fields, sizeof(rtcc_field_t) * h->nz, cudaMemcpyHostToDevice, s));
+    RTCC_CUDA(cudaMemcpyAsync(a->tdev, times, sizeof(double) * h->nz, cudaMemcpyHostToDevice, s));
+    RTCC_CUDA(cudaMemsetAsync(a->hdev, 0, sizeof(double) * h->nz, s));
+    k_fock<<<dim3(blocks_for((long long)h->nmo * h->nmo), h->nz), 256, 0, s>>>(a->F, h->f0, h->mu, h->d_fields,
+                                                                              a->tdev, a->hdev, 0.0, h->nz,
+                                                                              h->nmo * h->nmo);
+    // the VJP program reads the intermediates of the last forward and reverse sweeps at y
+    a->E->run(a->rhs.fwd);
+    a->E->run(a->rhs.rev);
+    // dydt = D raw with D = diag(-i on the T part, +i on the Lambda part), so the cotangent of the
+    // raw output is D u (D is diagonal and its own transpose)
+    copy_in(a->abar, u, bytes, s);
+    k_apply_D<<<blocks_for(h->ns * h->nz), 256, 0, s>>>(a->cot, a->abar, h->ns, h->nT, h->nz);
+    a->E->run(a->vjp);
+    RTCC_CUDA(cudaGetLastError());
+    a->E->check_error();
+    copy_out(ybar, a->ybar, bytes, s);
+    RTCC_CUDA(cudaStreamSynchronize(s));
   });
 }
 

@@ -64,6 +64,7 @@ _sig = {
     "rtcc_get_state": [_vp, C.c_int, _vp, _dp, _dp],
     "rtcc_set_state": [_vp, C.c_int, _vp, C.c_double, C.c_double],
     "rtcc_rhs": [_vp, _vp, C.POINTER(rtcc_field_t), _vp, _vp],
+    "rtcc_rhs_vjp": [_vp, _vp, C.POINTER(rtcc_field_t), _vp, _vp, _vp],
     "rtcc_dipole": [_vp, _vp],
     "rtcc_propagate": [_vp, C.POINTER(rtcc_field_t), C.POINTER(rtcc_integrator_t), C.c_int, _vp, _vp, _ip],
     "rtcc_last_stats": [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
@@ -196,6 +197,17 @@ class Handle:
         _check(_lib.rtcc_rhs(self.h, _ptr(y), fa, _ptr(tms), _ptr(out)))
         return out
 
+    def rhs_vjp(self, y, fields, times, u):
+        """(d dydt / dy)^T u for every trajectory at the states y (holomorphic; host arrays)."""
+        fa = (rtcc_field_t * self.ntraj)(*fields)
+        tms = _as_c(times)
+        y = np.ascontiguousarray(y, dtype=complex)
+        u = np.ascontiguousarray(u, dtype=complex)
+        assert y.shape == u.shape == (self.ntraj, self.ns)
+        out = np.zeros_like(y)
+        _check(_lib.rtcc_rhs_vjp(self.h, _ptr(y), fa, _ptr(tms), _ptr(u), _ptr(out)))
+        return out
+
     def dipole(self):
         out = np.zeros((self.ntraj, 3), complex)
         _check(_lib.rtcc_dipole(self.h, _ptr(out)))
@@ -272,17 +284,47 @@ def rtcc_selftest_gemm(prec, A, B):
     return Cm
 
 
+def _check_noalloc_args(A, B, Cout):
+    """The checks rtcc_gemm_noalloc needs before it hands raw device pointers to the library:
+    dtypes, shapes, contiguity and one CUDA device for all three tensors (ValueError otherwise)."""
+    import torch
+    for name, t in (("A", A), ("B", B), ("Cout", Cout)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if t.dtype not in (torch.float64, torch.complex128):
+            raise ValueError(f"{name} must be float64 or complex128, not {t.dtype}")
+        if t.dim() != 3:
+            raise ValueError(f"{name} must have three dimensions (batch, rows, K or columns)")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    nb, M, K = A.shape
+    N = B.shape[1]
+    if tuple(B.shape) != (nb, N, K):
+        raise ValueError(f"B has shape {tuple(B.shape)}, expected (batch, N, K) = ({nb}, N, {K})")
+    if tuple(Cout.shape) != (nb, M, N):
+        raise ValueError(f"Cout has shape {tuple(Cout.shape)}, expected ({nb}, {M}, {N})")
+    want = torch.complex128 if (A.is_complex() or B.is_complex()) else torch.float64
+    if Cout.dtype != want:
+        raise ValueError(f"Cout must be {want} for these inputs, not {Cout.dtype}")
+    if min(nb, M, N, K) < 1:
+        raise ValueError("empty GEMM")
+    devs = {t.device for t in (A, B, Cout)}
+    if len(devs) != 1 or next(iter(devs)).type != "cuda":
+        raise ValueError(f"A, B and Cout must be on one CUDA device, got {sorted(str(d) for d in devs)}")
+    return nb, M, N, K
+
+
 def rtcc_gemm_noalloc(prec, A, B, Cout, stream=None):
     """C[b] = A[b] @ B[b]^T on the GPU without any allocation by the library.
 
-    A (batch x M x K), B (batch x N x K) and Cout (batch x M x N) are contiguous CUDA tensors of
-    dtype float64 or complex128; Cout is overwritten.  For callers that own all device memory
-    themselves: the library's scratch is a fixed static device array.
+    A (batch x M x K), B (batch x N x K) and Cout (batch x M x N) are contiguous CUDA tensors on
+    one device, of dtype float64 or complex128 (Cout complex128 when either input is complex);
+    Cout is overwritten.  For callers that own all device memory themselves: the library's
+    scratch is a fixed static device array.  Bad dtypes, shapes or devices raise ValueError
+    before anything reaches the device.
     """
+    nb, M, N, K = _check_noalloc_args(A, B, Cout)
     ac, bc = A.is_complex(), B.is_complex()
-    nb, M, K = A.shape
-    N = B.shape[1]
-    assert Cout.shape == (nb, M, N) and Cout.is_complex() == (ac or bc)
     st = stream.cuda_stream if stream is not None else 0
     _check(_lib.rtcc_gemm_noalloc(int(prec), int(ac) | (int(bc) << 1), nb, M, N, K, _ptr(A), _ptr(B), _ptr(Cout),
                                   C.c_void_p(st)))

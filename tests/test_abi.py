@@ -163,3 +163,27 @@ def test_binding_refuses_to_import_without_the_library(tmp_path):
     r = subprocess.run([sys.executable, "-c", code], cwd=str(tmp_path), capture_output=True, text=True,
                        env=dict(os.environ, PYTHONPATH=str(tmp_path)))
     assert r.returncode != 0 and "ImportError" in r.stderr and "librtcc.so is missing" in r.stderr
+
+
+def test_noalloc_binding_rejects_bad_tensors_before_the_device(lib):
+    """rtcc_gemm_noalloc hands raw pointers to the library, so the binding refuses wrong dtypes,
+    shapes and devices with ValueError (CPU tensors here: nothing reaches a GPU)."""
+    import torch
+    ok_a = torch.zeros((2, 5, 7), dtype=torch.float64)
+    ok_b = torch.zeros((2, 3, 7), dtype=torch.float64)
+    ok_c = torch.zeros((2, 5, 3), dtype=torch.float64)
+    bad = [
+        (ok_a, ok_b, torch.zeros((2, 5, 3), dtype=torch.complex64)),           # complex64 output
+        (ok_a.float(), ok_b, ok_c),                                             # float32 input
+        (ok_a.to(torch.complex64), ok_b, ok_c),                                 # complex64 input
+        (ok_a, torch.zeros((2, 3, 6), dtype=torch.float64), ok_c),              # B's K differs
+        (ok_a, torch.zeros((1, 3, 7), dtype=torch.float64), ok_c),              # B's batch differs
+        (ok_a, ok_b, torch.zeros((2, 5, 4), dtype=torch.float64)),              # output shape
+        (ok_a.to(torch.complex128), ok_b, ok_c),                                # complex input, real output
+        (ok_a, ok_b, ok_c.to(torch.complex128)),                                # real inputs, complex output
+        (ok_a.transpose(1, 2).contiguous().transpose(1, 2), ok_b, ok_c),        # not contiguous
+        (ok_a, ok_b, ok_c),                                                     # right shapes, host memory
+    ]
+    for a, b, c in bad:
+        with pytest.raises(ValueError):
+            lib.rtcc_gemm_noalloc(3, a, b, c)

@@ -99,3 +99,36 @@ def test_autograd_function_backward():
         J2, g = H.propagate_vjp([rtcc.make_field(E0=0.05, omega=0.5, sigma=0.5, t0=1.0)], h, nsteps, w, 5)
     assert abs(J.item() - J2[0]) < 1e-14
     assert np.allclose(theta.grad.numpy(), 2.0 * g[0], rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("o,v", [(3, 8), (4, 24)])
+def test_rhs_vjp_dot_product(o, v):
+    """<u, J v> = <J^T u, v> for the right-hand side F of Eqs. derivT/derivL (holomorphic pairing,
+    no conjugation), two batched trajectories under different fields.  J^T u comes from the
+    library's vector-Jacobian program (rtcc_rhs_vjp); J v from the library's own right-hand side
+    by the five-point stencil in a complex scalar, exact because F is at most quartic in y."""
+    from paper_2205_05175_gb300 import rtcc
+    from tests.gpu_common import state_from
+    f, B, mu = synth.make_system(o, v)
+    nz = 2
+    ys, us, vs = [], [], []
+    for z in range(nz):
+        ys.append(state_from(*synth.random_amplitudes(o, v, seed=600 + z, s1=0.05, s2=0.02),
+                             *synth.random_amplitudes(o, v, seed=610 + z, s1=0.05, s2=0.02)))
+        us.append(state_from(*synth.random_amplitudes(o, v, seed=620 + z, s1=1.0, s2=1.0),
+                             *synth.random_amplitudes(o, v, seed=630 + z, s1=1.0, s2=1.0)))
+        vs.append(state_from(*synth.random_amplitudes(o, v, seed=640 + z, s1=1.0, s2=1.0),
+                             *synth.random_amplitudes(o, v, seed=650 + z, s1=1.0, s2=1.0)))
+    y, u, vv = np.stack(ys), np.stack(us), np.stack(vs)
+    fields = [rtcc.make_field(E0=0.3 * (z + 1), omega=0.5, sigma=0.5, t0=1.0, pol=(0.3, 0.5, 0.8)) for z in range(nz)]
+    times = np.array([0.7, 1.3])
+    with rtcc.Handle(f, B, mu, o, v, ntraj=nz, prec=rtcc.P64) as H:
+        ybar = H.rhs_vjp(y, fields, times, u)
+        hs = 0.05
+        Fs = [H.rhs(y + s * vv, fields, times) for s in (-2 * hs, -hs, hs, 2 * hs)]
+    jv = (Fs[0] - 8 * Fs[1] + 8 * Fs[2] - Fs[3]) / (12 * hs)
+    for z in range(nz):
+        lhs = np.sum(u[z] * jv[z])
+        rhs = np.sum(ybar[z] * vv[z])
+        assert abs(lhs - rhs) < 1e-9 * max(1.0, abs(lhs)), (z, lhs, rhs)
+        assert abs(lhs) > 1e-2

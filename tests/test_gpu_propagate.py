@@ -179,3 +179,30 @@ def test_cash_karp_checkpoint_resume_across_handles():
     assert ta[0, 0] == t and abs(ta[0, na[0] - 1] - 3.0) < 1e-12
     assert np.abs(ta[0, :na[0]] - tb[0, :nb[0]]).max() < 1e-9
     assert np.abs(ma[0, :na[0]] - mb[0, :nb[0]]).max() < 1e-9
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (2, 1e-5), (3, 1e-5)])
+def test_narrow_strong_pulse_mixed_step_matches_oracle(prec, tol):
+    """The narrow strong pulse of Sec. 4.2 (E0 = 100 au, sigma = 1e-6 au, a kick of 2.5e-4 au) through
+    mixed-step RK4 with h1 = 1e-7 au while the pulse is on (120 steps to t_switch = 1.2e-5 au, where
+    the cut step lands) and h2 = 0.05 au after it, to 1 au: the dipole of every sample against the
+    oracle, in float64 and in the split-precision modes (1e-5 au, the noise level below which the
+    spectrum is unchanged, Sec. 4.1)."""
+    from paper_2205_05175_gb300 import rtcc
+    o, v = 2, 6
+    f, B, mu = system(o, v)
+    s = rk.RTCC(f, B, mu, o)
+    y0, _, _ = s.ground_state(tol=1e-11)
+    E0, sigma, t0 = 100.0, 1e-6, 6e-6
+    fld = rk.Field(E0=E0, omega=0.0, sigma=sigma, t0=t0, carrier="cos")
+    integ = rk.Integrator(method="mixed", h1=1e-7, h2=0.05, t_switch=2 * t0, t_end=1.0)
+    tt, mm, _, _ = rk.propagate(s, y0, fld, integ)
+    t, m, n, _ = _gpu_traj(o, v, f, B, mu,
+                           [rtcc.make_field(E0=E0, omega=0.0, sigma=sigma, t0=t0, carrier=rtcc.CARRIER_COS)],
+                           rtcc.make_integrator(rtcc.MIXED_RK4, h1=1e-7, h2=0.05, t_switch=2 * t0, t_end=1.0),
+                           512, prec=prec, y0=y0)
+    assert n[0] == len(tt) and len(tt) > 130
+    assert np.abs(t[0, :n[0]] - tt).max() < 1e-12
+    # the kick moves the dipole by far more than the tolerance
+    assert np.abs(mm.real - mm[0].real).max() > 1e-3
+    assert np.abs(m[0, :n[0]] - mm).max() < tol

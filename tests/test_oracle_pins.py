@@ -642,3 +642,51 @@ def test_gauss_legendre_rtcc_follows_fci_with_h4_error(two_electron):
         errs.append(np.abs(mm[-1] - mf[-1]).max())
     assert errs[1] < 1e-6
     assert 10.0 < errs[0] / errs[1] < 25.0
+
+
+# --- the per-term flop counter (roofline's algorithmic work) ---------------------------
+
+def _numpy_naive_flops(subs, shapes):
+    """numpy's own real-flop count of an einsum, from einsum_path's report."""
+    import re
+    rep = np.einsum_path(subs, *[np.empty(s) for s in shapes], optimize=False)[1]
+    return float(re.search(r"Naive FLOP count:\s*([0-9.eE+-]+)", rep).group(1))
+
+
+def test_flop_counter_agrees_with_numpy_einsum_path_term_by_term():
+    """Every counted term: the counter's real flops equal numpy's naive flop count of the same
+    einsum (2 per product over a summed label, 1 for an outer product) times the real products
+    per complex product (1, 2 or 4), so a wrong extent, a missed label or a wrong complex factor
+    fails here."""
+    from oracle import flops
+    recs = flops.records(2, 3)
+    rows = flops.term_table(2, 3)
+    assert len(recs) == len(rows) > 50
+    for r, row in zip(recs, rows):
+        mine = row[2] * 2.0 ** row[3] * 3.0 ** row[4]
+        assert mine == r["cfac"] * _numpy_naive_flops(r["subs"], r["shapes"]), r["subs"]
+    # both residuals are counted: the reverse sweep has every forward contraction's adjoints
+    assert {r["phase"] for r in recs} == {"omega", "lambda"}
+
+
+def test_flop_counter_ladder_and_shape_independence():
+    """The particle-particle ladder is the only o^2 v^4 class: a complex-by-real contraction of
+    o^2 v^4 products in Omega and its adjoint in R, 2 x 4 o^2 v^4 flops in all.  The term table
+    taken at (2, 3) reproduces a direct count at (3, 5), so the program and the o/v assignment of
+    every label do not depend on the shape."""
+    from oracle import flops
+    o, v = 30, 114
+    r = flops.rhs_flops(o, v)
+    assert r["o2v4"] == 8.0 * o ** 2 * v ** 4
+    direct = sum(x["cfac"] * _numpy_naive_flops(x["subs"], x["shapes"]) for x in flops.records(3, 5))
+    assert flops.rhs_flops(3, 5)["total"] == direct
+
+
+def test_stored_flop_table_is_the_counters():
+    """tests/golden/rhs_flops.json (read by the benchmark) is what the counter gives now."""
+    import json
+    import os
+
+    from oracle import flops
+    doc = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "rhs_flops.json")))
+    assert [tuple(r) for r in doc["rows"]] == [tuple(r) for r in flops.term_table()]

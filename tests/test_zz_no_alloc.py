@@ -1,9 +1,12 @@
-"""The allocation-free GEMM entry point (rtcc_gemm_noalloc) against the allocating one.
+"""The allocation-free GEMM entry point (rtcc_gemm_noalloc) against a float64 product and the
+allocating entry point.
 
 This entry point exists for callers that cannot let a library allocate device memory (for
 example applications that hand out all device memory from their own pool); its scratch is a
 fixed static device array shared by every call, so two calls in a row must not see each
-other's leftovers.  The file is named to run last: a failure here leaves every other test run.
+other's leftovers.  The reference is np.einsum in float64, which shares nothing with the
+library's packing and GEMM kernels; the allocating entry point (rtcc_selftest_gemm) is checked
+beside it.  The file is named to run last: a failure here leaves every other test run.
 """
 import numpy as np
 import pytest
@@ -21,8 +24,8 @@ def _inputs(rng, nb, m, n, k, kinds):
 
 
 @pytest.mark.parametrize("prec", [1, 2, 3])
-@pytest.mark.parametrize("kinds", ["rr", "cc", "cr"])
-def test_noalloc_gemm_matches_allocating_entry_point_twice(prec, kinds):
+@pytest.mark.parametrize("kinds", ["rr", "cc", "cr", "rc"])
+def test_noalloc_gemm_matches_float64_product_twice(prec, kinds):
     import torch
 
     from paper_2205_05175_gb300 import rtcc
@@ -30,7 +33,8 @@ def test_noalloc_gemm_matches_allocating_entry_point_twice(prec, kinds):
     shapes = [(2, 300, 200, 150), (1, 129, 70, 1000)]   # second call: other shapes, fresh inputs
     for nb, m, n, k in shapes:
         a, b = _inputs(rng, nb, m, n, k, kinds)
-        ref = rtcc.rtcc_selftest_gemm(prec, a, b)
+        ref = np.einsum("bmk,bnk->bmn", a, b)
+        alloc = rtcc.rtcc_selftest_gemm(prec, a, b)
         ta = torch.from_numpy(np.ascontiguousarray(a)).cuda()
         tb = torch.from_numpy(np.ascontiguousarray(b)).cuda()
         cdt = torch.complex128 if (np.iscomplexobj(a) or np.iscomplexobj(b)) else torch.float64
@@ -38,8 +42,10 @@ def test_noalloc_gemm_matches_allocating_entry_point_twice(prec, kinds):
         rtcc.rtcc_gemm_noalloc(prec, ta, tb, tc)
         torch.cuda.synchronize()
         got = tc.cpu().numpy()
-        err = np.abs(got - ref).max() / (np.abs(a).max() * np.abs(b).max() * k)
+        scale = np.abs(a).max() * np.abs(b).max() * k
+        err = np.abs(got - ref).max() / scale
         assert err < TOL[prec], err
+        assert np.abs(alloc - ref).max() / scale < TOL[prec]
 
 
 def test_noalloc_rejects_oversized_and_float64():
