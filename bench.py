@@ -596,6 +596,74 @@ def config_x1():
             "wall_s": round(wall, 3), "peaks_clean": p0, "noise": rows}
 
 
+def config_c4():
+    """The batched configuration as specified: water-hexamer shape (o=30, v=114), 12 trajectories
+    (x/y/z polarisation x E0 in {0.001, 0.01, 0.05, 0.1} au, sine pulse omega=0.5, sigma=0.5, t0=1)
+    sharing one integral set, each with its own Cash-Karp step (tol 1e-6, h0 = 0.01), from the
+    ground state to t = 10 au (t_end mode: trajectories that finish early leave the batch).  Reports
+    trajectory-steps/s over the whole run and per-trajectory step counts.  Beside it, at the same
+    shape and from the same ground state (placed at t = 0.8 au, near the pulse maximum): one
+    trajectory (z, E0 = 0.1) by RK4 h = 0.05 for 4 steps in float64 and in the reduced mode, giving the float64 right-hand-side rate (the plain float64
+    GPU form) and max|dmu(t)| of the reduced mode against float64."""
+    import numpy as np
+
+    from paper_2205_05175_gb300 import rtcc, synth
+    o, v, T = 30, 114, 10.0
+    prec = rtcc.P32_BF16X3
+    f, B, mu = synth.make_system(o, v)
+    fields = [rtcc.make_field(E0=e, omega=0.5, sigma=0.5, t0=1.0, pol=p) for p in POLS for e in E0S]
+    nz = len(fields)
+    out = {"config": "c4", "workload": f"o={o} v={v} naux={4 * (o + v)}, {nz} Cash-Karp trajectories (tol 1e-6, h0 0.01), "
+                                       f"t_end {T} au, BF16x3 contractions, float64 state"}
+    with rtcc.Handle(f, B, mu, o, v, ntraj=nz, prec=prec) as H:
+        a = time.perf_counter()
+        H.ground_state(tol=1e-8, maxiter=300)
+        out["ground_state_s"] = round(time.perf_counter() - a, 2)
+        y0 = H.get_state(0)[0]
+        a = time.perf_counter()
+        out["tuned_gemm_shapes"] = H.autotune()
+        out["autotune_s"] = round(time.perf_counter() - a, 2)
+        integ = rtcc.make_integrator(rtcc.CK, h=0.01, tol=1e-6, t_end=T)
+        import torch
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            e0.record()
+            t, m, n = H.propagate(fields, integ, 20000)
+            e1.record()
+            torch.cuda.synchronize()
+        secs = e0.elapsed_time(e1) / 1e3
+        acc, rej, nrhs, launches = H.last_stats()
+        out.update({"seconds": secs, "accepted_steps": acc, "rejected_attempts": rej, "rhs_evaluations": nrhs,
+                    "trajectory_steps_per_s": acc / secs, "trajectory_rhs_per_s": nrhs / secs,
+                    "steps_per_trajectory": [int(x) - 1 for x in n],
+                    "t_end_reached": [float(t[z, n[z] - 1]) for z in range(nz)], "clocks": clk.summary()})
+        fl = rhs_flops(o, v)
+        out["algorithmic_tflops"] = fl * nrhs / secs / 1e12
+    # float64 against the reduced mode, one trajectory, same start, fixed RK4 steps
+    fz = [rtcc.make_field(E0=0.1, omega=0.5, sigma=0.5, t0=1.0, pol=(0.0, 0.0, 1.0))]
+    integ = rtcc.make_integrator(rtcc.RK4, h=0.05, nsteps=4)
+    res = {}
+    for name, p in (("p64", rtcc.P64), ("bf16x3", prec)):
+        with rtcc.Handle(f, B, mu, o, v, ntraj=1, prec=p) as H:
+            H.set_state(0, y0, 0.8, 0.0)        # start near the pulse maximum
+            import torch
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            _, m, n = H.propagate(fz, integ, 8)
+            secs = time.perf_counter() - a
+            nr = H.last_stats()[2]
+        res[name] = {"mu": m[0, :n[0]], "seconds": secs, "rhs": nr}
+    out["p64_one_trajectory"] = {"seconds": round(res["p64"]["seconds"], 2), "rhs_evaluations": res["p64"]["rhs"],
+                                 "trajectory_rhs_per_s": res["p64"]["rhs"] / res["p64"]["seconds"]}
+    out["reduced_one_trajectory"] = {"seconds": round(res["bf16x3"]["seconds"], 2),
+                                     "trajectory_rhs_per_s": res["bf16x3"]["rhs"] / res["bf16x3"]["seconds"]}
+    out["speedup_batched_reduced_over_plain_f64"] = out["trajectory_rhs_per_s"] / out["p64_one_trajectory"]["trajectory_rhs_per_s"]
+    out["max_abs_dmu_bf16x3_vs_f64_au"] = float(np.abs(res["bf16x3"]["mu"] - res["p64"]["mu"]).max())
+    out["dmu_segment"] = "RK4 h=0.05, 4 steps from the ground state placed at t = 0.8 au, z pulse E0=0.1 (t = 0.8 .. 1.0 au)"
+    return out
+
+
 def run_gpu(args, rank, world, local):
     import numpy as np
     import torch
@@ -725,7 +793,7 @@ def main(argv=None):
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-dipole-error", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
-    ap.add_argument("--config", default=None, choices=["c2", "c3", "c5", "f1", "f3", "f4", "x1"],
+    ap.add_argument("--config", default=None, choices=["c2", "c3", "c4", "c5", "f1", "f3", "f4", "x1"],
                     help="run an accuracy / integrator / adjoint measurement instead of the throughput line")
     args = ap.parse_args(argv)
     if args.config is not None:
@@ -733,7 +801,7 @@ def main(argv=None):
             print(json.dumps({"impl": "reference", "config": args.config,
                               "unavailable": "configuration runs compare the library's own precision modes"}))
             return 0
-        line = {"c2": config_c2, "c3": config_c3, "c5": config_c5, "f1": config_f1, "f3": config_f3,
+        line = {"c2": config_c2, "c3": config_c3, "c4": config_c4, "c5": config_c5, "f1": config_f1, "f3": config_f3,
                 "f4": config_f4, "x1": config_x1}[args.config]()
         print(json.dumps(line), flush=True)
         return 0

@@ -173,6 +173,16 @@ rtcc_status_t rtcc_set_state(rtcc_handle_t h, int traj, const double* y, double 
 rtcc_status_t rtcc_rhs(rtcc_handle_t h, const double* y, const rtcc_field_t* fields,
                        const double* times, double* dydt);
 
+/* Tile autotuning (performance only; results do not depend on it).  The reduced-precision
+ * modes run their large contractions on a tcgen05 GEMM whose N tile (64, 128 or 256 columns)
+ * is chosen per contraction shape by timing each usable tile on this GPU; rtcc_propagate does
+ * this the first time it runs a given number of unfinished trajectories, the ground state and
+ * the adjoint when their engines are built.  rtcc_autotune tunes every batch size of the handle
+ * now, so that later propagations spend no time on it.  Tuning runs kernels that overwrite
+ * intermediates only, never the state.  tuned_gemms (host, may be null): distinct GEMM shapes
+ * tuned so far.  Setting RTCC_NO_AUTOTUNE=1 keeps the default tiles.  Errors: CUDA, TIMEOUT. */
+rtcc_status_t rtcc_autotune(rtcc_handle_t h, int* tuned_gemms);
+
 /* Vector-Jacobian product of the right-hand side rtcc_rhs computes (Eqs. derivT/derivL; the
  * transposed Jacobian is what the adjoint of the propagation applies at every stage):
  *   ybar_z = (d dydt_z / d y_z)^T u_z      (holomorphic: no complex conjugation)

@@ -196,8 +196,10 @@ struct TcGemmPlan {
   int splits;
   long long NB;
 };
+// bn: N tile to use (64, 128 or 256; 0 picks one from N); a tile the plan cannot use (256 for a
+// both-plane item) falls back to the default choice.
 void tc_gemm_plan(TcGemmPlan& pl, int kind, const void* A, int planesA, const void* B, int planesB, long long M,
-                  long long N, long long Kpad, long long NB, int* err);
+                  long long N, long long Kpad, long long NB, int* err, int bn = 0);
 void launch_tc_gemm(const TcGemmPlan& p, cudaStream_t s);
 int tc_kblock_elems(int kind);   // K elements per 128-byte block: 32 (tf32) or 64 (bf16)
 // Streaming multiprocessors of the current device (queried once per device; 152 on GB300).

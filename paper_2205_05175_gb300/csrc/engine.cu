@@ -887,19 +887,29 @@ void Engine::bind_gemm(Compiled& k, const Tensor& A, const Tensor& B, const Tens
     bytes_ += bytes;
     return p;
   };
+  // constant operands are packed once per distinct pack (programs built for several batch sizes
+  // share them: a constant's pack does not depend on the number of trajectories)
+  auto const_pack = [&](PackDesc& pd, size_t bytes) {
+    const std::string key = pack_key(pd);
+    auto it = const_packs_.find(key);
+    if (it != const_packs_.end()) return it->second;
+    void* p = own(bytes);
+    pd.dst = p;
+    launch_pack(pd, stream_);
+    const_packs_[key] = p;
+    return p;
+  };
   if (k.a_const) {
-    k.a_pre = own(k.a_bytes);
+    k.a_pre = const_pack(k.pa, k.a_bytes);
     k.pa.dst = k.a_pre;
-    launch_pack(k.pa, stream_);
   } else if (k.pa_from) {
     k.pa.dst = k.pa_from_b ? k.pa_from->pb.dst : k.pa_from->pa.dst;
   } else {
     k.pa.dst = k.pa_keep ? own(k.a_bytes) : wsA_;
   }
   if (k.b_const) {
-    k.b_pre = own(k.b_bytes);
+    k.b_pre = const_pack(k.pb, k.b_bytes);
     k.pb.dst = k.b_pre;
-    launch_pack(k.pb, stream_);
   } else if (k.pb_from) {
     k.pb.dst = k.pb_from_b ? k.pb_from->pb.dst : k.pb_from->pa.dst;
   } else {
@@ -912,18 +922,30 @@ void Engine::bind_gemm(Compiled& k, const Tensor& A, const Tensor& B, const Tens
   }
 }
 
+// Index tables are uploaded once per distinct content, so that identical plans (the same
+// contraction planned for several batch sizes) refer to the same tables and share packs.
 const long long* Engine::upload(const std::vector<long long>& v) {
+  std::string key("L");
+  key.append(reinterpret_cast<const char*>(v.data()), v.size() * sizeof(long long));
+  auto it = tables_.find(key);
+  if (it != tables_.end()) return static_cast<const long long*>(it->second);
   void* p = dev_alloc(std::max<size_t>(1, v.size()) * sizeof(long long));
   allocs_.push_back(p);
   bytes_ += v.size() * sizeof(long long);
   RTCC_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(long long), cudaMemcpyHostToDevice));
+  tables_[key] = p;
   return static_cast<const long long*>(p);
 }
 const float* Engine::upload(const std::vector<float>& v) {
+  std::string key("F");
+  key.append(reinterpret_cast<const char*>(v.data()), v.size() * sizeof(float));
+  auto it = tables_.find(key);
+  if (it != tables_.end()) return static_cast<const float*>(it->second);
   void* p = dev_alloc(std::max<size_t>(1, v.size()) * sizeof(float));
   allocs_.push_back(p);
   bytes_ += v.size() * sizeof(float);
   RTCC_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(float), cudaMemcpyHostToDevice));
+  tables_[key] = p;
   return static_cast<const float*>(p);
 }
 
@@ -1195,6 +1217,70 @@ void Engine::run_gemm(const Compiled& k, Profiler& pr, const char* tag) {
   launch_unpack(k.up, stream_);
   pr.stop(stream_, KC_UNPACK, 0.0,
           (double)k.NB * k.GM * k.GN * (k.tc_kind >= 0 ? 4 : 8) + 2.0 * k.NB * k.up.M * k.up.N * (k.up.c_cplx ? 16 : 8), tag);
+}
+
+int Engine::autotune(Program& P) {
+  if (P.tuned) return 0;
+  P.tuned = true;
+  cudaEvent_t e0, e1;
+  RTCC_CUDA(cudaEventCreate(&e0));
+  RTCC_CUDA(cudaEventCreate(&e1));
+  struct Ev {
+    cudaEvent_t a, b;
+    ~Ev() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } ev{e0, e1};
+  int changed = 0;
+  for (auto& cp : P.comp)
+    for (Compiled* g = cp.get(); g; g = g->twin.get()) {
+      if (g->kind != CK_GEMM || g->tc_kind < 0) continue;
+      const TcGemmParams& q = g->tcp.p;
+      const long long M = g->pa.R, N = g->pb.R;
+      const std::string key = std::to_string(g->tc_kind) + ":" + std::to_string(M) + ":" + std::to_string(N) + ":" +
+                              std::to_string(g->Kpad) + ":" + std::to_string(g->NB) + ":" + std::to_string(q.nrb) +
+                              ":" + std::to_string(q.nseg[0]) + ":" + std::to_string(q.nseg[1]) + ":" +
+                              std::to_string(g->pa.nrb) + ":" + std::to_string(g->pb.nrb) + ":" +
+                              std::to_string(q.epi.c_cplx) + ":" + std::to_string(q.epi.unit_n) + ":" +
+                              std::to_string(q.epi.ctab1 != nullptr);
+      int best = 0;
+      auto it = tile_cache_.find(key);
+      if (it != tile_cache_.end()) {
+        best = it->second;
+      } else {
+        float tbest = 0.f;
+        for (int bn : {64, 128, 256}) {
+          if (bn > 64 && N <= bn / 2) continue;   // a tile twice as wide as N or more
+          TcGemmPlan trial = g->tcp;
+          tc_gemm_plan(trial, g->tc_kind, g->pa.dst, g->pa.nrb, g->pb.dst, g->pb.nrb, M, N, g->Kpad, g->NB, dev_err_, bn);
+          if (trial.bn != bn) continue;           // not usable for this item kind
+          launch_tc_gemm(trial, stream_);
+          float tmin = 0.f;
+          for (int r = 0; r < 3; ++r) {
+            RTCC_CUDA(cudaEventRecord(e0, stream_));
+            launch_tc_gemm(trial, stream_);
+            RTCC_CUDA(cudaEventRecord(e1, stream_));
+            RTCC_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            RTCC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (r == 0 || ms < tmin) tmin = ms;
+          }
+          if (best == 0 || tmin < tbest) {
+            tbest = tmin;
+            best = bn;
+          }
+        }
+        tile_cache_[key] = best;
+      }
+      if (best != 0 && best != g->tcp.bn) {
+        tc_gemm_plan(g->tcp, g->tc_kind, g->pa.dst, g->pa.nrb, g->pb.dst, g->pb.nrb, M, N, g->Kpad, g->NB, dev_err_,
+                     best);
+        ++changed;
+      }
+    }
+  check_error();
+  return changed;
 }
 
 EngineStats Engine::stats_of(const Program& P) const {

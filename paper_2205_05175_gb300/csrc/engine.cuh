@@ -59,6 +59,7 @@ struct Program {
   struct Zero2D { void* ptr; size_t pitch, width, height; };
   std::vector<Zero2D> zero2d;       // strided regions cleared before the first op
   int prec_override = -1;           // >= 0: run this program's GEMM-path contractions in this Prec
+  bool tuned = false;               // its tensor-core tiles were chosen by Engine::autotune
   std::vector<std::shared_ptr<Compiled>> comp;
 };
 
@@ -135,6 +136,13 @@ class Engine {
   void finalize(std::vector<Program*> progs);
 
   void run(const Program& P);
+  // Tile autotuner: times every tensor-core GEMM of P (after finalize) with each usable N tile
+  // (64, 128, 256) on this GPU and keeps the fastest; choices are cached per GEMM shape on the
+  // engine.  Runs kernels on the stream: outside stream capture, and only while no data in the
+  // programs' outputs or temporaries is needed (they are recomputed by every program run).
+  // Returns the number of GEMMs whose tile changed.
+  int autotune(Program& P);
+  int tuned_gemms() const { return (int)tile_cache_.size(); }
   void set_profiler(Profiler* p) { prof_ = p; }
   EngineStats stats_of(const Program& P) const;
   void check_error();   // throws on a device-side timeout recorded by a kernel
@@ -161,6 +169,9 @@ class Engine {
   std::vector<double*> arena_ptr_;
   std::vector<void*> allocs_;
   int* dev_err_ = nullptr;
+  std::map<std::string, void*> const_packs_;   // pack image of a constant operand -> its packed planes
+  std::map<std::string, void*> tables_;        // content of an uploaded index table -> its device copy
+  std::map<std::string, int> tile_cache_;      // GEMM shape -> N tile chosen by the autotuner
   void* wsA_ = nullptr;
   void* wsB_ = nullptr;
   void* wsC_ = nullptr;

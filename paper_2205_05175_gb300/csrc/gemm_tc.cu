@@ -533,11 +533,12 @@ void launch_inst(const TcGemmPlan& pl, cudaStream_t s) {
 int tc_kblock_elems(int kind) { return kind == 0 ? 32 : 64; }
 
 void tc_gemm_plan(TcGemmPlan& pl, int kind, const void* A, int planesA, const void* B, int planesB, long long M,
-                  long long N, long long Kpad, long long NB, int* err) {
+                  long long N, long long Kpad, long long NB, int* err, int bn) {
   RTCC_REQUIRE(M > 0 && N > 0 && Kpad > 0 && NB > 0, "empty GEMM");
   RTCC_REQUIRE(M * planesA < (1ll << 31) && N * planesB < (1ll << 31) && NB < 65536, "GEMM extents too large");
   pl.kind = kind;
   pl.bn = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
+  if (bn == 64 || bn == 128 || bn == 256) pl.bn = bn;
   // Short K loops leave the epilogue as the bottleneck: one item then covers both planes of a
   // complex output (whole 16-byte elements written once, by eight epilogue warps).  Two planes
   // of accumulators, double-buffered, fit TMEM's 512 columns up to a 128-column tile.

@@ -243,16 +243,17 @@ int residual_ops(Builder& b, const IntIds* I, int t1, int t2, const OneBody& f, 
     // ring intermediates: (m a, b b, e a, j b) and (m a, b b, e b, j a) spin blocks of W_mbej
     const int t1t1 = b.tmp("t1t1", {o, o, v, v});
     b.ein(t1t1, "zjnfb", t1, "zjf", t1, "znb");
+    // Uh = t2/2 + t1 t1 enters both ring blocks through <mn|ef>: one o^3 v^3 product each (the
+    // t2 and t1 t1 parts of W_mbej contracted together, and their adjoints in one product too)
+    const int Uh = b.tmp("Uh", {o, o, v, v});
+    b.add(Uh, "zjnfb", t2, "zjnfb", 0.5);
+    b.add(Uh, "zjnfb", t1t1, "zjnfb");
     const int Wa = b.tmp("Wa", {o, v, v, o});
     b.add(Wa, "zmbej", V(B::OVVO), "mbej");
     b.ein(Wa, "zmbej", t1, "zjf", V(B::OVVV), "mbef");
     b.ein(Wa, "zmbej", t1, "znb", V(B::OOVO), "mnej", -1.0);
-    b.ein(Wa, "zmbej", t1t1, "zjnfb", V(B::OOVV), "mnef", -1.0);
+    b.ein(Wa, "zmbej", Uh, "zjnfb", V(B::OOVV), "mnef", -1.0);
     b.ein(Wa, "zmbej", t2, "zjnbf", V(B::LOOVV), "mnef", 0.5);
-    b.ein(Wa, "zmbej", t2, "zjnfb", V(B::OOVV), "mnef", -0.5);
-    const int Uh = b.tmp("Uh", {o, o, v, v});
-    b.add(Uh, "zjnfb", t2, "zjnfb", 0.5);
-    b.add(Uh, "zjnfb", t1t1, "zjnfb");
     const int U = b.tmp("U", {o, v, v, o});
     b.add(U, "zmbej", V(B::OVOV), "mbje", -1.0);
     b.ein(U, "zmbej", t1, "zjf", V(B::OVVV), "mbfe", -1.0);
@@ -278,8 +279,18 @@ int residual_ops(Builder& b, const IntIds* I, int t1, int t2, const OneBody& f, 
 
 }  // namespace
 
+namespace {
+// an arena given by the caller is reused from its start (programs built for different batch
+// sizes share it; they never run interleaved); -1 asks for a new arena
+int reuse_arena(Engine& E, int a) {
+  if (a < 0) return E.new_arena();
+  E.arena_reset(a, 0);
+  return a;
+}
+}  // namespace
+
 RhsPrograms build_rhs(Engine& E, const IntIds& I, int nz, int o, int v, double* state, double* fock,
-                      double* out, bool with_lambda) {
+                      double* out, bool with_lambda, int fwd_arena, int rev_arena) {
   RhsPrograms R;
   const int n = o + v;
   const StateViews in = state_views(E, "y", state, nz, o, v);
@@ -290,7 +301,8 @@ RhsPrograms build_rhs(Engine& E, const IntIds& I, int nz, int o, int v, double* 
   f.oo = E.external("f.oo", {nz, o, o}, false, fock, {sf, n, 1});
   f.ov = E.external("f.ov", {nz, o, v}, false, fock + o, {sf, n, 1});
   f.vv = E.external("f.vv", {nz, v, v}, false, fock + (size_t)o * n + o, {sf, n, 1});
-  const int fa = E.new_arena();
+  const int fa = reuse_arena(E, fwd_arena);
+  R.fwd_arena = fa;
   R.fwd.name = "rhs_fwd";
   R.fwd.zero_arenas = {fa};
   const long long ns = 2ll * o * v + 2ll * o * o * v * v, nT = (long long)o * v + (long long)o * o * v * v;
@@ -310,7 +322,8 @@ RhsPrograms build_rhs(Engine& E, const IntIds& I, int nz, int o, int v, double* 
   R.tau = residual_ops(b, &I, in.x1, in.x2, f, ou.x1, ou.x2);
   if (!with_lambda) return R;
   std::map<int, int> adj;
-  const int ra = E.new_arena();
+  const int ra = reuse_arena(E, rev_arena);
+  R.rev_arena = ra;
   R.rev = E.reverse(R.fwd, {in.x1, in.x2}, ra, adj);
   R.rev.zero2d = {{out + 2 * nT, (size_t)ns * 16, (size_t)nT * 16, (size_t)nz}};
   // seeds: dL/dOmega = l, dE/dt1 = 2 f_ov, dE/dtau = L_ijab
@@ -328,7 +341,7 @@ RhsPrograms build_rhs(Engine& E, const IntIds& I, int nz, int o, int v, double* 
 }
 
 DipolePrograms build_dipole(Engine& E, int nz, int o, int v, double* state, const double* mu_dev,
-                            double* dip_out) {
+                            double* dip_out, int fwd_arena, int rev_arena) {
   // The dipole is the one-body Lagrangian evaluated with f -> mu_x (Eq. dipole).  That Lagrangian is
   // linear in the one-body operator, L1(f) = sum_pq rho_pq f_pq, so rho = dL1/df is the one-particle
   // density: one reverse sweep of the one-body program with f as the active input gives rho for
@@ -336,8 +349,10 @@ DipolePrograms build_dipole(Engine& E, int nz, int o, int v, double* state, cons
   DipolePrograms D;
   const int n = o + v;
   const StateViews in = state_views(E, "yd", state, nz, o, v);
-  const int fa = E.new_arena();
-  const int ra = E.new_arena();
+  const int fa = reuse_arena(E, fwd_arena);
+  const int ra = reuse_arena(E, rev_arena);
+  D.fwd_arena = fa;
+  D.rev_arena = ra;
   Program fwd;
   fwd.name = "dens_fwd";
   // a placeholder operator buffer: the pruned forward never reads it and the reverse pass only needs

@@ -36,9 +36,12 @@ struct RhsPrograms {
   int foo, fov, fvv;       // Fock views
   int r1, r2, rl1, rl2;    // output views
   int tau;                 // tau intermediate (used by the energy program)
+  int fwd_arena = -1, rev_arena = -1;   // arenas of the intermediates and of the reverse sweep
 };
+// fwd_arena / rev_arena >= 0 reuse those arenas from their start (programs of several batch sizes
+// over the same buffers share them); -1 creates new ones.
 RhsPrograms build_rhs(Engine& E, const IntIds& I, int nz, int o, int v, double* state, double* fock,
-                      double* out, bool with_lambda);
+                      double* out, bool with_lambda, int fwd_arena = -1, int rev_arena = -1);
 
 // Dipole of the state views: for each component x, mu_xz = E[mu_x] + l.Omega[mu_x]
 // (one-body programs; the reference term 2 sum_i mu_ii is added by the caller).
@@ -47,9 +50,10 @@ struct DipolePrograms {
   double* fdummy = nullptr;   // placeholder operator buffer (owned by the caller's allocation list)
   int y1, y2, y3, y4;          // state views (t1, t2, l1, l2)
   int dip;                     // output [3][nz]
+  int fwd_arena = -1, rev_arena = -1;
 };
 DipolePrograms build_dipole(Engine& E, int nz, int o, int v, double* state, const double* mu_dev,
-                            double* dip_out);
+                            double* dip_out, int fwd_arena = -1, int rev_arena = -1);
 
 // Vector-Jacobian product of one right-hand-side evaluation (the programs in R, last run on
 // the state in R's input buffer): given the cotangent `cot` of the raw output (Omega | R) in the

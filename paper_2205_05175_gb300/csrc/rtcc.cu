@@ -218,6 +218,7 @@ struct Ctl {
   unsigned long long* err_bits;
   long long* counters;   // [0] accepted, [1] rejected (summed over trajectories)
   int* nout;
+  int* perm;          // trajectory held by each slot (slots are compacted while propagating)
 };
 
 __global__ void k_prestep(Ctl c, rtcc_integrator_t in, int nz) {
@@ -294,12 +295,13 @@ __global__ void k_record(Ctl c, const double* dip, double r0, double r1, double 
   if (!force && !c.accepted[z]) return;
   const int n = c.nout[z];
   if (n >= max_out) return;
-  tout[(size_t)z * max_out + n] = c.t[z];
+  const int tr = c.perm[z];   // outputs are indexed by trajectory, not by slot
+  tout[(size_t)tr * max_out + n] = c.t[z];
   const double ref[3] = {r0, r1, r2};
   for (int x = 0; x < 3; ++x) {
     const size_t q = 2 * ((size_t)x * nz + z);
-    muout[2 * (((size_t)z * max_out + n) * 3 + x)] = dip[q] + ref[x];
-    muout[2 * (((size_t)z * max_out + n) * 3 + x) + 1] = dip[q + 1];
+    muout[2 * (((size_t)tr * max_out + n) * 3 + x)] = dip[q] + ref[x];
+    muout[2 * (((size_t)tr * max_out + n) * 3 + x) + 1] = dip[q + 1];
   }
   c.nout[z] = n + 1;
 }
@@ -739,6 +741,10 @@ struct rtcc_ctx {
   std::unique_ptr<Engine> E;
   RhsPrograms rhs;
   DipolePrograms dip;
+  // programs over the first k slots (k = 1 .. nz-1) of the same buffers: finished trajectories are
+  // moved behind the running ones and the attempts run on the running slots only
+  std::vector<RhsPrograms> rhs_k;
+  std::vector<DipolePrograms> dip_k;
   double *Y = nullptr, *Ys = nullptr, *Ynew = nullptr, *Rout = nullptr, *Rk[kMaxStages] = {nullptr}, *F = nullptr,
          *DIP = nullptr;
   rtcc_field_t* d_fields = nullptr;
@@ -747,6 +753,7 @@ struct rtcc_ctx {
   std::unique_ptr<GroundEngine> gs[4];   // per precision, one trajectory
   std::unique_ptr<AdjointEngine> adj;
   long long last_stats[4] = {0, 0, 0, 0};
+  long long last_slot_attempts = 0;   // sum over attempts of the slots they ran (last rtcc_propagate)
   Profiler prof;
   ~rtcc_ctx() {
     adj.reset();
@@ -791,15 +798,34 @@ void copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
   RTCC_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
 }
 
-void run_dipole(rtcc_ctx* h) {
-  h->E->run(h->dip.prog);
+void run_dipole(rtcc_ctx* h, int nact = 0) {
+  h->E->run((nact <= 0 || nact == h->nz) ? h->dip.prog : h->dip_k[nact].prog);
 }
 
-// One Runge-Kutta attempt over all trajectories (stages, combination, controller, accept, dipole, record).
-void run_attempt(rtcc_ctx* h, const Tableau& tb, const rtcc_integrator_t& in, double* tout, double* muout, int max_out) {
+const RhsPrograms& rhs_for(rtcc_ctx* h, int nact) { return (nact == h->nz) ? h->rhs : h->rhs_k[nact]; }
+
+bool autotune_on() {
+  const char* e = std::getenv("RTCC_NO_AUTOTUNE");
+  return !(e && e[0] == '1');
+}
+
+// Tensor-core tiles of the programs over nact slots, chosen on first use (Engine::autotune).
+void tune_slots(rtcc_ctx* h, int nact) {
+  if (!autotune_on() || h->prec == Prec::P64) return;
+  RhsPrograms& r = (nact == h->nz) ? h->rhs : h->rhs_k[nact];
+  DipolePrograms& d = (nact == h->nz) ? h->dip : h->dip_k[nact];
+  h->E->autotune(r.fwd);
+  h->E->autotune(r.rev);
+  h->E->autotune(d.prog);
+}
+
+// One Runge-Kutta attempt over the first nact slots (stages, combination, controller, accept, dipole, record).
+void run_attempt(rtcc_ctx* h, const Tableau& tb, const rtcc_integrator_t& in, double* tout, double* muout, int max_out,
+                 int nact) {
   cudaStream_t s = h->stream;
   Profiler& pr = h->prof;
-  const int nz = h->nz;
+  const int nz = nact;
+  const RhsPrograms& rp = rhs_for(h, nact);
   const long long ns = h->ns, nT = h->nT;
   const double sb = 16.0 * (double)ns * nz;   // bytes of one state-sized complex buffer
   const dim3 gst(blocks_for(ns) / nz + 1 > 4096 ? 4096 : blocks_for(ns) / nz + 1, nz);
@@ -815,8 +841,8 @@ void run_attempt(rtcc_ctx* h, const Tableau& tb, const rtcc_integrator_t& in, do
     k_fock<<<dim3(blocks_for((long long)h->nmo * h->nmo), nz), 256, 0, s>>>(h->F, h->f0, h->mu, h->d_fields, h->ctl.t,
                                                                            h->ctl.htry, c, nz, h->nmo * h->nmo);
     pr.stop(s, KC_RK, 0, 8.0 * h->nmo * h->nmo * (4 + nz));
-    h->E->run(h->rhs.fwd);
-    h->E->run(h->rhs.rev);
+    h->E->run(rp.fwd);
+    h->E->run(rp.rev);
   };
   const size_t rbytes = sizeof(double) * 2 * (size_t)ns * nz;
   if (tb.implicit) {
@@ -861,8 +887,8 @@ void run_attempt(rtcc_ctx* h, const Tableau& tb, const rtcc_integrator_t& in, do
     k_fock<<<dim3(blocks_for((long long)h->nmo * h->nmo), nz), 256, 0, s>>>(h->F, h->f0, h->mu, h->d_fields, h->ctl.t,
                                                                            h->ctl.htry, tb.c[st], nz, h->nmo * h->nmo);
     pr.stop(s, KC_RK, 0, 8.0 * h->nmo * h->nmo * (4 + nz));
-    h->E->run(h->rhs.fwd);
-    h->E->run(h->rhs.rev);
+    h->E->run(rp.fwd);
+    h->E->run(rp.rev);
   }
   StageArgs B{}, Ew{};
   for (int j = 0; j < tb.s; ++j) {
@@ -892,7 +918,7 @@ void run_attempt(rtcc_ctx* h, const Tableau& tb, const rtcc_integrator_t& in, do
   pr.start(s);
   k_accept<<<gst, 256, 0, s>>>(h->Y, h->Ynew, h->ctl.accepted, ns);
   pr.stop(s, KC_RK, 0, 2 * sb);
-  run_dipole(h);
+  run_dipole(h, nact);
   pr.start(s);
   k_record<<<(nz + 127) / 128, 128, 0, s>>>(h->ctl, h->DIP, h->mu_ref[0], h->mu_ref[1], h->mu_ref[2], tout, muout, max_out,
                                             nz, 0);
@@ -933,6 +959,10 @@ GroundEngine* ground_engine(rtcc_ctx* h, Prec p) {
     E.finalize({&g->rhs.fwd, &g->rhs.rev, &g->energy, &g->dip.prog});
   } else {
     E.finalize({&g->rhs.fwd, &g->rhs.rev, &g->energy});
+  }
+  if (autotune_on() && p != Prec::P64) {
+    E.autotune(g->rhs.fwd);
+    E.autotune(g->rhs.rev);
   }
   slot = std::move(g);
   return slot.get();
@@ -1074,6 +1104,8 @@ AdjointEngine* adjoint_engine(rtcc_ctx* h) {
   h->allocs.push_back(a->dip.fdummy);
   a->dvjp = build_dipole_vjp(E, a->dip, h->nz, h->o, h->v, a->wdip, a->ybar_obs);
   E.finalize({&a->rhs.fwd, &a->rhs.rev, &a->vjp, &a->dip.prog, &a->dvjp});
+  if (autotune_on() && h->prec != Prec::P64)
+    for (Program* P : {&a->rhs.fwd, &a->rhs.rev, &a->vjp, &a->dip.prog, &a->dvjp}) E.autotune(*P);
   h->adj = std::move(a);
   return h->adj.get();
 }
@@ -1255,12 +1287,29 @@ rtcc_status_t rtcc_create_frozen_core(const double* f_all, const double* B_all, 
     h->ctl.err_bits = h->alloc<unsigned long long>(h->nz);
     h->ctl.counters = h->alloc<long long>(4);
     h->ctl.nout = h->alloc<int>(h->nz);
+    h->ctl.perm = h->alloc<int>(h->nz);
+    {
+      std::vector<int> id(h->nz);
+      for (int z = 0; z < h->nz; ++z) id[z] = z;
+      RTCC_CUDA(cudaMemcpyAsync(h->ctl.perm, id.data(), sizeof(int) * h->nz, cudaMemcpyHostToDevice, h->stream));
+      RTCC_CUDA(cudaStreamSynchronize(h->stream));
+    }
     h->E = std::make_unique<Engine>(h->prec, h->stream);
     const IntIds I = register_integrals(*h->E, *h->ints);
     h->rhs = build_rhs(*h->E, I, h->nz, o, v, h->Ys, h->F, h->Rout, true);
     h->dip = build_dipole(*h->E, h->nz, o, v, h->Y, h->mu, h->DIP);
     h->allocs.push_back(h->dip.fdummy);
-    h->E->finalize({&h->rhs.fwd, &h->rhs.rev, &h->dip.prog});
+    std::vector<Program*> progs = {&h->rhs.fwd, &h->rhs.rev, &h->dip.prog};
+    // the same programs over the first k slots share the arenas (and every constant pack)
+    h->rhs_k.resize(h->nz);
+    h->dip_k.resize(h->nz);
+    for (int k = 1; k < h->nz; ++k) {
+      h->rhs_k[k] = build_rhs(*h->E, I, k, o, v, h->Ys, h->F, h->Rout, true, h->rhs.fwd_arena, h->rhs.rev_arena);
+      h->dip_k[k] = build_dipole(*h->E, k, o, v, h->Y, h->mu, h->DIP, h->dip.fwd_arena, h->dip.rev_arena);
+      h->allocs.push_back(h->dip_k[k].fdummy);
+      progs.insert(progs.end(), {&h->rhs_k[k].fwd, &h->rhs_k[k].rev, &h->dip_k[k].prog});
+    }
+    h->E->finalize(progs);
     h->E->set_profiler(&h->prof);
     RTCC_CUDA(cudaStreamSynchronize(h->stream));
   });
@@ -1324,6 +1373,22 @@ rtcc_status_t rtcc_rhs(rtcc_handle_t h, const double* y, const rtcc_field_t* fie
     h->E->check_error();
     copy_out(dydt, h->Ynew, bytes, h->stream);
     RTCC_CUDA(cudaStreamSynchronize(h->stream));
+  });
+}
+
+rtcc_status_t rtcc_autotune(rtcc_handle_t h, int* tuned_gemms) {
+  if (!h) return fail(RTCC_ERR_INVALID_ARG, "null handle");
+  return guarded([&] {
+    if (h->prec != Prec::P64)
+      for (int k = 1; k <= h->nz; ++k) {
+        RhsPrograms& r = (k == h->nz) ? h->rhs : h->rhs_k[k];
+        DipolePrograms& d = (k == h->nz) ? h->dip : h->dip_k[k];
+        h->E->autotune(r.fwd);
+        h->E->autotune(r.rev);
+        h->E->autotune(d.prog);
+      }
+    RTCC_CUDA(cudaStreamSynchronize(h->stream));
+    if (tuned_gemms) *tuned_gemms = h->E->tuned_gemms();
   });
 }
 
@@ -1474,61 +1539,159 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
     RTCC_CUDA(cudaGetLastError());
     const char* ng = std::getenv("RTCC_NO_GRAPH");
     const bool use_graph = !(ng && ng[0] == '1') && !h->prof.on();
-    // first attempt eagerly (sets kernel attributes and counts the launches of one attempt),
-    // then replay a captured graph
-    const long long c0 = total_count(h->prof);
-    run_attempt(h, tb, in, tout, muout, max_out);
-    const long long per_attempt = total_count(h->prof) - c0;
-    // owns the replayed graph, so every error thrown below also releases it
-    struct GraphExec {
-      cudaGraphExec_t e = nullptr;
-      ~GraphExec() {
-        if (e) cudaGraphExecDestroy(e);
+    // Slots: trajectories that have finished are moved behind the running ones between attempts
+    // (permuting the state, field and controller entries of every slot), and the attempts then run
+    // over the running slots only, with the programs built for that many slots.  The slot order is
+    // restored when the call ends, normally or by an error.
+    struct SlotOrder {
+      rtcc_ctx* h;
+      std::vector<int> perm;   // trajectory held by each slot
+      bool moved = false;
+      explicit SlotOrder(rtcc_ctx* hh) : h(hh), perm(hh->nz) {
+        for (int z = 0; z < hh->nz; ++z) perm[z] = z;
       }
-    } ge;
-    cudaGraphExec_t& exec = ge.e;
-    if (use_graph) {
-      cudaGraph_t graph = nullptr;
-      RTCC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      try {
-        run_attempt(h, tb, in, tout, muout, max_out);
-      } catch (...) {
-        cudaStreamEndCapture(s, &graph);
-        if (graph) cudaGraphDestroy(graph);
-        throw;
+      // new slot i takes the contents of old slot order[i] (i < n)
+      void apply(const std::vector<int>& order) {
+        const int n = (int)order.size();
+        cudaStream_t st = h->stream;
+        const size_t sb = sizeof(double) * 2 * (size_t)h->ns;
+        bool any = false;
+        for (int i = 0; i < n; ++i) any |= (order[i] != i);
+        if (!any) return;
+        moved = true;
+        // the state through Ynew (free between attempts), the small per-slot arrays through the host
+        for (int i = 0; i < n; ++i)
+          if (order[i] != i)
+            RTCC_CUDA(cudaMemcpyAsync(h->Ynew + (size_t)2 * h->ns * i, h->Y + (size_t)2 * h->ns * order[i], sb,
+                                      cudaMemcpyDeviceToDevice, st));
+        for (int i = 0; i < n; ++i)
+          if (order[i] != i)
+            RTCC_CUDA(cudaMemcpyAsync(h->Y + (size_t)2 * h->ns * i, h->Ynew + (size_t)2 * h->ns * i, sb,
+                                      cudaMemcpyDeviceToDevice, st));
+        auto permute = [&](auto* dev) {
+          using T = std::remove_pointer_t<decltype(dev)>;
+          std::vector<T> a(n), b(n);
+          RTCC_CUDA(cudaMemcpyAsync(a.data(), dev, sizeof(T) * n, cudaMemcpyDeviceToHost, st));
+          RTCC_CUDA(cudaStreamSynchronize(st));
+          for (int i = 0; i < n; ++i) b[i] = a[order[i]];
+          RTCC_CUDA(cudaMemcpyAsync(dev, b.data(), sizeof(T) * n, cudaMemcpyHostToDevice, st));
+          RTCC_CUDA(cudaStreamSynchronize(st));
+        };
+        permute(h->d_fields);
+        permute(h->ctl.t);
+        permute(h->ctl.h);
+        permute(h->ctl.status);
+        permute(h->ctl.steps);
+        permute(h->ctl.rejects);
+        permute(h->ctl.nout);
+        std::vector<int> p2(h->nz);
+        for (int i = 0; i < h->nz; ++i) p2[i] = (i < n) ? perm[order[i]] : perm[i];
+        perm = p2;
+        RTCC_CUDA(cudaMemcpyAsync(h->ctl.perm, perm.data(), sizeof(int) * h->nz, cudaMemcpyHostToDevice, st));
+        RTCC_CUDA(cudaStreamSynchronize(st));
       }
-      RTCC_CUDA(cudaStreamEndCapture(s, &graph));
-      const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
-      cudaGraphDestroy(graph);
-      RTCC_CUDA(ie);
-    }
+      void restore() {
+        if (!moved) return;
+        std::vector<int> order(h->nz);
+        for (int i = 0; i < h->nz; ++i) order[perm[i]] = i;   // slot j takes the slot holding trajectory j
+        apply(order);
+        moved = false;
+      }
+      ~SlotOrder() {
+        try {
+          restore();
+        } catch (...) {
+        }
+      }
+    } slots(h);
+    // one captured attempt per slot count in use (its first attempt runs eagerly: kernel
+    // attributes are set and the launches of one attempt counted)
+    struct Graphs {
+      std::vector<cudaGraphExec_t> e;
+      ~Graphs() {
+        for (auto x : e)
+          if (x) cudaGraphExecDestroy(x);
+      }
+    } graphs;
+    graphs.e.assign(nz + 1, nullptr);
+    std::vector<long long> per_attempt(nz + 1, -1), attempts_at(nz + 1, 0);
+    auto attempt = [&](int nact) {
+      if (per_attempt[nact] < 0) {
+        tune_slots(h, nact);
+        const long long c0 = total_count(h->prof);
+        run_attempt(h, tb, in, tout, muout, max_out, nact);
+        per_attempt[nact] = total_count(h->prof) - c0;
+        if (use_graph) {
+          cudaGraph_t graph = nullptr;
+          RTCC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+          try {
+            run_attempt(h, tb, in, tout, muout, max_out, nact);
+          } catch (...) {
+            cudaStreamEndCapture(s, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            throw;
+          }
+          RTCC_CUDA(cudaStreamEndCapture(s, &graph));
+          const cudaError_t ie = cudaGraphInstantiate(&graphs.e[nact], graph, 0);
+          cudaGraphDestroy(graph);
+          RTCC_CUDA(ie);
+        }
+      } else if (graphs.e[nact]) {
+        RTCC_CUDA(cudaGraphLaunch(graphs.e[nact], s));
+      } else {
+        run_attempt(h, tb, in, tout, muout, max_out, nact);
+      }
+      attempts_at[nact] += 1;
+    };
+    int nact = nz;
+    attempt(nact);
+    long long attempts = 1;
     std::vector<int> stat(nz), stp(nz);
     std::vector<double> tz(nz), hz(nz);
-    long long attempts = 1;
     const long long max_attempts = (in.nsteps > 0) ? (long long)in.nsteps * 64 + 64 : (1ll << 40);
     int check_every = 4;
     while (true) {
-      RTCC_CUDA(cudaMemcpyAsync(stat.data(), h->ctl.status, sizeof(int) * nz, cudaMemcpyDeviceToHost, s));
-      RTCC_CUDA(cudaMemcpyAsync(stp.data(), h->ctl.steps, sizeof(int) * nz, cudaMemcpyDeviceToHost, s));
-      RTCC_CUDA(cudaMemcpyAsync(tz.data(), h->ctl.t, sizeof(double) * nz, cudaMemcpyDeviceToHost, s));
-      RTCC_CUDA(cudaMemcpyAsync(hz.data(), h->ctl.h, sizeof(double) * nz, cudaMemcpyDeviceToHost, s));
+      RTCC_CUDA(cudaMemcpyAsync(stat.data(), h->ctl.status, sizeof(int) * nact, cudaMemcpyDeviceToHost, s));
+      RTCC_CUDA(cudaMemcpyAsync(stp.data(), h->ctl.steps, sizeof(int) * nact, cudaMemcpyDeviceToHost, s));
+      RTCC_CUDA(cudaMemcpyAsync(tz.data(), h->ctl.t, sizeof(double) * nact, cudaMemcpyDeviceToHost, s));
+      RTCC_CUDA(cudaMemcpyAsync(hz.data(), h->ctl.h, sizeof(double) * nact, cudaMemcpyDeviceToHost, s));
       RTCC_CUDA(cudaStreamSynchronize(s));
       h->E->check_error();
-      bool running = false;
-      for (int z = 0; z < nz; ++z) {
-        if (stat[z] == TS_DIVERGED) throw Error(RTCC_ERR_DIVERGED, "trajectory " + std::to_string(z) + " diverged");
-        if (stat[z] == TS_NOCONV)
-          throw Error(RTCC_ERR_NOCONV, "trajectory " + std::to_string(z) + ": implicit stages did not converge");
-        if (stat[z] == TS_UNDERFLOW)
-          throw Error(RTCC_ERR_STEP_UNDERFLOW, "trajectory " + std::to_string(z) + ": step size underflow");
-        running |= (stat[z] == TS_RUN);
+      int running = 0;
+      for (int z = 0; z < nact; ++z) {
+        const std::string who = "trajectory " + std::to_string(slots.perm[z]);
+        if (stat[z] == TS_DIVERGED) throw Error(RTCC_ERR_DIVERGED, who + " diverged");
+        if (stat[z] == TS_NOCONV) throw Error(RTCC_ERR_NOCONV, who + ": implicit stages did not converge");
+        if (stat[z] == TS_UNDERFLOW) throw Error(RTCC_ERR_STEP_UNDERFLOW, who + ": step size underflow");
+        running += (stat[z] == TS_RUN);
       }
-      if (!running) break;
+      if (running == 0) break;
       if (attempts >= max_attempts) throw Error(RTCC_ERR_TIMEOUT, "attempt limit reached");
+      if (running < nact) {
+        // running slots first (in their order), finished ones after them
+        std::vector<int> order;
+        for (int z = 0; z < nact; ++z)
+          if (stat[z] == TS_RUN) order.push_back(z);
+        for (int z = 0; z < nact; ++z)
+          if (stat[z] != TS_RUN) order.push_back(z);
+        slots.apply(order);
+        std::vector<int> st2(nact), sp2(nact);
+        std::vector<double> t2(nact), h2(nact);
+        for (int i = 0; i < nact; ++i) {
+          st2[i] = stat[order[i]];
+          sp2[i] = stp[order[i]];
+          t2[i] = tz[order[i]];
+          h2[i] = hz[order[i]];
+        }
+        std::copy(st2.begin(), st2.end(), stat.begin());
+        std::copy(sp2.begin(), sp2.end(), stp.begin());
+        std::copy(t2.begin(), t2.end(), tz.begin());
+        std::copy(h2.begin(), h2.end(), hz.begin());
+        nact = running;
+      }
       // every running trajectory needs at least `need` more attempts: replay that many before polling
       long long need = 1ll << 40;
-      for (int z = 0; z < nz; ++z) {
-        if (stat[z] != TS_RUN) continue;
+      for (int z = 0; z < nact; ++z) {
         long long nz_need;
         if (in.nsteps > 0) nz_need = in.nsteps - stp[z];
         else {
@@ -1539,13 +1702,11 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
         need = std::min(need, nz_need);
       }
       const long long k = std::max(1ll, std::min<long long>(need, check_every));
-      for (long long q = 0; q < k; ++q) {
-        if (exec) RTCC_CUDA(cudaGraphLaunch(exec, s));
-        else run_attempt(h, tb, in, tout, muout, max_out);
-      }
+      for (long long q = 0; q < k; ++q) attempt(nact);
       attempts += k;
       check_every = std::min(check_every * 2, 64);
     }
+    slots.restore();
     std::vector<int> nout(nz);
     long long cnt[4];
     RTCC_CUDA(cudaMemcpyAsync(nout.data(), h->ctl.nout, sizeof(int) * nz, cudaMemcpyDeviceToHost, s));
@@ -1556,10 +1717,16 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
     }
     RTCC_CUDA(cudaStreamSynchronize(s));
     for (int z = 0; z < nz; ++z) n_out[z] = nout[z];
+    long long launches = 0, slot_attempts = 0;
+    for (int k = 1; k <= nz; ++k) {
+      launches += std::max(0ll, per_attempt[k]) * attempts_at[k];
+      slot_attempts += (long long)k * attempts_at[k];
+    }
     h->last_stats[0] = cnt[0];
     h->last_stats[1] = cnt[1];
     h->last_stats[2] = (cnt[0] + cnt[1]) * (tb.implicit ? 1 + (long long)tb.s * tb.sweeps : tb.s);
-    h->last_stats[3] = per_attempt * attempts;
+    h->last_stats[3] = launches;
+    h->last_slot_attempts = slot_attempts;
   });
 }
 

@@ -65,6 +65,7 @@ _sig = {
     "rtcc_set_state": [_vp, C.c_int, _vp, C.c_double, C.c_double],
     "rtcc_rhs": [_vp, _vp, C.POINTER(rtcc_field_t), _vp, _vp],
     "rtcc_rhs_vjp": [_vp, _vp, C.POINTER(rtcc_field_t), _vp, _vp, _vp],
+    "rtcc_autotune": [_vp, _ip],
     "rtcc_dipole": [_vp, _vp],
     "rtcc_propagate": [_vp, C.POINTER(rtcc_field_t), C.POINTER(rtcc_integrator_t), C.c_int, _vp, _vp, _ip],
     "rtcc_last_stats": [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
@@ -196,6 +197,12 @@ class Handle:
             out = torch.empty_like(y)
         _check(_lib.rtcc_rhs(self.h, _ptr(y), fa, _ptr(tms), _ptr(out)))
         return out
+
+    def autotune(self):
+        """Choose the tensor-core tiles of every batch size now; returns the GEMM shapes tuned."""
+        n = C.c_int()
+        _check(_lib.rtcc_autotune(self.h, C.byref(n)))
+        return n.value
 
     def rhs_vjp(self, y, fields, times, u):
         """(d dydt / dy)^T u for every trajectory at the states y (holomorphic; host arrays)."""

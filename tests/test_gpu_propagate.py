@@ -206,3 +206,37 @@ def test_narrow_strong_pulse_mixed_step_matches_oracle(prec, tol):
     # the kick moves the dipole by far more than the tolerance
     assert np.abs(mm.real - mm[0].real).max() > 1e-3
     assert np.abs(m[0, :n[0]] - mm).max() < tol
+
+
+# float64: equal to rounding; BF16x3: split-K partial sums are added in a run-dependent order, so
+# the same trajectory alone and in a batch agree to the contraction's resolution only
+@pytest.mark.parametrize("prec,tol_t,tol", [(0, 1e-14, 1e-12), (3, 1e-6, 1e-6)])
+def test_cash_karp_compaction_keeps_every_trajectory_exact(prec, tol_t, tol):
+    """Per-trajectory Cash-Karp steps (Eqs. ck-h, ck-h-final) in t_end mode: weak-field trajectories
+    take longer steps and finish first, are moved behind the running ones, and the remaining
+    attempts run over the running trajectories only.  Every trajectory of the batch (given in an
+    order that interleaves strong and weak fields) must equal the same trajectory run alone, sample
+    by sample, and the handle's slots must hold the trajectories in their own order afterwards."""
+    from paper_2205_05175_gb300 import rtcc
+    o, v = 3, 8
+    f, B, mu = system(o, v)
+    e0s = [0.5, 0.001, 0.2, 0.01, 0.5]
+    pols = [(0, 0, 1.0), (1.0, 0, 0), (0, 1.0, 0), (0, 0, 1.0), (1.0, 0, 0)]
+    fields = [rtcc.make_field(E0=e, sigma=0.3, pol=p) for e, p in zip(e0s, pols)]
+    integ = rtcc.make_integrator(rtcc.CK, h=0.01, tol=1e-7, t_end=2.0)
+    with rtcc.Handle(f, B, mu, o, v, ntraj=len(fields), prec=prec) as h:
+        h.ground_state(tol=1e-11)
+        y0 = h.get_state(0)[0]
+        tb, mb, nb = h.propagate(fields, integ, 4096)
+        ends = [h.get_state(z) for z in range(len(fields))]
+    assert len(set(nb.tolist())) >= 3          # trajectories took different numbers of steps
+    for z in range(len(fields)):
+        with rtcc.Handle(f, B, mu, o, v, ntraj=1, prec=prec) as h1:
+            h1.set_state(0, y0, 0.0, 0.0)
+            ts, ms, ns = h1.propagate([fields[z]], integ, 4096)
+            end1 = h1.get_state(0)
+        assert nb[z] == ns[0]
+        assert np.abs(tb[z, :nb[z]] - ts[0, :ns[0]]).max() < tol_t
+        assert np.abs(mb[z, :nb[z]] - ms[0, :ns[0]]).max() < tol
+        assert np.abs(ends[z][0] - end1[0]).max() < tol and abs(ends[z][1] - 2.0) < 1e-12
+        assert abs(ends[z][2] - end1[2]) <= tol_t * end1[2]   # the stored trial step came back to its trajectory
