@@ -26,9 +26,9 @@ throughput line (one JSON line each):
   c5  water-dimer shape, RK4 h=0.05 for 500 steps, J = sum_t w(t) mu_z(t), w Gaussian at 15 au
       (width 2 au): dJ/d(E0, omega, sigma) by the checkpointed adjoint (every 25 steps) in
       TF32 and float64 against float64 central differences (delta 1e-5)
-  f1  water-dimer shape, narrow strong pulse (E0=100, sigma=1e-5, t0=6e-5, kick 2.5e-3 au) by
-      mixed-step RK4 (h1=1e-7 through the pulse, then h2=0.02 to 10 au): every reduced mode
-      against float64, max|dmu(t)| and the delta-kick spectrum peaks
+  f1  water-dimer shape, the paper's narrowest strong pulse (E0=100, sigma=1e-6, t0=5e-6, kick
+      2.5e-4 au) by mixed-step RK4 (h1=1e-7 through the pulse, then h2=0.01 to 10 au): every
+      reduced mode against float64, max|dmu(t)| and the delta-kick spectrum peaks
 """
 from __future__ import annotations
 
@@ -461,24 +461,25 @@ def config_f1():
     from paper_2205_05175_gb300 import rtcc, synth
     o, v = 10, 38
     f, B, mu = synth.make_system(o, v)
-    E0, sigma, t0 = 100.0, 1e-5, 6e-5
+    E0, sigma, t0 = 100.0, 1e-6, 5e-6          # the paper's narrowest pulse (Sec. 4.2)
     kick = E0 * sigma * np.sqrt(2.0 * np.pi)
     fld = rtcc.make_field(E0=E0, omega=0.0, sigma=sigma, t0=t0, pol=(0.0, 0.0, 1.0), carrier=rtcc.CARRIER_COS)
-    integ = rtcc.make_integrator(rtcc.MIXED_RK4, h1=1e-7, h2=0.02, t_switch=2 * t0, t_end=10.0)
+    integ = rtcc.make_integrator(rtcc.MIXED_RK4, h1=1e-7, h2=0.01, t_switch=2 * t0, t_end=10.0)
     om = np.linspace(0.05, 3.0, 6000)
     res = {}
     for name in ("p64", "tf32", "3xtf32", "bf16x3"):
         with rtcc.Handle(f, B, mu, o, v, ntraj=1, prec=rtcc.PRECISIONS[name]) as H:
             H.ground_state(tol=1e-10)
             t0w = time.perf_counter()
-            t, m, k = H.propagate([fld], integ, 4000)
+            t, m, k = H.propagate([fld], integ, 4096)
             wall = time.perf_counter() - t0w
             acc = H.last_stats()[0]
         t, m = t[0, :k[0]], m[0, :k[0]]
-        I = rtcc.rtcc_spectrum(t, m.real, fld, om, kappa=kick, gamma=0.05, dt=0.02)
+        I = rtcc.rtcc_spectrum(t, m.real, fld, om, kappa=kick, gamma=0.05, dt=0.01)
         res[name] = {"t": t, "mu": m, "peaks": _peaks(om, I), "wall_s": round(wall, 3), "steps": acc}
     ref = res["p64"]
-    out = {"config": "f1", "workload": "o=10 v=38, E0=100 sigma=1e-5 kick, mixed RK4 h1=1e-7 / h2=0.02 to 10 au",
+    out = {"config": "f1", "workload": "o=10 v=38, E0=100 sigma=1e-6 t0=5e-6 kick (Sec. 4.2), mixed RK4 h1=1e-7 to "
+                                       "t=1e-5 then h2=0.01 to 10 au",
            "kick_au": kick, "steps": ref["steps"], "peaks_p64": ref["peaks"], "wall_s_p64": ref["wall_s"],
            "max_abs_mu_induced_p64": float(np.abs(ref["mu"].real - ref["mu"][0].real).max()), "modes": {}}
     for name in ("tf32", "3xtf32", "bf16x3"):

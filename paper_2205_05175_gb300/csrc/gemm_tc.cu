@@ -72,6 +72,14 @@ __device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* tm, u
       "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(bar)
       : "memory");
 }
+// L2 prefetch of one tile of a tensor map (no shared memory, no barrier): brings a K block that
+// the producer will load a few stages later from DRAM into L2, so that its TMA load hits in L2.
+__device__ __forceinline__ void tma_prefetch3(const CUtensorMap* tm, int x, int y, int z) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                   reinterpret_cast<uint64_t>(tm)),
+               "r"(x), "r"(y), "r"(z)
+               : "memory");
+}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -271,6 +279,13 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
                       it.bz);
             tma_load3(su32(sB + s * B_BYTES), &p.tmB, su32(&full[s]), kb * KBLK, p.seg[rb][sg].pb * p.N + it.n0,
                       it.bz);
+            // the K block this loop loads STAGES iterations from now (same item and plane), into L2
+            if (i + STAGES < it.nvl) {
+              const int vf = v + STAGES;
+              const int sgf = vf / p.nkb, kbf = vf - sgf * p.nkb;
+              tma_prefetch3(&p.tmA, kbf * KBLK, p.seg[rb][sgf].pa * p.M + it.m0, it.bz);
+              tma_prefetch3(&p.tmB, kbf * KBLK, p.seg[rb][sgf].pb * p.N + it.n0, it.bz);
+            }
           }
         }
       }

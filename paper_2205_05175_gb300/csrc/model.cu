@@ -236,10 +236,12 @@ int residual_ops(Builder& b, const IntIds* I, int t1, int t2, const OneBody& f, 
     b.ein(Wmnij, "zmnij", t1, "zie", V(B::OOVO), "mnej");
     b.ein(Wmnij, "zmnij", tau, "zijef", V(B::OOVV), "mnef");
     b.ein(S, Q + "ijab", tau, "zmnab", Wmnij, "zmnij", 0.5);
-    // t1 pieces of the particle-particle ladder
-    const int Zijmb = b.tmp("Zijmb", {o, o, o, v});
-    b.ein(Zijmb, "zijmb", tau, "zijef", V(B::OVVV), "mbef");
-    b.ein(S, Q + "ijab", t1, "zma", Zijmb, "zijmb", -1.0);
+    // Every term of the form -t1[ma] Y[ijmb] is summed into one o^3 v intermediate before a single
+    // product with t1 (one pass over the o^2 v^2 output instead of four, and the same in the adjoint):
+    // the t1 pieces of the particle-particle ladder tau <mb|ef>, the t1 t1 <mb|ej> and t1 t1 <mb|ie>
+    // ring pieces, and t1 <mb|ij>.
+    const int Xijmb = b.tmp("Xijmb", {o, o, o, v});
+    b.ein(Xijmb, "zijmb", tau, "zijef", V(B::OVVV), "mbef");
     // ring intermediates: (m a, b b, e a, j b) and (m a, b b, e b, j a) spin blocks of W_mbej
     const int t1t1 = b.tmp("t1t1", {o, o, v, v});
     b.ein(t1t1, "zjnfb", t1, "zjf", t1, "znb");
@@ -262,15 +264,12 @@ int residual_ops(Builder& b, const IntIds* I, int t1, int t2, const OneBody& f, 
     b.ein(S, Q + "ijab", t2t, "zimae", Wa, "zmbej");
     b.ein(S, Q + "ijab", t2, "zimae", U, "zmbej");
     b.ein(S, Q + "ijab", t2, "zmjae", U, "zmbei");
-    // t1 t1 <mb|ej> and t1 t1 <mb|ie> rings, t1 <ab|ej>, t1 <mb|ij>
-    const int Q1 = b.tmp("Q1", {o, v, o, o});
-    b.ein(Q1, "zmbij", t1, "zie", V(B::OVVO), "mbej");
-    b.ein(S, Q + "ijab", t1, "zma", Q1, "zmbij", -1.0);
-    const int Q2 = b.tmp("Q2", {o, v, o, o});
-    b.ein(Q2, "zmbji", t1, "zje", V(B::OVOV), "mbie");
-    b.ein(S, Q + "ijab", t1, "zma", Q2, "zmbji", -1.0);
+    // t1 t1 <mb|ej> and t1 t1 <mb|ie> rings and t1 <mb|ij> join the ladder's t1 pieces; t1 <ab|ej>
+    b.ein(Xijmb, "zijmb", t1, "zie", V(B::OVVO), "mbej");
+    b.ein(Xijmb, "zijmb", t1, "zje", V(B::OVOV), "mbie");
+    b.add(Xijmb, "zijmb", V(B::OVOO), "mbij");
+    b.ein(S, Q + "ijab", t1, "zma", Xijmb, "zijmb", -1.0);
     b.ein(S, Q + "ijab", t1, "zie", V(B::VVVO), "abej");
-    b.ein(S, Q + "ijab", t1, "zma", V(B::OVOO), "mbij", -1.0);
   }
   b.add(r2, Q + "ijab", S, Q + "ijab");
   b.add(r2, Q + "ijab", S, Q + "jiba");
