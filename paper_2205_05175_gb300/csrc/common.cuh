@@ -186,6 +186,8 @@ struct TcGemmParams {
   int nseg[2];
   TcSeg seg[2][kMaxSeg];
   int vper;            // virtual K blocks (segments x nkb) per split
+  int chunk;           // K blocks per accumulation chunk (0: one accumulation over the item's K loop)
+  int prefetch;        // L2 prefetch distance of the producer in K blocks (0: none)
   TcEpilogue epi;
   int* err;            // device error word
 };
@@ -193,13 +195,19 @@ struct TcGemmPlan {
   TcGemmParams p;
   int kind;            // 0 tf32, 1 bf16
   int bn;              // N tile (64, 128 or 256)
+  int variant;         // 0: default stages and epilogue warps for bn; 1: bn 128 with 6 stages, 4 epilogue warps
   int splits;
   long long NB;
 };
 // bn: N tile to use (64, 128 or 256; 0 picks one from N); a tile the plan cannot use (256 for a
 // both-plane item) falls back to the default choice.
+// chunk > 0: the tensor cores accumulate at most `chunk` K blocks (of 128 bytes) in one float32
+// accumulator; the chunks of an item are then summed with round-to-nearest float32 adds in the
+// epilogue warps.  The tensor cores' float32 accumulation over a long K loop drifts (its rounding
+// errors add up in one direction, about K/16 units in the last place for K products); summing
+// short chunks keeps that drift to the chunk length.
 void tc_gemm_plan(TcGemmPlan& pl, int kind, const void* A, int planesA, const void* B, int planesB, long long M,
-                  long long N, long long Kpad, long long NB, int* err, int bn = 0);
+                  long long N, long long Kpad, long long NB, int* err, int bn = 0, int chunk = 0);
 void launch_tc_gemm(const TcGemmPlan& p, cudaStream_t s);
 int tc_kblock_elems(int kind);   // K elements per 128-byte block: 32 (tf32) or 64 (bf16)
 // Streaming multiprocessors of the current device (queried once per device; 152 on GB300).

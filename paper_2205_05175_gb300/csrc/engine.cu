@@ -39,6 +39,18 @@ long long prod_dims(const IndexMap& m) {
 
 long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
 
+// K blocks per tensor-core accumulation chunk.  The split modes (hi/lo products) resolve about
+// 2^-17 (BF16x3) or 2^-22 (3xTF32) per product, but the tensor cores' float32 accumulator drifts by
+// about one unit in the last place per 16 products (measured: at K ~ 10^4 the drift dominates the
+// dipole error of a whole trajectory), so their products are accumulated in chunks of 8 K blocks
+// (512 BF16 or 256 TF32 elements) and the chunks summed with round-to-nearest adds.  A single TF32
+// pass resolves only 2^-11 and keeps one accumulation.  RTCC_GEMM_CHUNK=<blocks> overrides (0: off).
+int accumulation_chunk(Prec prec) {
+  if (prec != Prec::TF32X3 && prec != Prec::BF16X3) return 0;
+  if (const char* e = std::getenv("RTCC_GEMM_CHUNK")) return std::max(0, std::atoi(e));
+  return 8;
+}
+
 // Order labels by decreasing |stride| in tensor t (so the unit-stride label comes last).
 std::string by_stride(const std::string& labs, const Tensor& t, const std::string& tl) {
   std::string out = labs;
@@ -117,6 +129,7 @@ struct Compiled {
   UnpackDesc up{};
   long long GM = 0, GN = 0, Kpad = 0, NB = 0;
   int tc_kind = -1;   // -1: float64 SIMT GEMM, 0: tf32, 1: bf16
+  int chunk = 0;      // K blocks per tensor-core accumulation chunk (0: none)
   TcGemmPlan tcp{};
   long long alg_flops = 0;    // useful real flops (one pass)
   long long exec_flops = 0;   // flops issued by the GEMM kernel (passes and padding included)
@@ -481,6 +494,7 @@ void Engine::plan(Program& P) {
       const int elem = (prec == Prec::BF16X3) ? PE_BF16 : PE_F32;
       const int esz = (elem == PE_F32) ? 4 : 2;
       k.tc_kind = (prec == Prec::BF16X3) ? 1 : 0;
+      k.chunk = accumulation_chunk(prec);
       const long long Kp = round_up(K, tc_kblock_elems(k.tc_kind));
       auto planes = [&](PackDesc& pd, const Tensor& T, const IndexMap& rows, const IndexMap& cols,
                         const IndexMap& bat, long long R) {
@@ -918,7 +932,8 @@ void Engine::bind_gemm(Compiled& k, const Tensor& A, const Tensor& B, const Tens
   k.up.gout = wsC_;
   if (k.tc_kind >= 0) {
     k.tcp.p.epi.C = C.ptr;
-    tc_gemm_plan(k.tcp, k.tc_kind, k.pa.dst, k.pa.nrb, k.pb.dst, k.pb.nrb, k.pa.R, k.pb.R, k.Kpad, k.NB, dev_err_);
+    tc_gemm_plan(k.tcp, k.tc_kind, k.pa.dst, k.pa.nrb, k.pb.dst, k.pb.nrb, k.pa.R, k.pb.R, k.Kpad, k.NB, dev_err_, 0,
+                 k.chunk);
   }
 }
 
@@ -1048,6 +1063,7 @@ bool Engine::plan_pairsym(Compiled& k, const Op& op, const std::string& Lm, cons
   auto build = [&](Compiled& g, int sign) {
     g.kind = CK_GEMM;
     g.tc_kind = kind;
+    g.chunk = accumulation_chunk(prec);
     planes(g.pa, A, M, sign);
     g.pa.rows = am;
     g.pa.ktab = ka_d;
@@ -1243,7 +1259,7 @@ int Engine::autotune(Program& P) {
                               ":" + std::to_string(q.nseg[0]) + ":" + std::to_string(q.nseg[1]) + ":" +
                               std::to_string(g->pa.nrb) + ":" + std::to_string(g->pb.nrb) + ":" +
                               std::to_string(q.epi.c_cplx) + ":" + std::to_string(q.epi.unit_n) + ":" +
-                              std::to_string(q.epi.ctab1 != nullptr);
+                              std::to_string(q.epi.ctab1 != nullptr) + ":" + std::to_string(g->chunk);
       int best = 0;
       auto it = tile_cache_.find(key);
       if (it != tile_cache_.end()) {
@@ -1253,7 +1269,8 @@ int Engine::autotune(Program& P) {
         for (int bn : {64, 128, 256}) {
           if (bn > 64 && N <= bn / 2) continue;   // a tile twice as wide as N or more
           TcGemmPlan trial = g->tcp;
-          tc_gemm_plan(trial, g->tc_kind, g->pa.dst, g->pa.nrb, g->pb.dst, g->pb.nrb, M, N, g->Kpad, g->NB, dev_err_, bn);
+          tc_gemm_plan(trial, g->tc_kind, g->pa.dst, g->pa.nrb, g->pb.dst, g->pb.nrb, M, N, g->Kpad, g->NB, dev_err_, bn,
+                       g->chunk);
           if (trial.bn != bn) continue;           // not usable for this item kind
           launch_tc_gemm(trial, stream_);
           float tmin = 0.f;
@@ -1275,7 +1292,7 @@ int Engine::autotune(Program& P) {
       }
       if (best != 0 && best != g->tcp.bn) {
         tc_gemm_plan(g->tcp, g->tc_kind, g->pa.dst, g->pa.nrb, g->pb.dst, g->pb.nrb, M, N, g->Kpad, g->NB, dev_err_,
-                     best);
+                     best, g->chunk);
         ++changed;
       }
     }

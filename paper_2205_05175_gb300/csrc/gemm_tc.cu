@@ -120,6 +120,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+      "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+      "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+      "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row core groups 1024 B apart.
 __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
   uint64_t d = 0;
@@ -229,11 +242,18 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   uint64_t* empty = full + STAGES;
   uint64_t* tfull = empty + STAGES;
   uint64_t* tempty = tfull + 2;
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tempty + 2);
+  uint64_t* cfull = tempty + 2;
+  uint64_t* cempty = cfull + 2;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(cempty + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int np_all = p.fused ? p.nrb : 1;                 // planes per work item
-  const uint32_t tcols = (uint32_t)(2 * np_all * BN);      // two accumulator sets
+  // TMEM: nreg item accumulators (the sums), and with chunked accumulation nreg chunk slots after them;
+  // two of each when they fit in the 512 columns (the epilogue of one item then overlaps the next)
+  const int chunk = p.chunk;
+  const int nreg = (chunk > 0 && 4 * np_all * BN > 512) ? 1 : 2;
+  const uint32_t tcols = (uint32_t)((chunk > 0 ? 2 : 1) * nreg * np_all * BN);
+  const uint32_t slot0 = (uint32_t)(nreg * np_all * BN);   // first chunk slot column
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -243,6 +263,8 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
       mbar_init(&tempty[a], 32 * EPW);
+      mbar_init(&cfull[a], 1);
+      mbar_init(&cempty[a], 32 * EPW);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -279,9 +301,9 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
                       it.bz);
             tma_load3(su32(sB + s * B_BYTES), &p.tmB, su32(&full[s]), kb * KBLK, p.seg[rb][sg].pb * p.N + it.n0,
                       it.bz);
-            // the K block this loop loads STAGES iterations from now (same item and plane), into L2
-            if (i + STAGES < it.nvl) {
-              const int vf = v + STAGES;
+            // the K block this loop loads `prefetch` iterations from now (same item and plane), into L2
+            if (p.prefetch > 0 && i + p.prefetch < it.nvl) {
+              const int vf = v + p.prefetch;
               const int sgf = vf / p.nkb, kbf = vf - sgf * p.nkb;
               tma_prefetch3(&p.tmA, kbf * KBLK, p.seg[rb][sgf].pa * p.M + it.m0, it.bz);
               tma_prefetch3(&p.tmB, kbf * KBLK, p.seg[rb][sgf].pb * p.N + it.n0, it.bz);
@@ -297,12 +319,12 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = idesc_make<KIND, BN>();
-      uint32_t g = 0;
+      uint32_t g = 0, gs = 0;   // K blocks consumed, chunk slots used
       int local = 0;
       bool alive = true;
       for (int w = blockIdx.x; w < total_items && alive; w += gridDim.x, ++local) {
         const Item it = decode_item<BN>(p, w, splits);
-        const int a = local & 1, u = local >> 1;
+        const int a = local % nreg, u = local / nreg;
         if (u > 0 && !mbar_wait(&tempty[a], (u - 1) & 1)) {
           atomicExch(p.err, DEV_TIMEOUT_MMA);
           break;
@@ -310,8 +332,24 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         tc_fence_after();
         for (int pl = 0; pl < it.np && alive; ++pl) {
           const int rb = it.rb + pl;
-          const uint32_t acc = tmem + (uint32_t)((a * it.np + pl) * BN);
+          const uint32_t acc_sum = tmem + (uint32_t)((a * it.np + pl) * BN);
+          uint32_t acc = acc_sum;
+          uint32_t slot = 0;
           for (int i = 0; i < it.nvl; ++i, ++g) {
+            // chunk 0 of the plane accumulates into the item's sum, every later chunk into a slot
+            // that the epilogue folds into the sum
+            const int ci = chunk > 0 ? i % chunk : i;
+            if (chunk > 0 && ci == 0 && i > 0) {
+              slot = gs % nreg;
+              const uint32_t sp = gs / nreg;
+              if (sp > 0 && !mbar_wait(&cempty[slot], (sp - 1) & 1)) {
+                atomicExch(p.err, DEV_TIMEOUT_MMA);
+                alive = false;
+                break;
+              }
+              tc_fence_after();
+              acc = tmem + slot0 + (uint32_t)((slot * it.np + pl) * BN);
+            }
             const int sg = (it.v0 + i) / p.nkb;
             const uint32_t s = g % STAGES;
             if (!mbar_wait(&full[s], (g / STAGES) & 1)) {
@@ -325,8 +363,12 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             const uint32_t id = idesc | ((uint32_t)p.seg[rb][sg].neg << 13);   // negate A for -Ai Bi
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)   // 4 MMAs of 32 bytes of K per 128-byte block
-              tc_mma<KIND>(acc, ad + 2ull * kk, bd + 2ull * kk, id, (i | kk) ? 1u : 0u);
+              tc_mma<KIND>(acc, ad + 2ull * kk, bd + 2ull * kk, id, (ci | kk) ? 1u : 0u);
             tc_commit(su32(&empty[s]));
+            if (chunk > 0 && i >= chunk && (ci == chunk - 1 || i == it.nvl - 1)) {
+              tc_commit(su32(&cfull[slot]));   // this chunk's slot is complete
+              ++gs;
+            }
           }
         }
         tc_commit(su32(&tfull[a]));   // arrives when this tile's MMAs have completed
@@ -349,9 +391,45 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     const bool dual = e.ctab1 != nullptr;          // pair-symmetric scatter to a second column
     const float s2 = e.sign2;
     int local = 0;
-    for (int w = blockIdx.x; w < total_items; w += gridDim.x, ++local) {
+    uint32_t gs = 0;   // chunk slots folded
+    bool alive = true;
+    for (int w = blockIdx.x; w < total_items && alive; w += gridDim.x, ++local) {
       const Item it = decode_item<BN>(p, w, splits);
-      const int a = local & 1, u = local >> 1;
+      const int a = local % nreg, u = local / nreg;
+      // fold every chunk after the first into the plane's sum, in the order the MMA warp issued them:
+      // sum += slot with round-to-nearest float32 adds, then the slot is handed back
+      if (chunk > 0) {
+        const uint32_t lanes = ((uint32_t)(q * 32) << 16);
+        for (int pl = 0; pl < it.np && alive; ++pl) {
+          const int nch = (it.nvl + chunk - 1) / chunk;
+          for (int c = 1; c < nch; ++c, ++gs) {
+            const uint32_t slot = gs % nreg, sp = gs / nreg;
+            bool okc = mbar_wait(&cfull[slot], sp & 1);
+            okc = __all_sync(0xffffffffu, okc);
+            if (!okc) {
+              if (lane == 0) atomicExch(p.err, DEV_TIMEOUT_EPI);
+              alive = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sum_c = tmem + lanes + (uint32_t)((a * it.np + pl) * BN + hc);
+            const uint32_t slot_c = tmem + lanes + slot0 + (uint32_t)((slot * it.np + pl) * BN + hc);
+#pragma unroll 1
+            for (int cc = 0; cc < WCOLS; cc += 32) {
+              uint32_t x[32], y[32];
+              tmem_ld32(slot_c + (uint32_t)cc, x);
+              tmem_ld32(sum_c + (uint32_t)cc, y);
+#pragma unroll
+              for (int j = 0; j < 32; ++j) y[j] = __float_as_uint(__fadd_rn(__uint_as_float(y[j]), __uint_as_float(x[j])));
+              tmem_st32(sum_c + (uint32_t)cc, y);
+            }
+            tmem_wait_st();
+            tc_fence_before();
+            mbar_arrive(&cempty[slot]);
+          }
+        }
+        if (!alive) break;
+      }
       // output offsets of this item (computed while the MMAs of the item are still running)
       __syncwarp();
       for (int c = lane; c < WCOLS; c += 32) {
@@ -492,7 +570,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
 template <int BN, int KIND, int STAGES, int EPW>
 constexpr size_t smem_bytes() {
   return 1024 + (size_t)STAGES * (BM * 128 + BN * 128) + (size_t)EPW * 32 * 33 * 4 + (size_t)2 * 4 * BN * 8 +
-         (2 * STAGES + 4) * 8 + 16;
+         (2 * STAGES + 8) * 8 + 16;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -548,7 +626,11 @@ void launch_inst(const TcGemmPlan& pl, cudaStream_t s) {
 int tc_kblock_elems(int kind) { return kind == 0 ? 32 : 64; }
 
 void tc_gemm_plan(TcGemmPlan& pl, int kind, const void* A, int planesA, const void* B, int planesB, long long M,
-                  long long N, long long Kpad, long long NB, int* err, int bn) {
+                  long long N, long long Kpad, long long NB, int* err, int bn, int chunk) {
+  RTCC_REQUIRE(chunk >= 0, "negative accumulation chunk");
+  pl.p.chunk = chunk;
+  pl.variant = 0;
+  pl.p.prefetch = 0;
   RTCC_REQUIRE(M > 0 && N > 0 && Kpad > 0 && NB > 0, "empty GEMM");
   RTCC_REQUIRE(M * planesA < (1ll << 31) && N * planesB < (1ll << 31) && NB < 65536, "GEMM extents too large");
   pl.kind = kind;
@@ -581,12 +663,16 @@ void tc_gemm_plan(TcGemmPlan& pl, int kind, const void* A, int planesA, const vo
 void launch_tc_gemm(const TcGemmPlan& p, cudaStream_t s) {
   if (p.kind == 0) {
     if (p.bn == 64) launch_inst<64, 0, 7, 8>(p, s);
-    else if (p.bn == 128) launch_inst<128, 0, 5, 8>(p, s);
-    else launch_inst<256, 0, 4, 4>(p, s);
+    else if (p.bn == 128) {
+      if (p.variant == 1) launch_inst<128, 0, 6, 4>(p, s);
+      else launch_inst<128, 0, 5, 8>(p, s);
+    } else launch_inst<256, 0, 4, 4>(p, s);
   } else {
     if (p.bn == 64) launch_inst<64, 1, 7, 8>(p, s);
-    else if (p.bn == 128) launch_inst<128, 1, 5, 8>(p, s);
-    else launch_inst<256, 1, 4, 4>(p, s);
+    else if (p.bn == 128) {
+      if (p.variant == 1) launch_inst<128, 1, 6, 4>(p, s);
+      else launch_inst<128, 1, 5, 8>(p, s);
+    } else launch_inst<256, 1, 4, 4>(p, s);
   }
 }
 
