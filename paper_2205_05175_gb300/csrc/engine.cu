@@ -42,13 +42,15 @@ long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
 // K blocks per tensor-core accumulation chunk.  The split modes (hi/lo products) resolve about
 // 2^-17 (BF16x3) or 2^-22 (3xTF32) per product, but the tensor cores' float32 accumulator drifts by
 // about one unit in the last place per 16 products (measured: at K ~ 10^4 the drift dominates the
-// dipole error of a whole trajectory), so their products are accumulated in chunks of 8 K blocks
-// (512 BF16 or 256 TF32 elements) and the chunks summed with round-to-nearest adds.  A single TF32
-// pass resolves only 2^-11 and keeps one accumulation.  RTCC_GEMM_CHUNK=<blocks> overrides (0: off).
+// dipole error of a whole trajectory), so their products are accumulated in chunks of 16 K blocks
+// (1024 BF16 or 512 TF32 elements) and the chunks summed with round-to-nearest adds (at the hexamer
+// shape: max|dmu| over 24 RK4 steps through the pulse 2.7e-6 au with chunks of 16 blocks, 2.3e-6 with
+// 8, 1.2e-5 after 8 steps without chunks).  A single TF32 pass resolves only 2^-11 and keeps one
+// accumulation.  RTCC_GEMM_CHUNK=<blocks> overrides (0: off).
 int accumulation_chunk(Prec prec) {
   if (prec != Prec::TF32X3 && prec != Prec::BF16X3) return 0;
   if (const char* e = std::getenv("RTCC_GEMM_CHUNK")) return std::max(0, std::atoi(e));
-  return 8;
+  return 16;
 }
 
 // Order labels by decreasing |stride| in tensor t (so the unit-stride label comes last).

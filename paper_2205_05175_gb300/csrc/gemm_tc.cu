@@ -120,6 +120,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// tcgen05.ld without the wait (the next tmem_ld32 waits for every load of the thread)
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
@@ -254,6 +267,9 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   const int nreg = (chunk > 0 && 4 * np_all * BN > 512) ? 1 : 2;
   const uint32_t tcols = (uint32_t)((chunk > 0 ? 2 : 1) * nreg * np_all * BN);
   const uint32_t slot0 = (uint32_t)(nreg * np_all * BN);   // first chunk slot column
+  // with one sum and one slot every chunk (the first too) goes through the slot and the epilogue
+  // starts the sum by a copy: the MMAs never wait for the previous item's write-out of the sum
+  const bool all_slots = chunk > 0 && nreg == 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -325,7 +341,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
       for (int w = blockIdx.x; w < total_items && alive; w += gridDim.x, ++local) {
         const Item it = decode_item<BN>(p, w, splits);
         const int a = local % nreg, u = local / nreg;
-        if (u > 0 && !mbar_wait(&tempty[a], (u - 1) & 1)) {
+        if (!all_slots && u > 0 && !mbar_wait(&tempty[a], (u - 1) & 1)) {
           atomicExch(p.err, DEV_TIMEOUT_MMA);
           break;
         }
@@ -339,7 +355,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             // chunk 0 of the plane accumulates into the item's sum, every later chunk into a slot
             // that the epilogue folds into the sum
             const int ci = chunk > 0 ? i % chunk : i;
-            if (chunk > 0 && ci == 0 && i > 0) {
+            if (chunk > 0 && ci == 0 && (i > 0 || all_slots)) {
               slot = gs % nreg;
               const uint32_t sp = gs / nreg;
               if (sp > 0 && !mbar_wait(&cempty[slot], (sp - 1) & 1)) {
@@ -365,7 +381,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             for (int kk = 0; kk < 4; ++kk)   // 4 MMAs of 32 bytes of K per 128-byte block
               tc_mma<KIND>(acc, ad + 2ull * kk, bd + 2ull * kk, id, (ci | kk) ? 1u : 0u);
             tc_commit(su32(&empty[s]));
-            if (chunk > 0 && i >= chunk && (ci == chunk - 1 || i == it.nvl - 1)) {
+            if (chunk > 0 && (i >= chunk || all_slots) && (ci == chunk - 1 || i == it.nvl - 1)) {
               tc_commit(su32(&cfull[slot]));   // this chunk's slot is complete
               ++gs;
             }
@@ -402,7 +418,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         const uint32_t lanes = ((uint32_t)(q * 32) << 16);
         for (int pl = 0; pl < it.np && alive; ++pl) {
           const int nch = (it.nvl + chunk - 1) / chunk;
-          for (int c = 1; c < nch; ++c, ++gs) {
+          for (int c = all_slots ? 0 : 1; c < nch; ++c, ++gs) {
             const uint32_t slot = gs % nreg, sp = gs / nreg;
             bool okc = mbar_wait(&cfull[slot], sp & 1);
             okc = __all_sync(0xffffffffu, okc);
@@ -414,14 +430,24 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             tc_fence_after();
             const uint32_t sum_c = tmem + lanes + (uint32_t)((a * it.np + pl) * BN + hc);
             const uint32_t slot_c = tmem + lanes + slot0 + (uint32_t)((slot * it.np + pl) * BN + hc);
+            if (c == 0) {   // the item's first chunk starts the sum
 #pragma unroll 1
-            for (int cc = 0; cc < WCOLS; cc += 32) {
-              uint32_t x[32], y[32];
-              tmem_ld32(slot_c + (uint32_t)cc, x);
-              tmem_ld32(sum_c + (uint32_t)cc, y);
+              for (int cc = 0; cc < WCOLS; cc += 32) {
+                uint32_t x[32];
+                tmem_ld32(slot_c + (uint32_t)cc, x);
+                tmem_st32(sum_c + (uint32_t)cc, x);
+              }
+            } else {
+#pragma unroll 1
+              for (int cc = 0; cc < WCOLS; cc += 32) {
+                uint32_t x[32], y[32];
+                tmem_ld32_nowait(slot_c + (uint32_t)cc, x);
+                tmem_ld32(sum_c + (uint32_t)cc, y);   // waits for both loads
 #pragma unroll
-              for (int j = 0; j < 32; ++j) y[j] = __float_as_uint(__fadd_rn(__uint_as_float(y[j]), __uint_as_float(x[j])));
-              tmem_st32(sum_c + (uint32_t)cc, y);
+                for (int j = 0; j < 32; ++j)
+                  y[j] = __float_as_uint(__fadd_rn(__uint_as_float(y[j]), __uint_as_float(x[j])));
+                tmem_st32(sum_c + (uint32_t)cc, y);
+              }
             }
             tmem_wait_st();
             tc_fence_before();

@@ -47,7 +47,7 @@ def test_complex_gemm_matches_float64(prec, kinds, shape):
 @pytest.mark.parametrize("kinds", ["rr", "cc"])
 def test_long_k_accumulation_is_chunked(prec, kinds):
     """A long K loop of same-sign products (K = 32768, nonnegative inputs, so the sum grows with
-    every product): the split modes accumulate on the tensor cores in chunks of 8 K blocks summed
+    every product): the split modes accumulate on the tensor cores in chunks of 16 K blocks summed
     with round-to-nearest float32 adds, which holds the result to a few parts in 10^6 of itself.
     The allocation-free entry point keeps one float32 accumulation over the whole K loop; its error
     is printed beside (the drift that chunking removes)."""
