@@ -437,16 +437,30 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
                 tmem_ld32(slot_c + (uint32_t)cc, x);
                 tmem_st32(sum_c + (uint32_t)cc, x);
               }
-            } else {
-#pragma unroll 1
-              for (int cc = 0; cc < WCOLS; cc += 32) {
-                uint32_t x[32], y[32];
-                tmem_ld32_nowait(slot_c + (uint32_t)cc, x);
-                tmem_ld32(sum_c + (uint32_t)cc, y);   // waits for both loads
+            } else if constexpr (WCOLS % 64 != 0) {
+              uint32_t x[32], y[32];
+              tmem_ld32_nowait(slot_c, x);
+              tmem_ld32(sum_c, y);   // waits for both loads
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
+              for (int j = 0; j < 32; ++j)
+                y[j] = __float_as_uint(__fadd_rn(__uint_as_float(y[j]), __uint_as_float(x[j])));
+              tmem_st32(sum_c, y);
+            } else {
+              // 64 columns per round trip: four loads in flight, one wait
+#pragma unroll 1
+              for (int cc = 0; cc < WCOLS; cc += 64) {
+                uint32_t x[32], y[32], x2[32], y2[32];
+                tmem_ld32_nowait(slot_c + (uint32_t)cc, x);
+                tmem_ld32_nowait(sum_c + (uint32_t)cc, y);
+                tmem_ld32_nowait(slot_c + (uint32_t)(cc + 32), x2);
+                tmem_ld32(sum_c + (uint32_t)(cc + 32), y2);   // waits for all four loads
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
                   y[j] = __float_as_uint(__fadd_rn(__uint_as_float(y[j]), __uint_as_float(x[j])));
+                  y2[j] = __float_as_uint(__fadd_rn(__uint_as_float(y2[j]), __uint_as_float(x2[j])));
+                }
                 tmem_st32(sum_c + (uint32_t)cc, y);
+                tmem_st32(sum_c + (uint32_t)(cc + 32), y2);
               }
             }
             tmem_wait_st();
@@ -684,6 +698,8 @@ void tc_gemm_plan(TcGemmPlan& pl, int kind, const void* A, int planesA, const vo
   splits = std::min(splits, 64);
   pl.p.vper = (nv + splits - 1) / splits;
   pl.splits = (nv + pl.p.vper - 1) / pl.p.vper;
+  // an item whose K loop fits in one chunk accumulates once, in the double-buffered accumulators
+  if (pl.p.chunk >= pl.p.vper) pl.p.chunk = 0;
 }
 
 void launch_tc_gemm(const TcGemmPlan& p, cudaStream_t s) {
