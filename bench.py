@@ -46,7 +46,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "RT-CCSD steps/s at o=30,v=114; tensor-pipe % of peak; max |dmu(t)| vs FP64"
 UNIT = "trajectory-steps/s"
-WORKLOAD = "water-hexamer-shaped RT-CCSD, o={o} v={v} naux={naux}, 12 Cash-Karp trajectories (tol 1e-6)"
+WORKLOAD = "water-hexamer-shaped RT-CCSD, o={o} v={v} naux={naux}, {nz} Cash-Karp trajectories (tol 1e-6)"
 E0S = (0.001, 0.01, 0.05, 0.1)
 POLS = ((1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0))
 NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25      # dense tensor-core rate ratio (nominal)
@@ -295,6 +295,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return 0
     o, v = getattr(args, "o", 30), getattr(args, "v", 114)
+    nz = getattr(args, "ntraj", 12)
     t0 = time.perf_counter()
     ratio = _rhs_over_omega()
     med, times = _omega_seconds(o, v, args.steps, args.warmup)
@@ -308,7 +309,7 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "step_kind": "sample (one T-residual evaluation of one trajectory)",
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD.format(o=o, v=v, naux=4 * (o + v)), "sample": sample},
+            "config": {"workload": WORKLOAD.format(o=o, v=v, naux=4 * (o + v), nz=nz), "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
@@ -491,32 +492,43 @@ def config_f1():
 
 
 def config_f3():
-    """Implicit Gauss-Legendre against RK4 at the same step: accuracy against a float64 RK4 run at a
-    quarter of the step, right-hand-side evaluations and wall time (dimer shape, 5 au)."""
+    """Implicit Gauss-Legendre against RK4: at RK4's step (stages by sweeps and by Newton-GMRES) and
+    at a step beyond RK4's stability limit (Newton-GMRES only; RK4 diverges there): accuracy against
+    a float64 RK4 run at a quarter of the short step, right-hand-side evaluations and wall time
+    (dimer shape, 6 au)."""
     import numpy as np
 
     from paper_2205_05175_gb300 import rtcc, synth
-    o, v, h, T = 10, 38, 0.05, 5.0
+    o, v, h, hl, T = 10, 38, 0.05, 0.4, 6.0
     f, B, mu = synth.make_system(o, v)
     fld = rtcc.make_field(E0=0.01, omega=0.5, sigma=0.5, t0=1.0, pol=(0.0, 0.0, 1.0))
-    n = int(round(T / h))
+    n, nl = int(round(T / h)), int(round(T / hl))
     with rtcc.Handle(f, B, mu, o, v, ntraj=1, prec=rtcc.P64) as H:
         H.ground_state(tol=1e-10)
         _, mref, k = H.propagate([fld], rtcc.make_integrator(rtcc.RK4, h=h / 4, nsteps=4 * n), 4 * n + 1)
-    mref = mref[0, :k[0]:4]
-    out = {"config": "f3", "workload": f"o={o} v={v}, E0=0.01 z sine pulse, {T} au at h={h}; reference float64 RK4 h={h / 4}",
-           "runs": {}}
+    mref = mref[0, :k[0]]
+    out = {"config": "f3", "workload": f"o={o} v={v}, E0=0.01 z sine pulse, {T} au at h={h} and h={hl}; "
+                                       f"reference float64 RK4 h={h / 4}", "runs": {}}
     for prec in ("p64", "bf16x3"):
         with rtcc.Handle(f, B, mu, o, v, ntraj=1, prec=rtcc.PRECISIONS[prec]) as H:
             H.ground_state(tol=1e-10)
             y0 = H.get_state(0)[0]
-            for name, integ in (("rk4", rtcc.make_integrator(rtcc.RK4, h=h, nsteps=n)),
-                                ("gl2", rtcc.make_integrator(rtcc.GL2, h=h, nsteps=n, tol=1e-6, sweeps=20))):
+            for name, hs, integ in (
+                    ("rk4", h, rtcc.make_integrator(rtcc.RK4, h=h, nsteps=n)),
+                    ("gl2", h, rtcc.make_integrator(rtcc.GL2, h=h, nsteps=n, tol=1e-6, sweeps=20)),
+                    ("gl2n", h, rtcc.make_integrator(rtcc.GL2_NEWTON, h=h, nsteps=n, tol=1e-6, sweeps=2, krylov=4)),
+                    ("rk4_long", hl, rtcc.make_integrator(rtcc.RK4, h=hl, nsteps=nl)),
+                    ("gl2n_long", hl, rtcc.make_integrator(rtcc.GL2_NEWTON, h=hl, nsteps=nl, tol=1e-6))):
                 H.set_state(0, y0, 0.0, 0.0)
+                stride = int(round(4 * hs / h))
                 t0 = time.perf_counter()
-                _, m, k = H.propagate([fld], integ, n + 1)
+                try:
+                    _, m, k = H.propagate([fld], integ, int(round(T / hs)) + 1)
+                except rtcc.RtccError as e:
+                    out["runs"][f"{name}_{prec}"] = {"status": e.status, "wall_s": round(time.perf_counter() - t0, 3)}
+                    continue
                 wall = time.perf_counter() - t0
-                out["runs"][f"{name}_{prec}"] = {"max_abs_dmu": float(np.abs(m[0, :k[0]] - mref).max()),
+                out["runs"][f"{name}_{prec}"] = {"h": hs, "max_abs_dmu": float(np.abs(m[0, :k[0]] - mref[::stride]).max()),
                                                  "rhs": H.last_stats()[2], "wall_s": round(wall, 3)}
     return out
 
@@ -674,6 +686,7 @@ def run_gpu(args, rank, world, local):
     prec = rtcc.PRECISIONS[args.prec]
     o, v = args.o, args.v
     fields = [rtcc.make_field(E0=e, omega=0.5, sigma=0.5, t0=1.0, pol=p) for p in POLS for e in E0S]
+    fields = fields[:args.ntraj]     # fewer trajectories: profiling runs only (the workload has 12)
     nz = len(fields)
     f, B, mu = synth.make_system(o, v)
     t_setup = time.perf_counter()
@@ -764,7 +777,7 @@ def run_gpu(args, rank, world, local):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / max(1, acc / nz), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
-                "config": {"workload": WORKLOAD.format(o=o, v=v, naux=4 * (o + v)), "o": o, "v": v, "naux": 4 * (o + v), "trajectories_per_gpu": nz,
+                "config": {"workload": WORKLOAD.format(o=o, v=v, naux=4 * (o + v), nz=nz), "o": o, "v": v, "naux": 4 * (o + v), "trajectories_per_gpu": nz,
                            "precision": args.prec, "accepted_steps": acc, "rejected_attempts": rej,
                            "rhs_evaluations": nrhs, "l2": "inputs larger than L2 (state 4.5 GB, vvvv 1.35 GB)",
                            "parallelism": f"replicas x{world}", "ground_state_setup_s": round(t_setup, 2),
@@ -790,6 +803,7 @@ def main(argv=None):
     ap.add_argument("--prec", default="bf16x3", choices=["p64", "tf32", "3xtf32", "bf16x3"])
     ap.add_argument("--o", type=int, default=30)
     ap.add_argument("--v", type=int, default=114)
+    ap.add_argument("--ntraj", type=int, default=12, help="trajectories (the workload has 12; fewer for profiling)")
     ap.add_argument("--gs-tol", type=float, default=1e-8)
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-dipole-error", action="store_true")

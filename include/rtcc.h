@@ -80,7 +80,7 @@ typedef struct {
     double sign;    /* +1 or -1 */
 } rtcc_field_t;
 
-typedef enum { RTCC_RK4 = 0, RTCC_CK = 1, RTCC_MIXED_RK4 = 2, RTCC_GL2 = 3 } rtcc_method_t;
+typedef enum { RTCC_RK4 = 0, RTCC_CK = 1, RTCC_MIXED_RK4 = 2, RTCC_GL2 = 3, RTCC_GL2_NEWTON = 4 } rtcc_method_t;
 
 /* Integrator settings (Sec. 2.1, Sec. 4.2).
  *   RK4:        fixed step h.
@@ -105,6 +105,18 @@ typedef enum { RTCC_RK4 = 0, RTCC_CK = 1, RTCC_MIXED_RK4 = 2, RTCC_GL2 = 3 } rtc
  *               stability limit, so they do not lengthen the usable step; what GL2 adds is
  *               that it conserves quadratic invariants (the norm, for Hermitian linear
  *               dynamics), which RK4 does not.
+ *   GL2_NEWTON: the same collocation method with the stage equations solved by `sweeps`
+ *               simplified Newton iterations (0: 6): the residuals G_i = K_i - f(t + c_i h,
+ *               y + h sum_j a_ij K_j) and a correction from (I - h A x J) dK = -G, where J is
+ *               the Jacobian of f at (t, y) applied by a forward difference of the library's own
+ *               right-hand side and the linear system is solved by GMRES with `krylov` Arnoldi
+ *               vectors (0: 12; at most 32; Hermitian inner product, classical Gram-Schmidt done
+ *               twice, Givens rotations, all on the device).  Each Newton iteration costs
+ *               2 + 2 krylov right-hand sides (one more per step for f(t, y)).  A step whose last
+ *               Newton correction still moves h K_2 by more than tol stops the call with
+ *               RTCC_ERR_NOCONV.  This converges for steps well beyond RK4's stability limit
+ *               (at o = 2, v = 6: h = 0.4, where the sweeps of GL2 diverge).  Device memory:
+ *               2 krylov + 9 state-sized complex vectors per trajectory, allocated on first use.
  * Stop after nsteps accepted steps if nsteps > 0, else at t_end (last step cut to land). */
 typedef struct {
     int method;        /* rtcc_method_t */
@@ -113,7 +125,8 @@ typedef struct {
     int max_rejects;
     int nsteps;
     double t_end;
-    int sweeps;        /* GL2 only */
+    int sweeps;        /* GL2: fixed-point sweeps; GL2_NEWTON: Newton iterations */
+    int krylov;        /* GL2_NEWTON only: Arnoldi vectors of the GMRES solve */
 } rtcc_integrator_t;
 
 typedef struct rtcc_ctx* rtcc_handle_t;

@@ -223,6 +223,43 @@ class RTCC:
             raise RuntimeError("implicit stages did not converge")
         return y + h * (b[0] * K[0] + b[1] * K[1])
 
+    def jacobian(self, tt, y, fld, step=0.1):
+        """J = d rhs / d y at (tt, y), one column per unit vector by the five-point stencil in a
+        complex scalar; exact up to rounding because the right-hand side is a polynomial of degree
+        at most four in y (and holomorphic: no conjugates)."""
+        n = y.size
+        J = np.empty((n, n), dtype=complex)
+        for k in range(n):
+            e = np.zeros(n, dtype=complex)
+            e[k] = step
+            J[:, k] = (self.rhs(tt, y - 2 * e, fld) - 8 * self.rhs(tt, y - e, fld) + 8 * self.rhs(tt, y + e, fld)
+                       - self.rhs(tt, y + 2 * e, fld)) / (12 * step)
+        return J
+
+    def gl2_step_newton(self, tt, y, h, fld, tol=1e-13, maxiter=30, return_stages=False):
+        """The same collocation system as gl2_step, K_i = f(t + c_i h, y + h sum_j a_ij K_j), solved
+        by Newton's method: G_i(K) = K_i - f(...) with the exact Jacobian dG_i/dK_j = delta_ij -
+        h a_ij J(t + c_i h, Y_i) and a dense solve per iteration.  Converges for steps where the
+        fixed-point iteration diverges."""
+        c, a, b = GL2_TABLE["c"], GL2_TABLE["a"], GL2_TABLE["b"]
+        k0 = self.rhs(tt, y, fld)
+        K = [k0.copy(), k0.copy()]
+        n = y.size
+        for _ in range(maxiter):
+            Y = [y + h * (a[i][0] * K[0] + a[i][1] * K[1]) for i in range(2)]
+            G = [K[i] - self.rhs(tt + c[i] * h, Y[i], fld) for i in range(2)]
+            if max(float(np.abs(g).max()) for g in G) <= tol * max(1.0, max(float(np.abs(k).max()) for k in K)):
+                y1 = y + h * (b[0] * K[0] + b[1] * K[1])
+                return (y1, K) if return_stages else y1
+            J = [self.jacobian(tt + c[i] * h, Y[i], fld) for i in range(2)]
+            M = np.zeros((2 * n, 2 * n), dtype=complex)
+            for i in range(2):
+                for j in range(2):
+                    M[i * n:(i + 1) * n, j * n:(j + 1) * n] = (np.eye(n) if i == j else 0) - h * a[i][j] * J[i]
+            d = np.linalg.solve(M, -np.concatenate(G))
+            K = [K[0] + d[:n], K[1] + d[n:]]
+        raise RuntimeError("Newton iterations of the implicit stages did not converge")
+
     def ck_attempt(self, tt, y, h, fld):
         tab = as_float(CK_TABLE)
         ks = self.stages(tab, tt, y, h, fld)
@@ -233,7 +270,8 @@ class RTCC:
 
 @dataclass
 class Integrator:
-    method: str = "rk4"          # "rk4", "ck", "mixed", "gl2" (implicit Gauss-Legendre)
+    method: str = "rk4"          # "rk4", "ck", "mixed", "gl2" (implicit Gauss-Legendre, fixed point),
+                                 # "gl2n" (the same, Newton)
     h: float = 0.05
     h1: float = 0.005
     h2: float = 0.05
@@ -264,14 +302,14 @@ def propagate(sys: RTCC, y0, fld: Field, integ: Integrator, t_start=0.0):
     times, mus = [tt], [sys.dipole(y)]
     stats = {"accepted": 0, "rejected": 0, "rhs_evals": 0}
     eps = 1e-12
-    if integ.method in ("rk4", "mixed", "gl2"):
+    if integ.method in ("rk4", "mixed", "gl2", "gl2n"):
         step = 0
         while True:
             if integ.nsteps > 0 and step >= integ.nsteps:
                 break
             if integ.nsteps <= 0 and tt >= integ.t_end - eps:
                 break
-            if integ.method in ("rk4", "gl2"):
+            if integ.method in ("rk4", "gl2", "gl2n"):
                 h = integ.h
             else:
                 h = integ.h1 if tt < integ.t_switch - eps else integ.h2
@@ -279,7 +317,12 @@ def propagate(sys: RTCC, y0, fld: Field, integ: Integrator, t_start=0.0):
                     h = min(h, integ.t_switch - tt)
             if integ.nsteps <= 0:
                 h = min(h, integ.t_end - tt)
-            y = sys.rk4_step(tt, y, h, fld) if integ.method != "gl2" else sys.gl2_step(tt, y, h, fld)
+            if integ.method == "gl2":
+                y = sys.gl2_step(tt, y, h, fld)
+            elif integ.method == "gl2n":
+                y = sys.gl2_step_newton(tt, y, h, fld)
+            else:
+                y = sys.rk4_step(tt, y, h, fld)
             tt = tt + h
             step += 1
             stats["accepted"] += 1

@@ -195,7 +195,8 @@ struct TcGemmPlan {
   TcGemmParams p;
   int kind;            // 0 tf32, 1 bf16
   int bn;              // N tile (64, 128 or 256)
-  int variant;         // 0: default stages and epilogue warps for bn; 1: bn 128 with 6 stages, 4 epilogue warps
+  int variant;         // 0: default stages and epilogue warps for bn; 1: bn 128 with 6 stages and 4
+                       // epilogue warps, or bn 256 with 3 stages and 8 epilogue warps
   int splits;
   long long NB;
 };

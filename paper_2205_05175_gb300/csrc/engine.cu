@@ -1268,12 +1268,16 @@ int Engine::autotune(Program& P) {
         best = it->second;
       } else {
         float tbest = 0.f;
-        for (int bn : {64, 128, 256}) {
+        // candidates (code 2 * bn + variant): N tiles of 64, 128 and 256 columns, and the 256 tile
+        // with three stages and eight epilogue warps (a faster chunk fold, a shallower pipeline)
+        for (int cand : {128, 256, 512, 513}) {
+          const int bn = cand / 2, var = cand & 1;
           if (bn > 64 && N <= bn / 2) continue;   // a tile twice as wide as N or more
           TcGemmPlan trial = g->tcp;
           tc_gemm_plan(trial, g->tc_kind, g->pa.dst, g->pa.nrb, g->pb.dst, g->pb.nrb, M, N, g->Kpad, g->NB, dev_err_, bn,
                        g->chunk);
           if (trial.bn != bn) continue;           // not usable for this item kind
+          trial.variant = var;
           launch_tc_gemm(trial, stream_);
           float tmin = 0.f;
           for (int r = 0; r < 3; ++r) {
@@ -1287,14 +1291,15 @@ int Engine::autotune(Program& P) {
           }
           if (best == 0 || tmin < tbest) {
             tbest = tmin;
-            best = bn;
+            best = cand;
           }
         }
         tile_cache_[key] = best;
       }
-      if (best != 0 && best != g->tcp.bn) {
+      if (best != 0 && best != 2 * g->tcp.bn + g->tcp.variant) {
         tc_gemm_plan(g->tcp, g->tc_kind, g->pa.dst, g->pa.nrb, g->pb.dst, g->pb.nrb, M, N, g->Kpad, g->NB, dev_err_,
-                     best, g->chunk);
+                     best / 2, g->chunk);
+        g->tcp.variant = best & 1;
         ++changed;
       }
     }

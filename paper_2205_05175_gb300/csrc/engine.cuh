@@ -137,8 +137,8 @@ class Engine {
 
   void run(const Program& P);
   // Tile autotuner: times every tensor-core GEMM of P (after finalize) with each usable N tile
-  // (64, 128, 256) on this GPU and keeps the fastest; choices are cached per GEMM shape on the
-  // engine.  Runs kernels on the stream: outside stream capture, and only while no data in the
+  // (64, 128, 256 columns; the 256 tile also with three stages and eight epilogue warps) on this
+  // GPU and keeps the fastest; choices are cached per GEMM shape on the engine.  Runs kernels on the stream: outside stream capture, and only while no data in the
   // programs' outputs or temporaries is needed (they are recomputed by every program run).
   // Returns the number of GEMMs whose tile changed.
   int autotune(Program& P);

@@ -387,6 +387,14 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             }
           }
         }
+        // With one sum the item's MMAs never wait for the previous write-out, so the commit below must:
+        // an mbarrier phase completes only once its waiter has seen the previous one, and a short item
+        // (a split remainder of a few K blocks, or none) could otherwise complete tfull twice before the
+        // epilogue waits on the first completion, which it would then never see.
+        if (all_slots && alive && local > 0 && !mbar_wait(&tempty[a], (local - 1) & 1)) {
+          atomicExch(p.err, DEV_TIMEOUT_MMA);
+          break;
+        }
         tc_commit(su32(&tfull[a]));   // arrives when this tile's MMAs have completed
       }
     }
@@ -708,13 +716,21 @@ void launch_tc_gemm(const TcGemmPlan& p, cudaStream_t s) {
     else if (p.bn == 128) {
       if (p.variant == 1) launch_inst<128, 0, 6, 4>(p, s);
       else launch_inst<128, 0, 5, 8>(p, s);
-    } else launch_inst<256, 0, 4, 4>(p, s);
+    } else if (p.variant == 1) {
+      launch_inst<256, 0, 3, 8>(p, s);
+    } else {
+      launch_inst<256, 0, 4, 4>(p, s);
+    }
   } else {
     if (p.bn == 64) launch_inst<64, 1, 7, 8>(p, s);
     else if (p.bn == 128) {
       if (p.variant == 1) launch_inst<128, 1, 6, 4>(p, s);
       else launch_inst<128, 1, 5, 8>(p, s);
-    } else launch_inst<256, 1, 4, 4>(p, s);
+    } else if (p.variant == 1) {
+      launch_inst<256, 1, 3, 8>(p, s);
+    } else {
+      launch_inst<256, 1, 4, 4>(p, s);
+    }
   }
 }
 

@@ -2,6 +2,7 @@
 // propagation with a device-side step controller, dipole recording, spectrum.
 #include "model.cuh"
 #include "pade_core.cuh"
+#include <algorithm>
 #include <vector>
 #include "../../include/rtcc.h"
 #include <cmath>
@@ -30,6 +31,8 @@ struct Tableau {
   bool adaptive;
   bool implicit = false;   // full A: stages solved by fixed-point sweeps
   int sweeps = 0;
+  bool newton = false;     // implicit stages solved by simplified Newton iterations with GMRES
+  int krylov = 0;          // Arnoldi vectors per GMRES solve
 };
 
 Tableau rk4_tableau() {
@@ -57,6 +60,19 @@ Tableau gl2_tableau(int sweeps) {
   t.adaptive = false;
   t.implicit = true;
   t.sweeps = sweeps > 0 ? sweeps : 20;
+  return t;
+}
+
+constexpr int kKrylovMax = 32;
+
+// The same collocation method with the stage equations solved by `newton` simplified Newton
+// iterations, each correction from a GMRES solve with `krylov` Arnoldi vectors.
+Tableau gl2_newton_tableau(int newton, int krylov) {
+  Tableau t = gl2_tableau(0);
+  t.implicit = false;
+  t.newton = true;
+  t.sweeps = newton > 0 ? newton : 6;
+  t.krylov = krylov > 0 ? krylov : 12;
   return t;
 }
 
@@ -233,7 +249,7 @@ __global__ void k_prestep(Ctl c, rtcc_integrator_t in, int nz) {
   const double t = c.t[z];
   const double eps = 1e-12;
   double hs;
-  if (in.method == RTCC_RK4 || in.method == RTCC_GL2) hs = in.h;
+  if (in.method == RTCC_RK4 || in.method == RTCC_GL2 || in.method == RTCC_GL2_NEWTON) hs = in.h;
   else if (in.method == RTCC_MIXED_RK4) hs = (t < in.t_switch - eps) ? fmin(in.h1, in.t_switch - t) : in.h2;
   else hs = c.h[z];
   if (in.nsteps <= 0) hs = fmin(hs, in.t_end - t);
@@ -250,7 +266,7 @@ __global__ void k_controller(Ctl c, rtcc_integrator_t in, int nz) {
     c.status[z] = TS_DIVERGED;
     return;
   }
-  if (in.method == RTCC_GL2 && delta > in.tol) {
+  if ((in.method == RTCC_GL2 || in.method == RTCC_GL2_NEWTON) && delta > in.tol) {
     // the last Gauss-Seidel sweep still moved h K_2 by more than tol: the stages have not converged
     c.status[z] = TS_NOCONV;
     return;
@@ -621,6 +637,172 @@ __global__ void k_pade_eval(const double* coef, int M, double dt, double t0, dou
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Newton-Krylov kernels of the implicit Gauss-Legendre stages.  A Krylov vector holds both stage
+// blocks, each [nz][ns] complex; `bstride` is the distance (in doubles) between the two blocks and
+// blockIdx.y is the trajectory.  Every inner product is Hermitian: <v, w> = sum conj(v) w.
+
+// out[z][k] += <V_k, w>_z for k = blockIdx.z (V_k at V + k * vstride); out has ldo entries per z
+__global__ void k_zdots(const double* __restrict__ V, long long vstride, const double* __restrict__ w,
+                        long long bstride, long long ns, int ldo, double* out) {
+  const int z = blockIdx.y, k = blockIdx.z;
+  double sr = 0.0, si = 0.0;
+  for (int b = 0; b < 2; ++b) {
+    const double* vb = V + (size_t)k * vstride + (size_t)b * bstride + (size_t)z * 2 * ns;
+    const double* wb = w + (size_t)b * bstride + (size_t)z * 2 * ns;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ns; i += (long long)gridDim.x * blockDim.x) {
+      const double vr = vb[2 * i], vi = vb[2 * i + 1], wr = wb[2 * i], wi = wb[2 * i + 1];
+      sr += vr * wr + vi * wi;
+      si += vr * wi - vi * wr;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    sr += __shfl_down_sync(0xffffffffu, sr, off);
+    si += __shfl_down_sync(0xffffffffu, si, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&out[2 * ((size_t)z * ldo + k)], sr);
+    atomicAdd(&out[2 * ((size_t)z * ldo + k) + 1], si);
+  }
+}
+
+// w += alpha * sum_{k < nvec} coef[z][k] V_k   (coef complex, ldo entries per z)
+__global__ void k_zupdate(double* __restrict__ w, const double* __restrict__ V, long long vstride, int nvec,
+                          const double* __restrict__ coef, int ldo, double alpha, long long bstride, long long ns) {
+  const int z = blockIdx.y;
+  for (int b = 0; b < 2; ++b) {
+    double* wb = w + (size_t)b * bstride + (size_t)z * 2 * ns;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ns; i += (long long)gridDim.x * blockDim.x) {
+      double ar = 0.0, ai = 0.0;
+      for (int k = 0; k < nvec; ++k) {
+        const double* vb = V + (size_t)k * vstride + (size_t)b * bstride + (size_t)z * 2 * ns;
+        const double cr = coef[2 * ((size_t)z * ldo + k)], ci = coef[2 * ((size_t)z * ldo + k) + 1];
+        const double vr = vb[2 * i], vi = vb[2 * i + 1];
+        ar += cr * vr - ci * vi;
+        ai += cr * vi + ci * vr;
+      }
+      wb[2 * i] += alpha * ar;
+      wb[2 * i + 1] += alpha * ai;
+    }
+  }
+}
+
+// out = scale[z] * in over both stage blocks
+__global__ void k_zscale(double* __restrict__ out, const double* __restrict__ in, const double* __restrict__ scale,
+                         long long bstride, long long ns) {
+  const int z = blockIdx.y;
+  const double sc = scale[z];
+  for (int b = 0; b < 2; ++b) {
+    const size_t base = (size_t)b * bstride + (size_t)z * 2 * ns;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 2 * ns; i += (long long)gridDim.x * blockDim.x)
+      out[base + i] = sc * in[base + i];
+  }
+}
+
+// out = x - h_z (c0 u0 + c1 u1) over one block [nz][ns] complex
+__global__ void k_lincomb_h(double* __restrict__ out, const double* __restrict__ x, const double* __restrict__ u0,
+                            const double* __restrict__ u1, double c0, double c1, const double* __restrict__ hz,
+                            long long ns) {
+  const int z = blockIdx.y;
+  const double h = hz[z];
+  const size_t base = (size_t)z * 2 * ns;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 2 * ns; i += (long long)gridDim.x * blockDim.x)
+    out[base + i] = x[base + i] - h * (c0 * u0[base + i] + c1 * u1[base + i]);
+}
+
+// GMRES start: beta = |r0| (nrm holds <r0, r0>), V_0 = r0 / beta = -G / beta (scale), g = beta e_1
+__global__ void k_gm_start(const double* nrm, double* scale, double* g, int m, int nz) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= nz) return;
+  const double beta = sqrt(fmax(0.0, nrm[2 * z]));
+  scale[z] = (beta > 1e-300) ? -1.0 / beta : 0.0;
+  for (int k = 0; k <= m; ++k) {
+    g[2 * ((size_t)z * (m + 1) + k)] = (k == 0) ? beta : 0.0;
+    g[2 * ((size_t)z * (m + 1) + k) + 1] = 0.0;
+  }
+}
+
+// Column j of the Hessenberg matrix from the two Gram-Schmidt passes (d1 + d2) and |w|, the earlier
+// Givens rotations applied to it, a new rotation that zeroes H[j+1][j], and the rotated right-hand
+// side g; scale = 1 / H[j+1][j] normalises the next Arnoldi vector (0 after a breakdown).
+// Rotation k: [c_k, s_k; -conj(s_k), c_k] with c_k real.
+__global__ void k_gm_col(int j, int m, const double* d1, const double* d2, int ldo, const double* nrm, double* H,
+                         double* cs, double* sn, double* g, double* scale, int nz) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= nz) return;
+  double* Hz = H + 2 * (size_t)z * (m + 1) * m;          // H[r][c] at 2 * (r * m + c)
+  double* csz = cs + (size_t)z * m;
+  double* snz = sn + 2 * (size_t)z * m;
+  double* gz = g + 2 * (size_t)z * (m + 1);
+  for (int r = 0; r <= j; ++r) {
+    Hz[2 * (r * m + j)] = d1[2 * ((size_t)z * ldo + r)] + d2[2 * ((size_t)z * ldo + r)];
+    Hz[2 * (r * m + j) + 1] = d1[2 * ((size_t)z * ldo + r) + 1] + d2[2 * ((size_t)z * ldo + r) + 1];
+  }
+  const double hn = sqrt(fmax(0.0, nrm[2 * z]));
+  for (int k = 0; k < j; ++k) {
+    const double c = csz[k], sr = snz[2 * k], si = snz[2 * k + 1];
+    const double xr = Hz[2 * (k * m + j)], xi = Hz[2 * (k * m + j) + 1];
+    const double yr = Hz[2 * ((k + 1) * m + j)], yi = Hz[2 * ((k + 1) * m + j) + 1];
+    // x' = c x + s y ; y' = -conj(s) x + c y
+    Hz[2 * (k * m + j)] = c * xr + (sr * yr - si * yi);
+    Hz[2 * (k * m + j) + 1] = c * xi + (sr * yi + si * yr);
+    Hz[2 * ((k + 1) * m + j)] = -(sr * xr + si * xi) + c * yr;
+    Hz[2 * ((k + 1) * m + j) + 1] = -(sr * xi - si * xr) + c * yi;
+  }
+  const double ar = Hz[2 * (j * m + j)], ai = Hz[2 * (j * m + j) + 1];
+  const double aa = sqrt(ar * ar + ai * ai);
+  const double r = sqrt(aa * aa + hn * hn);
+  double c, sr, si;
+  if (r == 0.0) {
+    c = 1.0; sr = 0.0; si = 0.0;
+  } else if (aa == 0.0) {
+    c = 0.0; sr = 1.0; si = 0.0;
+  } else {
+    c = aa / r;
+    sr = ar / aa * hn / r;
+    si = ai / aa * hn / r;
+  }
+  csz[j] = c;
+  snz[2 * j] = sr;
+  snz[2 * j + 1] = si;
+  Hz[2 * (j * m + j)] = c * ar + sr * hn;
+  Hz[2 * (j * m + j) + 1] = c * ai + si * hn;
+  Hz[2 * ((j + 1) * m + j)] = 0.0;      // the rotation zeroes H[j+1][j]
+  Hz[2 * ((j + 1) * m + j) + 1] = 0.0;
+  const double gr = gz[2 * j], gi = gz[2 * j + 1];
+  gz[2 * (j + 1)] = -(sr * gr + si * gi);
+  gz[2 * (j + 1) + 1] = -(sr * gi - si * gr);
+  gz[2 * j] = c * gr;
+  gz[2 * j + 1] = c * gi;
+  scale[z] = (hn > 1e-300) ? 1.0 / hn : 0.0;
+}
+
+// Back substitution R y = g over the first m rows (a zero pivot contributes nothing)
+__global__ void k_gm_solve(int m, const double* H, const double* g, double* y, int ldo, int nz) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= nz) return;
+  const double* Hz = H + 2 * (size_t)z * (m + 1) * m;
+  const double* gz = g + 2 * (size_t)z * (m + 1);
+  double* yz = y + 2 * (size_t)z * ldo;
+  for (int k = m - 1; k >= 0; --k) {
+    double br = gz[2 * k], bi = gz[2 * k + 1];
+    for (int l = k + 1; l < m; ++l) {
+      const double hr = Hz[2 * (k * m + l)], hi = Hz[2 * (k * m + l) + 1];
+      br -= hr * yz[2 * l] - hi * yz[2 * l + 1];
+      bi -= hr * yz[2 * l + 1] + hi * yz[2 * l];
+    }
+    const double pr = Hz[2 * (k * m + k)], pi = Hz[2 * (k * m + k) + 1];
+    const double den = pr * pr + pi * pi;
+    if (den > 0.0) {
+      yz[2 * k] = (br * pr + bi * pi) / den;
+      yz[2 * k + 1] = (bi * pr - br * pi) / den;
+    } else {
+      yz[2 * k] = 0.0;
+      yz[2 * k + 1] = 0.0;
+    }
+  }
+}
+
 // y += alpha * x over complex state-sized buffers (alpha real)
 __global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, double alpha, long long n) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < 2 * n; k += (long long)gridDim.x * blockDim.x)
@@ -750,6 +932,14 @@ struct rtcc_ctx {
   rtcc_field_t* d_fields = nullptr;
   Ctl ctl{};
   std::vector<void*> allocs;
+  // Newton-Krylov work of the implicit Gauss-Legendre stages (allocated on first use)
+  struct Krylov {
+    int m = 0;
+    long long bstride = 0;                       // doubles per [nz][ns] complex block
+    double *V = nullptr, *W = nullptr, *DL = nullptr, *U = nullptr, *raw0 = nullptr;
+    double *d1 = nullptr, *d2 = nullptr, *nrm = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr,
+           *y = nullptr, *scale = nullptr, *eps = nullptr;
+  } kry;
   std::unique_ptr<GroundEngine> gs[4];   // per precision, one trajectory
   std::unique_ptr<AdjointEngine> adj;
   long long last_stats[4] = {0, 0, 0, 0};
@@ -819,6 +1009,46 @@ void tune_slots(rtcc_ctx* h, int nact) {
   h->E->autotune(d.prog);
 }
 
+// Step of the forward-difference Jacobian products of the Newton-Krylov stage solve (the Krylov
+// vectors have unit norm): small in float64; in the split modes large enough that the
+// right-hand side's rounding (about 1e-6 of it) stays well below the difference.
+double kry_eps(Prec p) { return p == Prec::P64 ? 1e-6 : 1e-3; }
+
+// Krylov work for m Arnoldi vectors over all slots (grown when a later call asks for more).
+void ensure_krylov(rtcc_ctx* h, int m) {
+  rtcc_ctx::Krylov& K = h->kry;
+  if (K.m >= m) return;
+  RTCC_CUDA(cudaStreamSynchronize(h->stream));
+  for (double* p : {K.V, K.W, K.DL, K.U, K.raw0, K.d1, K.d2, K.nrm, K.H, K.cs, K.sn, K.g, K.y, K.scale, K.eps}) {
+    if (!p) continue;
+    auto it = std::find(h->allocs.begin(), h->allocs.end(), (void*)p);
+    if (it != h->allocs.end()) h->allocs.erase(it);
+    cudaFree(p);
+  }
+  const size_t nz = h->nz, ldo = kKrylovMax + 1;
+  K.bstride = 2 * h->ns * (long long)nz;
+  const size_t bs = (size_t)K.bstride;
+  K.V = h->alloc<double>(2 * bs * (m + 1));
+  K.W = h->alloc<double>(2 * bs);
+  K.DL = h->alloc<double>(2 * bs);
+  K.U = h->alloc<double>(2 * bs);
+  K.raw0 = h->alloc<double>(bs);
+  K.d1 = h->alloc<double>(2 * nz * ldo);
+  K.d2 = h->alloc<double>(2 * nz * ldo);
+  K.y = h->alloc<double>(2 * nz * ldo);
+  K.nrm = h->alloc<double>(2 * nz);
+  K.H = h->alloc<double>(2 * nz * (m + 1) * m);
+  K.cs = h->alloc<double>(nz * m);
+  K.sn = h->alloc<double>(2 * nz * m);
+  K.g = h->alloc<double>(2 * nz * (m + 1));
+  K.scale = h->alloc<double>(nz);
+  K.eps = h->alloc<double>(nz);
+  std::vector<double> e(nz, kry_eps(h->prec));
+  RTCC_CUDA(cudaMemcpyAsync(K.eps, e.data(), sizeof(double) * nz, cudaMemcpyHostToDevice, h->stream));
+  RTCC_CUDA(cudaStreamSynchronize(h->stream));
+  K.m = m;
+}
+
 // One Runge-Kutta attempt over the first nact slots (stages, combination, controller, accept, dipole, record).
 void run_attempt(rtcc_ctx* h, const Tableau& tb, const rtcc_integrator_t& in, double* tout, double* muout, int max_out,
                  int nact) {
@@ -866,7 +1096,91 @@ void run_attempt(rtcc_ctx* h, const Tableau& tb, const rtcc_integrator_t& in, do
           RTCC_CUDA(cudaMemcpyAsync(h->Rk[st], h->Rout, rbytes, cudaMemcpyDeviceToDevice, s));
       }
   }
-  for (int st = 0; st < (tb.implicit ? 0 : tb.s); ++st) {
+  if (tb.newton) {
+    // Simplified Newton on G_i(K) = K_i - f(t + c_i h, y + h sum_j a_ij D K_j) (raw right-hand sides K_i),
+    // each correction from (I - h A x J) dK = -G with J = df/dy at (t, y), J v = (f(t, y + eps D v) -
+    // f(t, y)) / eps, solved by GMRES(m) from dK = 0: Arnoldi with classical Gram-Schmidt done twice,
+    // Givens rotations and the back substitution per trajectory on the device.
+    rtcc_ctx::Krylov& K = h->kry;
+    const int m = tb.krylov;
+    const long long bs = K.bstride;
+    const int ldo = kKrylovMax + 1;
+    const dim3 gv(gst.x, nz);
+    const unsigned gx = std::min<unsigned>(gst.x, 128u);
+    const unsigned gsc = (unsigned)((nz + 127) / 128);
+    auto jvp_stage = [&](const double* v) {   // Ys = y + eps_z D v
+      StageArgs A{};
+      A.nterms = 1;
+      A.R[0] = v;
+      A.coef[0] = 1.0;
+      if (h->prec != Prec::P64) k_stage<true><<<gst, 256, 0, s>>>(h->Ys, h->Y, A, K.eps, ns, nT);
+      else k_stage<false><<<gst, 256, 0, s>>>(h->Ys, h->Y, A, K.eps, ns, nT);
+      k_fock<<<dim3(blocks_for((long long)h->nmo * h->nmo), nz), 256, 0, s>>>(h->F, h->f0, h->mu, h->d_fields, h->ctl.t,
+                                                                             h->ctl.htry, 0.0, nz, h->nmo * h->nmo);
+      h->E->run(rp.fwd);
+      h->E->run(rp.rev);
+    };
+    auto dots = [&](const double* V, int nvec, const double* w, double* out, int ld) {
+      RTCC_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * 2 * (size_t)nz * ld, s));
+      k_zdots<<<dim3(gx, nz, nvec), 256, 0, s>>>(V, 2 * bs, w, bs, ns, ld, out);
+    };
+    StageArgs A0{};
+    stage_rhs(A0, 0.0);   // f(t, y): the starting stages and the base point of the Jacobian products
+    RTCC_CUDA(cudaMemcpyAsync(K.raw0, h->Rout, rbytes, cudaMemcpyDeviceToDevice, s));
+    RTCC_CUDA(cudaMemcpyAsync(h->Rk[0], h->Rout, rbytes, cudaMemcpyDeviceToDevice, s));
+    RTCC_CUDA(cudaMemcpyAsync(h->Rk[1], h->Rout, rbytes, cudaMemcpyDeviceToDevice, s));
+    for (int it = 0; it < tb.sweeps; ++it) {
+      for (int st = 0; st < 2; ++st) {   // G_i into W (block i)
+        StageArgs A{};
+        A.nterms = 2;
+        for (int j = 0; j < 2; ++j) {
+          A.R[j] = h->Rk[j];
+          A.coef[j] = tb.a[st][j];
+        }
+        stage_rhs(A, tb.c[st]);
+        Combo C{};
+        C.m = 2;
+        C.x[0] = h->Rk[st];
+        C.c[0] = 1.0;
+        C.x[1] = h->Rout;
+        C.c[1] = -1.0;
+        k_combine<<<blocks_for(ns * nz), 256, 0, s>>>(K.W + st * bs, C, ns * nz);
+      }
+      dots(K.W, 1, K.W, K.nrm, 1);
+      k_gm_start<<<gsc, 128, 0, s>>>(K.nrm, K.scale, K.g, m, nz);
+      k_zscale<<<gv, 256, 0, s>>>(K.V, K.W, K.scale, bs, ns);   // V_0 = -G / |G|
+      for (int j = 0; j < m; ++j) {
+        const double* Vj = K.V + (size_t)j * 2 * bs;
+        for (int jj = 0; jj < 2; ++jj) {   // u_jj = J D V_j[jj]
+          jvp_stage(Vj + jj * bs);
+          Combo C{};
+          C.m = 2;
+          C.x[0] = h->Rout;
+          C.c[0] = 1.0 / kry_eps(h->prec);
+          C.x[1] = K.raw0;
+          C.c[1] = -1.0 / kry_eps(h->prec);
+          k_combine<<<blocks_for(ns * nz), 256, 0, s>>>(K.U + jj * bs, C, ns * nz);
+        }
+        for (int i = 0; i < 2; ++i)   // W_i = V_j[i] - h sum_jj a_i,jj u_jj
+          k_lincomb_h<<<gv, 256, 0, s>>>(K.W + i * bs, Vj + i * bs, K.U, K.U + bs, tb.a[i][0], tb.a[i][1],
+                                         h->ctl.htry, ns);
+        dots(K.V, j + 1, K.W, K.d1, ldo);
+        k_zupdate<<<gv, 256, 0, s>>>(K.W, K.V, 2 * bs, j + 1, K.d1, ldo, -1.0, bs, ns);
+        dots(K.V, j + 1, K.W, K.d2, ldo);
+        k_zupdate<<<gv, 256, 0, s>>>(K.W, K.V, 2 * bs, j + 1, K.d2, ldo, -1.0, bs, ns);
+        dots(K.W, 1, K.W, K.nrm, 1);
+        k_gm_col<<<gsc, 128, 0, s>>>(j, m, K.d1, K.d2, ldo, K.nrm, K.H, K.cs, K.sn, K.g, K.scale, nz);
+        k_zscale<<<gv, 256, 0, s>>>(K.V + (size_t)(j + 1) * 2 * bs, K.W, K.scale, bs, ns);
+      }
+      k_gm_solve<<<gsc, 128, 0, s>>>(m, K.H, K.g, K.y, ldo, nz);
+      RTCC_CUDA(cudaMemsetAsync(K.DL, 0, rbytes, s));
+      RTCC_CUDA(cudaMemsetAsync(K.DL + bs, 0, rbytes, s));
+      k_zupdate<<<gv, 256, 0, s>>>(K.DL, K.V, 2 * bs, m, K.y, ldo, 1.0, bs, ns);
+      k_axpy<<<blocks_for(ns * nz), 256, 0, s>>>(h->Rk[0], K.DL, 1.0, ns * nz);
+      k_axpy<<<blocks_for(ns * nz), 256, 0, s>>>(h->Rk[1], K.DL + bs, 1.0, ns * nz);
+    }
+  }
+  for (int st = 0; st < ((tb.implicit || tb.newton) ? 0 : tb.s); ++st) {
     StageArgs A{};
     A.nterms = 0;
     for (int j = 0; j < st; ++j) {
@@ -897,6 +1211,18 @@ void run_attempt(rtcc_ctx* h, const Tableau& tb, const rtcc_integrator_t& in, do
     Ew.coef[j] = tb.e[j];
   }
   B.nterms = tb.s;
+  if (tb.newton) {
+    // the converged stages; error slot: h max |last Newton correction of K_2|
+    B.R[0] = h->Rk[0];
+    B.R[1] = h->Rk[1];
+    B.R[2] = h->kry.DL + h->kry.bstride;
+    B.coef[0] = tb.b[0];
+    B.coef[1] = tb.b[1];
+    B.coef[2] = 0.0;
+    Ew.coef[0] = Ew.coef[1] = 0.0;
+    Ew.coef[2] = 1.0;
+    B.nterms = 3;
+  }
   if (tb.implicit) {
     // error slot: +1 on the newest K_2 (Rout), -1 on the previous sweep's K_2 (Rk[1], weight 0 in y)
     for (int j = 0; j < tb.s; ++j) Ew.coef[j] = (j == tb.s - 1) ? 1.0 : 0.0;
@@ -905,7 +1231,7 @@ void run_attempt(rtcc_ctx* h, const Tableau& tb, const rtcc_integrator_t& in, do
     Ew.coef[tb.s] = -1.0;
     B.nterms = tb.s + 1;
   }
-  const int measure = (tb.adaptive || tb.implicit) ? 1 : 0;
+  const int measure = (tb.adaptive || tb.implicit || tb.newton) ? 1 : 0;
   pr.start(s);
   if (h->prec != Prec::P64)
     k_final<true><<<gst, 256, 0, s>>>(h->Ynew, h->Y, B, Ew, h->ctl.htry, ns, nT, h->ctl.err_bits, measure);
@@ -1482,9 +1808,13 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
   if (!h || !fields || !integ || max_out < 1 || !t_out || !mu_out || !n_out)
     return fail(RTCC_ERR_INVALID_ARG, "null argument or max_out < 1");
   const rtcc_integrator_t in = *integ;
-  if (in.method < 0 || in.method > 3) return fail(RTCC_ERR_INVALID_ARG, "unknown integrator");
+  if (in.method < 0 || in.method > 4) return fail(RTCC_ERR_INVALID_ARG, "unknown integrator");
   if (in.method == RTCC_GL2 && (!(in.h > 0) || !(in.tol > 0) || in.sweeps < 0 || in.sweeps > 1000))
     return fail(RTCC_ERR_INVALID_ARG, "Gauss-Legendre needs h > 0, tol > 0 and 0 <= sweeps <= 1000");
+  if (in.method == RTCC_GL2_NEWTON &&
+      (!(in.h > 0) || !(in.tol > 0) || in.sweeps < 0 || in.sweeps > 100 || in.krylov < 0 || in.krylov > kKrylovMax))
+    return fail(RTCC_ERR_INVALID_ARG,
+                "Gauss-Legendre (Newton) needs h > 0, tol > 0, 0 <= sweeps <= 100 and 0 <= krylov <= 32");
   if (in.nsteps <= 0 && !(in.t_end > 0)) return fail(RTCC_ERR_INVALID_ARG, "need nsteps > 0 or t_end > 0");
   if (in.method == RTCC_RK4 && !(in.h > 0)) return fail(RTCC_ERR_INVALID_ARG, "h must be positive");
   if (in.method == RTCC_MIXED_RK4 && !(in.h1 > 0 && in.h2 > 0)) return fail(RTCC_ERR_INVALID_ARG, "h1, h2 must be positive");
@@ -1532,7 +1862,11 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
                                                   " has no stored Cash-Karp step in [h_min, h_max]; pass h > 0");
       }
     }
-    const Tableau tb = (in.method == RTCC_CK) ? ck_tableau() : (in.method == RTCC_GL2 ? gl2_tableau(in.sweeps) : rk4_tableau());
+    const Tableau tb = (in.method == RTCC_CK)           ? ck_tableau()
+                       : (in.method == RTCC_GL2)        ? gl2_tableau(in.sweeps)
+                       : (in.method == RTCC_GL2_NEWTON) ? gl2_newton_tableau(in.sweeps, in.krylov)
+                                                        : rk4_tableau();
+    if (tb.newton) ensure_krylov(h, tb.krylov);
     run_dipole(h);
     k_record<<<(nz + 127) / 128, 128, 0, s>>>(h->ctl, h->DIP, h->mu_ref[0], h->mu_ref[1], h->mu_ref[2], tout, muout,
                                              max_out, nz, 1);
@@ -1696,7 +2030,9 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
         if (in.nsteps > 0) nz_need = in.nsteps - stp[z];
         else {
           const double hstep = (in.method == RTCC_CK) ? hz[z] * 5.0
-                               : ((in.method == RTCC_RK4 || in.method == RTCC_GL2) ? in.h : std::max(in.h1, in.h2));
+                               : ((in.method == RTCC_RK4 || in.method == RTCC_GL2 || in.method == RTCC_GL2_NEWTON)
+                                      ? in.h
+                                      : std::max(in.h1, in.h2));
           nz_need = (long long)std::floor((in.t_end - tz[z]) / hstep);
         }
         need = std::min(need, nz_need);
@@ -1724,7 +2060,10 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
     }
     h->last_stats[0] = cnt[0];
     h->last_stats[1] = cnt[1];
-    h->last_stats[2] = (cnt[0] + cnt[1]) * (tb.implicit ? 1 + (long long)tb.s * tb.sweeps : tb.s);
+    const long long per_attempt_rhs = tb.implicit ? 1 + (long long)tb.s * tb.sweeps
+                                      : tb.newton ? 1 + (long long)tb.sweeps * (2 + 2 * tb.krylov)
+                                                  : tb.s;
+    h->last_stats[2] = (cnt[0] + cnt[1]) * per_attempt_rhs;
     h->last_stats[3] = launches;
     h->last_slot_attempts = slot_attempts;
   });

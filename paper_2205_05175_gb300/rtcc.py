@@ -21,7 +21,7 @@ _lib = C.CDLL(LIB_PATH)
 
 P64, P32_TF32, P32_3XTF32, P32_BF16X3 = 0, 1, 2, 3
 PRECISIONS = {"p64": P64, "tf32": P32_TF32, "3xtf32": P32_3XTF32, "bf16x3": P32_BF16X3}
-RK4, CK, MIXED_RK4, GL2 = 0, 1, 2, 3
+RK4, CK, MIXED_RK4, GL2, GL2_NEWTON = 0, 1, 2, 3, 4
 CARRIER_SIN, CARRIER_COS = 0, 1
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOCONV", 5: "DIVERGED",
           6: "STEP_UNDERFLOW", 7: "TIMEOUT", 8: "UNSUPPORTED"}
@@ -36,7 +36,7 @@ class rtcc_integrator_t(C.Structure):
     _fields_ = [("method", C.c_int), ("h", C.c_double), ("h1", C.c_double), ("h2", C.c_double),
                 ("t_switch", C.c_double), ("tol", C.c_double), ("safety", C.c_double),
                 ("h_min", C.c_double), ("h_max", C.c_double), ("max_rejects", C.c_int),
-                ("nsteps", C.c_int), ("t_end", C.c_double), ("sweeps", C.c_int)]
+                ("nsteps", C.c_int), ("t_end", C.c_double), ("sweeps", C.c_int), ("krylov", C.c_int)]
 
 
 class rtcc_profile_t(C.Structure):
@@ -120,11 +120,11 @@ def make_field(E0=0.01, omega=0.5, sigma=0.5, t0=1.0, pol=(0.0, 0.0, 1.0), carri
 
 
 def make_integrator(method=RK4, h=0.05, h1=0.005, h2=0.05, t_switch=0.0, tol=1e-6, safety=0.84, h_min=1e-9,
-                    h_max=1.0, max_rejects=50, nsteps=0, t_end=0.0, sweeps=0):
+                    h_max=1.0, max_rejects=50, nsteps=0, t_end=0.0, sweeps=0, krylov=0):
     i = rtcc_integrator_t()
     i.method, i.h, i.h1, i.h2, i.t_switch = method, h, h1, h2, t_switch
     i.tol, i.safety, i.h_min, i.h_max, i.max_rejects = tol, safety, h_min, h_max, max_rejects
-    i.nsteps, i.t_end, i.sweeps = nsteps, t_end, sweeps
+    i.nsteps, i.t_end, i.sweeps, i.krylov = nsteps, t_end, sweeps, krylov
     return i
 
 

@@ -89,10 +89,11 @@ int main(void) {
   F(rtcc_integrator_t, t_switch); F(rtcc_integrator_t, tol); F(rtcc_integrator_t, safety);
   F(rtcc_integrator_t, h_min); F(rtcc_integrator_t, h_max); F(rtcc_integrator_t, max_rejects);
   F(rtcc_integrator_t, nsteps); F(rtcc_integrator_t, t_end); F(rtcc_integrator_t, sweeps);
+  F(rtcc_integrator_t, krylov);
   F(rtcc_profile_t, launches); F(rtcc_profile_t, ms); F(rtcc_profile_t, flops); F(rtcc_profile_t, bytes);
   printf("sizeof rtcc_field_t %zu\nsizeof rtcc_integrator_t %zu\nsizeof rtcc_profile_t %zu\n",
          sizeof(rtcc_field_t), sizeof(rtcc_integrator_t), sizeof(rtcc_profile_t));
-  printf("enum %d %d %d %d %d %d %d %d %d %d\n", RTCC_RK4, RTCC_CK, RTCC_MIXED_RK4, RTCC_GL2, RTCC_P64,
+  printf("enum %d %d %d %d %d %d %d %d %d %d %d\n", RTCC_RK4, RTCC_CK, RTCC_MIXED_RK4, RTCC_GL2, RTCC_GL2_NEWTON, RTCC_P64,
          RTCC_P32_TF32, RTCC_P32_3XTF32, RTCC_P32_BF16X3, RTCC_CARRIER_SIN, RTCC_CARRIER_COS);
   printf("status %d %d %d %d %d %d %d %d %d\n", RTCC_OK, RTCC_ERR_INVALID_ARG, RTCC_ERR_OOM, RTCC_ERR_CUDA,
          RTCC_ERR_NOCONV, RTCC_ERR_DIVERGED, RTCC_ERR_STEP_UNDERFLOW, RTCC_ERR_TIMEOUT, RTCC_ERR_UNSUPPORTED);
@@ -117,7 +118,7 @@ def test_struct_layouts_and_enums_match_the_header(lib, tmp_path):
         if w[0] == "sizeof":
             assert int(w[2]) == ctypes.sizeof(mirrors[w[1]]), line
         elif w[0] == "enum":
-            assert [int(x) for x in w[1:]] == [lib.RK4, lib.CK, lib.MIXED_RK4, lib.GL2, lib.P64, lib.P32_TF32,
+            assert [int(x) for x in w[1:]] == [lib.RK4, lib.CK, lib.MIXED_RK4, lib.GL2, lib.GL2_NEWTON, lib.P64, lib.P32_TF32,
                                                lib.P32_3XTF32, lib.P32_BF16X3, lib.CARRIER_SIN, lib.CARRIER_COS]
         elif w[0] == "status":
             names = ["OK", "INVALID_ARG", "OOM", "CUDA", "NOCONV", "DIVERGED", "STEP_UNDERFLOW", "TIMEOUT", "UNSUPPORTED"]

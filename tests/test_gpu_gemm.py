@@ -70,3 +70,20 @@ def test_long_k_accumulation_is_chunked(prec, kinds):
         err_one = "n/a"
     print(f"prec {prec} {kinds}: chunked {err:.2e}, one accumulation {err_one}")
     assert err < 1e-5, (err, err_one)
+
+
+@pytest.mark.parametrize("shape", [(40, 128, 256, 3000), (60, 64, 300, 2000), (24, 200, 260, 5000), (9, 130, 257, 8100)])
+def test_chunked_split_k_items(shape):
+    """Long K over few output tiles: the K loop is split across CTAs, and with chunked accumulation
+    (BF16x3) items of one or two chunks and short remainders follow each other on one CTA, the
+    case in which the single-sum protocol must not run a phase ahead of the epilogue."""
+    from paper_2205_05175_gb300 import rtcc
+    nb, M, N, K = shape
+    rng = np.random.default_rng(4321 + K)
+    A = rng.standard_normal((nb, M, K))
+    B = rng.standard_normal((nb, N, K))
+    ref = np.einsum("bmk,bnk->bmn", A, B)
+    for _ in range(3):
+        C = rtcc.rtcc_selftest_gemm(3, A, B)
+        err = np.abs(C - ref).max() / (np.abs(A).max() * np.abs(B).max() * K)
+        assert err < TOL[3], err

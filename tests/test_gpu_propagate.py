@@ -1,4 +1,4 @@
-"""Trajectory parity (RK4, Cash-Karp, mixed-step RK4, Gauss-Legendre) of the CUDA path against the oracle, the
+"""Trajectory parity (RK4, Cash-Karp, mixed-step RK4, Gauss-Legendre by sweeps and by Newton) of the CUDA path against the oracle, the
 zero-field fixed point, two-electron exactness against FCI, and batched-trajectory independence."""
 import numpy as np
 import pytest
@@ -109,6 +109,40 @@ def test_gauss_legendre_matches_oracle():
     assert stats[2] == 20 * (1 + 2 * 20)
     assert np.abs(t[0, :21] - tt).max() < 1e-12
     assert np.abs(m[0, :21] - mm).max() < 1e-10
+
+
+@pytest.mark.last
+def test_gauss_legendre_newton_beyond_the_fixed_point_limit_matches_oracle():
+    """h = 0.4 at o = 1, v = 4, where the Gauss-Seidel sweeps of the stage equations diverge: the
+    device's simplified Newton iterations with GMRES reach the collocation solution that the
+    oracle's dense Newton solve gives; the sweeps stop with NOCONV; the Krylov size is checked."""
+    from paper_2205_05175_gb300 import rtcc
+    o, v = 1, 4
+    f, B, mu = system(o, v)
+    s = rk.RTCC(f, B, mu, o)
+    y0, _, _ = s.ground_state(tol=1e-11)
+    fld = rk.Field(E0=0.05, omega=0.5, sigma=0.5, t0=0.5)
+    nsteps = 4
+    tt, mm, _, _ = rk.propagate(s, y0, fld, rk.Integrator(method="gl2n", h=0.4, nsteps=nsteps))
+    field = [rtcc.make_field(E0=0.05, t0=0.5)]
+    integ = rtcc.make_integrator(rtcc.GL2_NEWTON, h=0.4, nsteps=nsteps, tol=1e-12)
+    t, m, n, stats = _gpu_traj(o, v, f, B, mu, field, integ, 16, prec=0, y0=y0)
+    assert n[0] == nsteps + 1
+    assert stats[2] == nsteps * (1 + 6 * (2 + 2 * 12))
+    assert np.abs(t[0, :n[0]] - tt).max() < 1e-12
+    assert np.abs(m[0, :n[0]] - mm).max() < 1e-10
+    # the split-precision right-hand side: the same solution to the mode's accuracy
+    _, mb, nb, _ = _gpu_traj(o, v, f, B, mu, field, rtcc.make_integrator(rtcc.GL2_NEWTON, h=0.4, nsteps=nsteps, tol=1e-6),
+                             16, prec=rtcc.P32_BF16X3, y0=y0)
+    assert nb[0] == nsteps + 1 and np.abs(mb[0, :nb[0]] - mm).max() < 1e-5
+    with rtcc.Handle(f, B, mu, o, v, ntraj=1, prec=0) as h:
+        h.set_state(0, y0, 0.0, 0.0)
+        with pytest.raises(rtcc.RtccError) as e:
+            h.propagate(field, rtcc.make_integrator(rtcc.GL2, h=0.4, nsteps=nsteps, tol=1e-8, sweeps=20), 16)
+        assert e.value.status == "NOCONV"
+        with pytest.raises(rtcc.RtccError) as e:
+            h.propagate(field, rtcc.make_integrator(rtcc.GL2_NEWTON, h=0.4, nsteps=1, krylov=33), 16)
+        assert e.value.status == "INVALID_ARG"
 
 
 def test_zero_field_fixed_point_on_device():

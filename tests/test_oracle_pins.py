@@ -690,3 +690,55 @@ def test_stored_flop_table_is_the_counters():
     from oracle import flops
     doc = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "rhs_flops.json")))
     assert [tuple(r) for r in doc["rows"]] == [tuple(r) for r in flops.term_table()]
+
+
+def test_gauss_legendre_newton_is_the_pade_stability_function_beyond_the_fixed_point_limit():
+    """y' = -i H y, H Hermitian, at h ||H|| = 4: the Gauss-Legendre step is R(-i h H) y with R the
+    (2, 2) Pade approximant of exp, R(z) = (1 + z/2 + z^2/12) / (1 - z/2 + z^2/12) (a closed form),
+    which keeps the norm.  Newton's method reaches it; the fixed-point iteration diverges there."""
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal((6, 6)) + 1j * rng.standard_normal((6, 6))
+    H = (X + X.conj().T) / 2
+    H = H * (4.0 / np.abs(np.linalg.eigvalsh(H)).max())
+
+    class Lin(rk.RTCC):
+        def __init__(self):
+            pass
+
+        def rhs(self, tt, y, fld):
+            return -1j * (H @ y)
+
+    s = Lin()
+    y0 = rng.standard_normal(6) + 1j * rng.standard_normal(6)
+    h = 1.0
+    w, U = np.linalg.eigh(H)
+    z = -1j * h * w
+    R = (1 + z / 2 + z * z / 12) / (1 - z / 2 + z * z / 12)
+    exact = U @ (R * (U.conj().T @ y0))
+    y1 = s.gl2_step_newton(0.0, y0, h, None)
+    assert np.abs(y1 - exact).max() < 1e-12 * np.abs(y0).max()
+    assert abs(np.linalg.norm(y1) - np.linalg.norm(y0)) < 1e-12 * np.linalg.norm(y0)
+    with pytest.raises(RuntimeError):
+        s.gl2_step(0.0, y0, h, None, maxiter=60)
+
+
+def test_gauss_legendre_newton_equals_fixed_point_and_solves_collocation_rtcc():
+    """On the RT-CC equations (o = 1, v = 3, strong field): where the fixed-point iteration
+    converges, Newton's method gives the same step; at a step 4x longer it still satisfies the
+    collocation equations K_i = f(t + c_i h, y + h sum_j a_ij K_j) to rounding."""
+    o, v = 1, 3
+    f, B, mu = synth.make_system(o, v, seed=9)
+    s = rk.RTCC(f, B, mu, o)
+    y0, _, _ = s.ground_state(tol=1e-12)
+    fld = rk.Field(E0=2.0, omega=0.5, sigma=0.5, t0=1.0)
+    ya = s.gl2_step(0.9, y0, 0.05, fld)
+    yb = s.gl2_step_newton(0.9, y0, 0.05, fld)
+    assert np.abs(ya - yb).max() < 1e-12
+    # the longer step: the returned stages satisfy the stage equations and give the step
+    c, a = rk.GL2_TABLE["c"], rk.GL2_TABLE["a"]
+    h = 0.2
+    y1, K = s.gl2_step_newton(0.9, y0, h, fld, return_stages=True)
+    assert np.all(np.isfinite(y1)) and np.abs(y1 - y0).max() > 1e-4
+    assert np.abs(y0 + h * (K[0] + K[1]) / 2 - y1).max() < 1e-13
+    resid = [K[i] - s.rhs(0.9 + c[i] * h, y0 + h * (a[i][0] * K[0] + a[i][1] * K[1]), fld) for i in range(2)]
+    assert max(np.abs(r).max() for r in resid) < 1e-12
