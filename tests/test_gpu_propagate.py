@@ -145,6 +145,30 @@ def test_gauss_legendre_newton_beyond_the_fixed_point_limit_matches_oracle():
         assert e.value.status == "INVALID_ARG"
 
 
+@pytest.mark.last
+def test_gauss_legendre_newton_at_o2_v6_matches_the_stored_oracle_record():
+    """o = 2, v = 6, h = 0.4 (the sweeps diverge there): the device's Newton-Krylov steps against the
+    oracle's dense-Newton record written by tests/golden/make_gl2n_reference.py."""
+    import json
+    import os
+
+    from paper_2205_05175_gb300 import rtcc
+    with open(os.path.join(os.path.dirname(__file__), "golden", "gl2n_o2v6_h04.json")) as fh:
+        doc = json.load(fh)
+    o, v = doc["o"], doc["v"]
+    f, B, mu = synth.make_system(o, v, seed=doc["seed"])
+    y0 = np.array([complex(a, b) for a, b in doc["y0"]])
+    tt = np.array(doc["t"])
+    mm = np.array([[complex(r[2 * x], r[2 * x + 1]) for x in range(3)] for r in doc["mu"]])
+    fl = doc["field"]
+    integ = rtcc.make_integrator(rtcc.GL2_NEWTON, h=doc["h"], nsteps=doc["nsteps"], tol=1e-12, sweeps=10, krylov=20)
+    t, m, n, _ = _gpu_traj(o, v, f, B, mu, [rtcc.make_field(E0=fl["E0"], omega=fl["omega"], sigma=fl["sigma"],
+                                                             t0=fl["t0"])], integ, 8, prec=0, y0=y0)
+    assert n[0] == doc["nsteps"] + 1
+    assert np.abs(t[0, :n[0]] - tt).max() < 1e-12
+    assert np.abs(m[0, :n[0]] - mm).max() < 1e-10
+
+
 def test_zero_field_fixed_point_on_device():
     from paper_2205_05175_gb300 import rtcc
     o, v = 5, 19

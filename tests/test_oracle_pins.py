@@ -742,3 +742,22 @@ def test_gauss_legendre_newton_equals_fixed_point_and_solves_collocation_rtcc():
     assert np.abs(y0 + h * (K[0] + K[1]) / 2 - y1).max() < 1e-13
     resid = [K[i] - s.rhs(0.9 + c[i] * h, y0 + h * (a[i][0] * K[0] + a[i][1] * K[1]), fld) for i in range(2)]
     assert max(np.abs(r).max() for r in resid) < 1e-12
+
+
+def test_stored_gauss_legendre_newton_record_starts_from_the_oracle_ground_state():
+    """The stored dense-Newton record (tests/golden/gl2n_o2v6_h04.json) starts from the oracle's
+    ground state of the seeded system, samples every h, and its first dipole is that state's."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "gl2n_o2v6_h04.json")) as fh:
+        doc = json.load(fh)
+    o, v = doc["o"], doc["v"]
+    f, B, mu = synth.make_system(o, v, seed=doc["seed"])
+    s = rk.RTCC(f, B, mu, o)
+    y0, _, _ = s.ground_state(tol=1e-12)
+    ys = np.array([complex(a, b) for a, b in doc["y0"]])
+    assert np.abs(ys - y0).max() < 1e-10
+    assert np.allclose(doc["t"], doc["h"] * np.arange(doc["nsteps"] + 1), atol=1e-14)
+    m0 = s.dipole(ys)
+    assert np.abs(np.array(doc["mu"][0][0::2]) + 1j * np.array(doc["mu"][0][1::2]) - m0).max() < 1e-13
+    assert np.isfinite(doc["mu"]).all()
