@@ -180,6 +180,7 @@ struct TcEpilogue {
 };
 struct TcGemmParams {
   CUtensorMap tmA, tmB;
+  CUtensorMap tmA2, tmB2;   // the same operands as boxes of two consecutive K blocks (4-D maps)
   int M, N, nkb;       // rows of one A plane, rows of one B plane, K blocks per plane
   int nrb;             // output planes
   int fused;           // 1: one work item covers both planes of a complex output (nseg[0] == nseg[1])
@@ -187,6 +188,7 @@ struct TcGemmParams {
   TcSeg seg[2][kMaxSeg];
   int vper;            // virtual K blocks (segments x nkb) per split
   int chunk;           // K blocks per accumulation chunk (0: one accumulation over the item's K loop)
+  int nminor[2];       // leading segments of each output plane that hold a low-order split part
   int prefetch;        // L2 prefetch distance of the producer in K blocks (0: none)
   TcEpilogue epi;
   int* err;            // device error word
@@ -196,7 +198,10 @@ struct TcGemmPlan {
   int kind;            // 0 tf32, 1 bf16
   int bn;              // N tile (64, 128 or 256)
   int variant;         // 0: default stages and epilogue warps for bn; 1: bn 128 with 6 stages and 4
-                       // epilogue warps, or bn 256 with 3 stages and 8 epilogue warps
+                       // epilogue warps, or bn 256 with 3 stages and 8 epilogue warps; 2: two K
+                       // blocks per pipeline stage (one TMA box each for A and B), bn 128 with 3
+                       // stages or bn 256 with 2 stages, 4 epilogue warps (bn 64: as variant 0)
+  bool pair_maps;      // the two-K-block tensor maps could be encoded (variant 2 usable)
   int splits;
   long long NB;
 };

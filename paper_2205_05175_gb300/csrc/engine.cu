@@ -1268,15 +1268,17 @@ int Engine::autotune(Program& P) {
         best = it->second;
       } else {
         float tbest = 0.f;
-        // candidates (code 2 * bn + variant): N tiles of 64, 128 and 256 columns, and the 256 tile
-        // with three stages and eight epilogue warps (a faster chunk fold, a shallower pipeline)
-        for (int cand : {128, 256, 512, 513}) {
-          const int bn = cand / 2, var = cand & 1;
+        // candidates (code 4 * bn + variant): N tiles of 64, 128 and 256 columns; the 256 tile with
+        // three stages and eight epilogue warps (a faster chunk fold, a shallower pipeline); the 128
+        // and 256 tiles with two K blocks per pipeline stage
+        for (int cand : {256, 512, 514, 1024, 1025, 1026}) {
+          const int bn = cand / 4, var = cand & 3;
           if (bn > 64 && N <= bn / 2) continue;   // a tile twice as wide as N or more
           TcGemmPlan trial = g->tcp;
           tc_gemm_plan(trial, g->tc_kind, g->pa.dst, g->pa.nrb, g->pb.dst, g->pb.nrb, M, N, g->Kpad, g->NB, dev_err_, bn,
                        g->chunk);
           if (trial.bn != bn) continue;           // not usable for this item kind
+          if (var == 2 && !trial.pair_maps) continue;
           trial.variant = var;
           launch_tc_gemm(trial, stream_);
           float tmin = 0.f;
@@ -1296,10 +1298,10 @@ int Engine::autotune(Program& P) {
         }
         tile_cache_[key] = best;
       }
-      if (best != 0 && best != 2 * g->tcp.bn + g->tcp.variant) {
+      if (best != 0 && best != 4 * g->tcp.bn + g->tcp.variant) {
         tc_gemm_plan(g->tcp, g->tc_kind, g->pa.dst, g->pa.nrb, g->pb.dst, g->pb.nrb, M, N, g->Kpad, g->NB, dev_err_,
-                     best / 2, g->chunk);
-        g->tcp.variant = best & 1;
+                     best / 4, g->chunk);
+        g->tcp.variant = best & 3;
         ++changed;
       }
     }

@@ -22,6 +22,8 @@
 #include "common.cuh"
 #include <cudaTypedefs.h>
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 
 namespace rtcc {
 namespace {
@@ -72,6 +74,14 @@ __device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* tm, u
       "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(bar)
       : "memory");
 }
+// The same for a 4-D map whose box holds two consecutive K blocks: {x, row, K block, batch}.
+__device__ __forceinline__ void tma_load4(uint32_t dst, const CUtensorMap* tm, uint32_t bar, int y, int kb, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(0), "r"(y), "r"(kb), "r"(z), "r"(bar)
+      : "memory");
+}
 // L2 prefetch of one tile of a tensor map (no shared memory, no barrier): brings a K block that
 // the producer will load a few stages later from DRAM into L2, so that its TMA load hits in L2.
 __device__ __forceinline__ void tma_prefetch3(const CUtensorMap* tm, int x, int y, int z) {
@@ -106,6 +116,15 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
         : "memory");
   }
 }
+// tcgen05.wait::ld that names the loaded registers as operands, so that no use of them can be
+// scheduled before the wait; reg_after_wait orders further register arrays after the same wait.
+#define RTCC_R32_OPERANDS \
+  "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" : RTCC_R32_OPERANDS::"memory");
+}
+__device__ __forceinline__ void reg_after_wait(uint32_t (&r)[32]) { asm volatile("" : RTCC_R32_OPERANDS::"memory"); }
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -117,7 +136,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
         "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  tmem_wait_ld(r);
 }
 
 // tcgen05.ld without the wait (the next tmem_ld32 waits for every load of the thread)
@@ -143,6 +162,17 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
       "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
       "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
       : "memory");
+}
+// 16-column forms (32 lanes x 16 columns per warp), load with its wait
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])::"memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+               : "memory");
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
@@ -236,11 +266,34 @@ __device__ __forceinline__ void put_cplx(void* C, long long i, bool f32, float v
 // Persistent warp-specialised GEMM: each CTA walks work items (batch, output plane(s), split, tile);
 // two TMEM accumulator sets let the epilogue of one tile overlap the main loop of the next.
 // EPW epilogue warps: with 8, two warps share each TMEM lane quarter and split its columns.
-template <int BN, int KIND, int STAGES, int EPW>
+// KPB K blocks per pipeline stage: with 2, one TMA box of A and one of B carry two consecutive K
+// blocks (the TMA unit takes a roughly fixed time per stage for boxes up to 32 KB, so a stage that
+// carries twice the K halves that cost per MMA).  A stage holds two blocks when both lie in the
+// item's K range and in one segment; otherwise its second half (loaded, possibly zero-filled past
+// the last K block) is not used.
+// Accumulation chunk of virtual K block v (segment-major) of output plane rb.  The segments that
+// hold a low-order split part (hi x lo, lo x hi) come first and are summed in chunks of 16 x chunk
+// blocks: their products are 2^8 (BF16) or 2^11 (TF32) smaller than the hi x hi ones, so a long
+// float32 accumulation of them drifts no more than a chunk of the leading products does.  The
+// hi x hi segments follow in chunks of `chunk` blocks.
+__device__ __forceinline__ int chunk_of(const TcGemmParams& p, int rb, int v) {
+  const int mv = p.nminor[rb] * p.nkb, lm = 16 * p.chunk;
+  return v < mv ? v / lm : (mv + lm - 1) / lm + (v - mv) / p.chunk;
+}
+// First virtual K block after v that starts a new chunk (the MMA loop tracks chunks with it, one
+// division per chunk instead of several per K block).
+__device__ __forceinline__ int next_chunk_start(const TcGemmParams& p, int rb, int v) {
+  const int mv = p.nminor[rb] * p.nkb, lm = 16 * p.chunk;
+  return v < mv ? min(mv, (v / lm + 1) * lm) : mv + ((v - mv) / p.chunk + 1) * p.chunk;
+}
+
+template <int BN, int KIND, int STAGES, int EPW, int KPB>
 __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     tc_gemm_kernel(const __grid_constant__ TcGemmParams p, int splits, int total_items) {
-  constexpr int A_BYTES = BM * 128;
-  constexpr int B_BYTES = BN * 128;
+  static_assert(KPB == 1 || KPB == 2, "K blocks per stage");
+  constexpr int A_BLK = BM * 128, B_BLK = BN * 128;   // bytes of one K block of A and of B
+  constexpr int A_BYTES = A_BLK * KPB;
+  constexpr int B_BYTES = B_BLK * KPB;
   constexpr int KBLK = (KIND == 0) ? 32 : 64;
   constexpr int WCOLS = BN * 4 / EPW;   // accumulator columns per epilogue warp
   static_assert(WCOLS % 32 == 0, "epilogue column split");
@@ -265,6 +318,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   // two of each when they fit in the 512 columns (the epilogue of one item then overlaps the next)
   const int chunk = p.chunk;
   const int nreg = (chunk > 0 && 4 * np_all * BN > 512) ? 1 : 2;
+  const int nslot = nreg;
   const uint32_t tcols = (uint32_t)((chunk > 0 ? 2 : 1) * nreg * np_all * BN);
   const uint32_t slot0 = (uint32_t)(nreg * np_all * BN);   // first chunk slot column
   // with one sum and one slot every chunk (the first too) goes through the slot and the epilogue
@@ -303,9 +357,10 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         const Item it = decode_item<BN>(p, w, splits);
         for (int pl = 0; pl < it.np && alive; ++pl) {
           const int rb = it.rb + pl;
-          for (int i = 0; i < it.nvl; ++i, ++g) {
+          for (int i = 0; i < it.nvl; ++g) {
             const int v = it.v0 + i;
             const int sg = v / p.nkb, kb = v - sg * p.nkb;
+            const int nb = (KPB == 2 && i + 1 < it.nvl && kb + 1 < p.nkb) ? 2 : 1;   // K blocks used
             const uint32_t s = g % STAGES;
             if (g >= STAGES && !mbar_wait(&empty[s], ((g / STAGES) - 1) & 1)) {
               atomicExch(p.err, DEV_TIMEOUT_PRODUCER);
@@ -313,12 +368,18 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
               break;
             }
             mbar_arrive_tx(&full[s], A_BYTES + B_BYTES);
-            tma_load3(su32(sA + s * A_BYTES), &p.tmA, su32(&full[s]), kb * KBLK, p.seg[rb][sg].pa * p.M + it.m0,
-                      it.bz);
-            tma_load3(su32(sB + s * B_BYTES), &p.tmB, su32(&full[s]), kb * KBLK, p.seg[rb][sg].pb * p.N + it.n0,
-                      it.bz);
+            if constexpr (KPB == 2) {
+              tma_load4(su32(sA + s * A_BYTES), &p.tmA2, su32(&full[s]), p.seg[rb][sg].pa * p.M + it.m0, kb, it.bz);
+              tma_load4(su32(sB + s * B_BYTES), &p.tmB2, su32(&full[s]), p.seg[rb][sg].pb * p.N + it.n0, kb, it.bz);
+            } else {
+              tma_load3(su32(sA + s * A_BYTES), &p.tmA, su32(&full[s]), kb * KBLK, p.seg[rb][sg].pa * p.M + it.m0,
+                        it.bz);
+              tma_load3(su32(sB + s * B_BYTES), &p.tmB, su32(&full[s]), kb * KBLK, p.seg[rb][sg].pb * p.N + it.n0,
+                        it.bz);
+            }
+            i += nb;
             // the K block this loop loads `prefetch` iterations from now (same item and plane), into L2
-            if (p.prefetch > 0 && i + p.prefetch < it.nvl) {
+            if (KPB == 1 && p.prefetch > 0 && i - 1 + p.prefetch < it.nvl) {
               const int vf = v + p.prefetch;
               const int sgf = vf / p.nkb, kbf = vf - sgf * p.nkb;
               tma_prefetch3(&p.tmA, kbf * KBLK, p.seg[rb][sgf].pa * p.M + it.m0, it.bz);
@@ -351,40 +412,58 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
           const uint32_t acc_sum = tmem + (uint32_t)((a * it.np + pl) * BN);
           uint32_t acc = acc_sum;
           uint32_t slot = 0;
-          for (int i = 0; i < it.nvl; ++i, ++g) {
-            // chunk 0 of the plane accumulates into the item's sum, every later chunk into a slot
-            // that the epilogue folds into the sum
-            const int ci = chunk > 0 ? i % chunk : i;
-            if (chunk > 0 && ci == 0 && (i > 0 || all_slots)) {
-              slot = gs % nreg;
-              const uint32_t sp = gs / nreg;
-              if (sp > 0 && !mbar_wait(&cempty[slot], (sp - 1) & 1)) {
-                atomicExch(p.err, DEV_TIMEOUT_MMA);
-                alive = false;
-                break;
-              }
-              tc_fence_after();
-              acc = tmem + slot0 + (uint32_t)((slot * it.np + pl) * BN);
-            }
-            const int sg = (it.v0 + i) / p.nkb;
+          const int vend = it.v0 + it.nvl;
+          int cnext = chunk > 0 ? next_chunk_start(p, rb, it.v0) : vend;   // where the next chunk starts
+          bool later = false;                                             // past the item's first chunk
+          for (int i = 0; i < it.nvl && alive; ++g) {
+            const int v = it.v0 + i;
+            const int sg = v / p.nkb;
+            const int nb = (KPB == 2 && i + 1 < it.nvl && v - sg * p.nkb + 1 < p.nkb) ? 2 : 1;   // as the producer
             const uint32_t s = g % STAGES;
-            if (!mbar_wait(&full[s], (g / STAGES) & 1)) {
-              atomicExch(p.err, DEV_TIMEOUT_MMA);
-              alive = false;
-              break;
-            }
-            tc_fence_after();
-            const uint64_t ad = sdesc_sw128(su32(sA + s * A_BYTES));
-            const uint64_t bd = sdesc_sw128(su32(sB + s * B_BYTES));
-            const uint32_t id = idesc | ((uint32_t)p.seg[rb][sg].neg << 13);   // negate A for -Ai Bi
+            for (int j = 0; j < nb; ++j) {
+              const int vb = v + j;   // virtual K block
+              // chunk 0 of the plane accumulates into the item's sum, every later chunk into a slot
+              // that the epilogue folds into the sum
+              bool cstart = j == 0 && i == 0;
+              if (vb == cnext) {
+                cstart = true;
+                later = true;
+                cnext = next_chunk_start(p, rb, vb);
+              }
+              const bool cend = vb + 1 == vend || vb + 1 == cnext;
+              if (chunk > 0 && cstart && (later || all_slots)) {
+                slot = gs % nslot;
+                const uint32_t sp = gs / nslot;
+                if (sp > 0 && !mbar_wait(&cempty[slot], (sp - 1) & 1)) {
+                  atomicExch(p.err, DEV_TIMEOUT_MMA);
+                  alive = false;
+                  break;
+                }
+                tc_fence_after();
+                acc = tmem + slot0 + (uint32_t)((slot * it.np + pl) * BN);
+              }
+              if (j == 0) {
+                if (!mbar_wait(&full[s], (g / STAGES) & 1)) {
+                  atomicExch(p.err, DEV_TIMEOUT_MMA);
+                  alive = false;
+                  break;
+                }
+                tc_fence_after();
+              }
+              const uint64_t ad = sdesc_sw128(su32(sA + s * A_BYTES + j * A_BLK));
+              const uint64_t bd = sdesc_sw128(su32(sB + s * B_BYTES + j * B_BLK));
+              const uint32_t id = idesc | ((uint32_t)p.seg[rb][sg].neg << 13);   // negate A for -Ai Bi
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)   // 4 MMAs of 32 bytes of K per 128-byte block
-              tc_mma<KIND>(acc, ad + 2ull * kk, bd + 2ull * kk, id, (ci | kk) ? 1u : 0u);
-            tc_commit(su32(&empty[s]));
-            if (chunk > 0 && (i >= chunk || all_slots) && (ci == chunk - 1 || i == it.nvl - 1)) {
-              tc_commit(su32(&cfull[slot]));   // this chunk's slot is complete
-              ++gs;
+              for (int kk = 0; kk < 4; ++kk)   // 4 MMAs of 32 bytes of K per 128-byte block
+                tc_mma<KIND>(acc, ad + 2ull * kk, bd + 2ull * kk, id, (cstart && kk == 0) ? 0u : 1u);
+              if (chunk > 0 && (later || all_slots) && cend) {
+                tc_commit(su32(&cfull[slot]));   // this chunk's slot is complete
+                ++gs;
+              }
             }
+            if (!alive) break;
+            tc_commit(su32(&empty[s]));   // the stage is free once its MMAs have read it
+            i += nb;
           }
         }
         // With one sum the item's MMAs never wait for the previous write-out, so the commit below must:
@@ -420,14 +499,15 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     for (int w = blockIdx.x; w < total_items && alive; w += gridDim.x, ++local) {
       const Item it = decode_item<BN>(p, w, splits);
       const int a = local % nreg, u = local / nreg;
-      // fold every chunk after the first into the plane's sum, in the order the MMA warp issued them:
-      // sum += slot with round-to-nearest float32 adds, then the slot is handed back
       if (chunk > 0) {
+        // fold every chunk after the first into the plane's sum, in the order the MMA warp issued
+        // them: sum += slot with round-to-nearest float32 adds, then the slot is handed back
         const uint32_t lanes = ((uint32_t)(q * 32) << 16);
         for (int pl = 0; pl < it.np && alive; ++pl) {
-          const int nch = (it.nvl + chunk - 1) / chunk;
+          const int rbp = it.rb + pl;
+          const int nch = it.nvl > 0 ? chunk_of(p, rbp, it.v0 + it.nvl - 1) - chunk_of(p, rbp, it.v0) + 1 : 0;
           for (int c = all_slots ? 0 : 1; c < nch; ++c, ++gs) {
-            const uint32_t slot = gs % nreg, sp = gs / nreg;
+            const uint32_t slot = gs % nslot, sp = gs / nslot;
             bool okc = mbar_wait(&cfull[slot], sp & 1);
             okc = __all_sync(0xffffffffu, okc);
             if (!okc) {
@@ -438,6 +518,37 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             tc_fence_after();
             const uint32_t sum_c = tmem + lanes + (uint32_t)((a * it.np + pl) * BN + hc);
             const uint32_t slot_c = tmem + lanes + slot0 + (uint32_t)((slot * it.np + pl) * BN + hc);
+            if constexpr (WCOLS <= 128) {
+              // the slot's columns are copied into registers and the slot is handed back at once, so
+              // the MMAs wait only for these loads; the sum is updated afterwards
+              constexpr int NP = WCOLS / 32;
+              uint32_t xs[NP][32];
+#pragma unroll
+              for (int k = 0; k < NP; ++k) tmem_ld32_nowait(slot_c + (uint32_t)(32 * k), xs[k]);
+              tmem_wait_ld(xs[0]);
+#pragma unroll
+              for (int k = 1; k < NP; ++k) reg_after_wait(xs[k]);
+              tc_fence_before();
+              mbar_arrive(&cempty[slot]);
+#pragma unroll
+              for (int k = 0; k < NP; ++k) {
+                if (c == 0) {   // the item's first chunk starts the sum
+                  tmem_st32(sum_c + (uint32_t)(32 * k), xs[k]);
+                } else {   // 16 columns at a time: the copy of the slot already holds most registers
+#pragma unroll
+                  for (int hh = 0; hh < 2; ++hh) {
+                    uint32_t y[16];
+                    tmem_ld16(sum_c + (uint32_t)(32 * k + 16 * hh), y);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                      y[j] = __float_as_uint(__fadd_rn(__uint_as_float(y[j]), __uint_as_float(xs[k][16 * hh + j])));
+                    tmem_st16(sum_c + (uint32_t)(32 * k + 16 * hh), y);
+                  }
+                }
+              }
+              tmem_wait_st();
+              continue;
+            }
             if (c == 0) {   // the item's first chunk starts the sum
 #pragma unroll 1
               for (int cc = 0; cc < WCOLS; cc += 32) {
@@ -449,6 +560,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
               uint32_t x[32], y[32];
               tmem_ld32_nowait(slot_c, x);
               tmem_ld32(sum_c, y);   // waits for both loads
+              reg_after_wait(x);
 #pragma unroll
               for (int j = 0; j < 32; ++j)
                 y[j] = __float_as_uint(__fadd_rn(__uint_as_float(y[j]), __uint_as_float(x[j])));
@@ -462,6 +574,9 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
                 tmem_ld32_nowait(sum_c + (uint32_t)cc, y);
                 tmem_ld32_nowait(slot_c + (uint32_t)(cc + 32), x2);
                 tmem_ld32(sum_c + (uint32_t)(cc + 32), y2);   // waits for all four loads
+                reg_after_wait(x);
+                reg_after_wait(y);
+                reg_after_wait(x2);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                   y[j] = __float_as_uint(__fadd_rn(__uint_as_float(y[j]), __uint_as_float(x[j])));
@@ -615,9 +730,9 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
   }
 }
 
-template <int BN, int KIND, int STAGES, int EPW>
+template <int BN, int KIND, int STAGES, int EPW, int KPB>
 constexpr size_t smem_bytes() {
-  return 1024 + (size_t)STAGES * (BM * 128 + BN * 128) + (size_t)EPW * 32 * 33 * 4 + (size_t)2 * 4 * BN * 8 +
+  return 1024 + (size_t)STAGES * KPB * (BM * 128 + BN * 128) + (size_t)EPW * 32 * 33 * 4 + (size_t)2 * 4 * BN * 8 +
          (2 * STAGES + 8) * 8 + 16;
 }
 
@@ -650,10 +765,29 @@ void make_map(CUtensorMap* tm, int kind, const void* ptr, long long rows, long l
   if (r != CUDA_SUCCESS) throw Error(3, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
 }
 
-template <int BN, int KIND, int STAGES, int EPW>
+// The same operand as a 4-D view {K within a block, row, K block, batch} (strides: row, 128 bytes,
+// batch) whose box holds two consecutive K blocks of box_rows rows: in shared memory the two
+// blocks land one after the other, each laid out as a single-block box.  Returns false when the
+// driver does not accept the view (the two-block variant is then not used).
+bool make_map_pair(CUtensorMap* tm, int kind, const void* ptr, long long rows, long long Kpad, long long NB,
+                   int box_rows) {
+  const int esz = (kind == 0) ? 4 : 2;
+  const long long nkb = Kpad * esz / 128;
+  cuuint64_t dims[4] = {(cuuint64_t)(128 / esz), (cuuint64_t)rows, (cuuint64_t)nkb, (cuuint64_t)NB};
+  cuuint64_t strides[3] = {(cuuint64_t)(Kpad * esz), 128, (cuuint64_t)(rows * Kpad * esz)};
+  cuuint32_t box[4] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows, 2, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = encode_fn()(tm, kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
+                           const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN, int KIND, int STAGES, int EPW, int KPB = 1>
 void launch_inst(const TcGemmPlan& pl, cudaStream_t s) {
-  auto kern = tc_gemm_kernel<BN, KIND, STAGES, EPW>;
-  constexpr size_t sm = smem_bytes<BN, KIND, STAGES, EPW>();
+  auto kern = tc_gemm_kernel<BN, KIND, STAGES, EPW, KPB>;
+  constexpr size_t sm = smem_bytes<BN, KIND, STAGES, EPW, KPB>();
   static_assert(sm <= 227 * 1024, "shared memory budget");
   static bool attr = false;
   if (!attr) {
@@ -684,6 +818,17 @@ void tc_gemm_plan(TcGemmPlan& pl, int kind, const void* A, int planesA, const vo
   pl.kind = kind;
   pl.bn = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
   if (bn == 64 || bn == 128 || bn == 256) pl.bn = bn;
+  // RTCC_GEMM_TILE=<n>[:<variant>] forces the tile (n = 64, 128 or 256) and its variant, for tests
+  // of every kernel instantiation; a complex output fused into one item still takes n <= 128
+  int forced_variant = -1;
+  if (const char* e = std::getenv("RTCC_GEMM_TILE")) {
+    int fb = 0, fv = 0;
+    const int got = std::sscanf(e, "%d:%d", &fb, &fv);
+    if (got >= 1 && (fb == 64 || fb == 128 || fb == 256)) {
+      pl.bn = fb;
+      forced_variant = got == 2 ? std::max(0, std::min(fv, 2)) : 0;
+    }
+  }
   // Short K loops leave the epilogue as the bottleneck: one item then covers both planes of a
   // complex output (whole 16-byte elements written once, by eight epilogue warps).  Two planes
   // of accumulators, double-buffered, fit TMEM's 512 columns up to a 128-column tile.
@@ -697,6 +842,8 @@ void tc_gemm_plan(TcGemmPlan& pl, int kind, const void* A, int planesA, const vo
   pl.p.err = err;
   make_map(&pl.p.tmA, kind, A, M * planesA, Kpad, NB, BM);
   make_map(&pl.p.tmB, kind, B, N * planesB, Kpad, NB, pl.bn);
+  pl.pair_maps = make_map_pair(&pl.p.tmA2, kind, A, M * planesA, Kpad, NB, BM) &&
+                 make_map_pair(&pl.p.tmB2, kind, B, N * planesB, Kpad, NB, pl.bn);
   // split K when the output has less than one wave of tiles and the K loop is long
   const long long tiles = ((M + BM - 1) / BM) * ((N + pl.bn - 1) / pl.bn) * NB * (pl.p.fused ? 1 : pl.p.nrb);
   const int nv = pl.p.nseg[0] * pl.p.nkb;
@@ -708,30 +855,49 @@ void tc_gemm_plan(TcGemmPlan& pl, int kind, const void* A, int planesA, const vo
   pl.splits = (nv + pl.p.vper - 1) / pl.p.vper;
   // an item whose K loop fits in one chunk accumulates once, in the double-buffered accumulators
   if (pl.p.chunk >= pl.p.vper) pl.p.chunk = 0;
+  // with chunks, the split parts' segments (planes are component x 2 + part, part 0 the high
+  // half) go first, in their given order, then the hi x hi ones (see chunk_of)
+  for (int rb = 0; rb < 2; ++rb) {
+    pl.p.nminor[rb] = 0;
+    if (pl.p.chunk == 0 || rb >= pl.p.nrb) continue;
+    RTCC_REQUIRE(planesA % 2 == 0 && planesB % 2 == 0, "chunked accumulation needs split operand planes");
+    TcSeg ordered[kMaxSeg];
+    int n = 0;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int q = 0; q < pl.p.nseg[rb]; ++q) {
+        const TcSeg& sgm = pl.p.seg[rb][q];
+        const bool major = sgm.pa % 2 == 0 && sgm.pb % 2 == 0;
+        if (major == (pass == 1)) ordered[n++] = sgm;
+      }
+    for (int q = 0; q < n; ++q) {
+      pl.p.seg[rb][q] = ordered[q];
+      if (!(ordered[q].pa % 2 == 0 && ordered[q].pb % 2 == 0)) pl.p.nminor[rb] = q + 1;
+    }
+  }
+  if (forced_variant >= 0) pl.variant = forced_variant;
+  if (pl.variant == 2 && !pl.pair_maps) pl.variant = 0;
+}
+
+template <int KIND>
+void launch_kind(const TcGemmPlan& p, cudaStream_t s) {
+  if (p.bn == 64) launch_inst<64, KIND, 7, 8>(p, s);
+  else if (p.bn == 128) {
+    if (p.variant == 2) launch_inst<128, KIND, 3, 4, 2>(p, s);
+    else if (p.variant == 1) launch_inst<128, KIND, 6, 4>(p, s);
+    else launch_inst<128, KIND, 5, 8>(p, s);
+  } else if (p.variant == 2) {
+    launch_inst<256, KIND, 2, 4, 2>(p, s);
+  } else if (p.variant == 1) {
+    launch_inst<256, KIND, 3, 8>(p, s);
+  } else {
+    launch_inst<256, KIND, 4, 4>(p, s);
+  }
 }
 
 void launch_tc_gemm(const TcGemmPlan& p, cudaStream_t s) {
-  if (p.kind == 0) {
-    if (p.bn == 64) launch_inst<64, 0, 7, 8>(p, s);
-    else if (p.bn == 128) {
-      if (p.variant == 1) launch_inst<128, 0, 6, 4>(p, s);
-      else launch_inst<128, 0, 5, 8>(p, s);
-    } else if (p.variant == 1) {
-      launch_inst<256, 0, 3, 8>(p, s);
-    } else {
-      launch_inst<256, 0, 4, 4>(p, s);
-    }
-  } else {
-    if (p.bn == 64) launch_inst<64, 1, 7, 8>(p, s);
-    else if (p.bn == 128) {
-      if (p.variant == 1) launch_inst<128, 1, 6, 4>(p, s);
-      else launch_inst<128, 1, 5, 8>(p, s);
-    } else if (p.variant == 1) {
-      launch_inst<256, 1, 3, 8>(p, s);
-    } else {
-      launch_inst<256, 1, 4, 4>(p, s);
-    }
-  }
+  RTCC_REQUIRE(p.variant != 2 || p.pair_maps, "two-K-block GEMM variant without its tensor maps");
+  if (p.kind == 0) launch_kind<0>(p, s);
+  else launch_kind<1>(p, s);
 }
 
 }  // namespace rtcc

@@ -944,6 +944,8 @@ struct rtcc_ctx {
   std::unique_ptr<AdjointEngine> adj;
   long long last_stats[4] = {0, 0, 0, 0};
   long long last_slot_attempts = 0;   // sum over attempts of the slots they ran (last rtcc_propagate)
+  void* out_stage = nullptr;          // device staging of host-side propagation outputs
+  size_t out_stage_bytes = 0;
   Profiler prof;
   ~rtcc_ctx() {
     adj.reset();
@@ -951,6 +953,7 @@ struct rtcc_ctx {
     E.reset();
     ints.reset();
     for (void* p : allocs) cudaFree(p);
+    if (out_stage) cudaFree(out_stage);
     if (stream) cudaStreamDestroy(stream);
   }
   template <class T>
@@ -1824,20 +1827,23 @@ rtcc_status_t rtcc_propagate(rtcc_handle_t h, const rtcc_field_t* fields, const 
     cudaStream_t s = h->stream;
     const int nz = h->nz;
     const bool dev_out = is_device_ptr(t_out);
-    // device staging of host outputs, released when the call returns (normally or by an error)
-    struct Staging {
-      void* p = nullptr;
-      ~Staging() {
-        if (p) cudaFree(p);
-      }
-    } st_t, st_mu;
+    // device staging of host outputs: one buffer on the handle, grown when a call needs more
     double* tout = t_out;
     double* muout = mu_out;
     if (!dev_out) {
-      st_t.p = dev_alloc(sizeof(double) * nz * max_out);
-      st_mu.p = dev_alloc(sizeof(double) * nz * max_out * 6);
-      tout = static_cast<double*>(st_t.p);
-      muout = static_cast<double*>(st_mu.p);
+      const size_t need = sizeof(double) * (size_t)nz * max_out * 7;
+      if (h->out_stage_bytes < need) {
+        if (h->out_stage) {
+          RTCC_CUDA(cudaStreamSynchronize(s));
+          cudaFree(h->out_stage);
+          h->out_stage = nullptr;
+          h->out_stage_bytes = 0;
+        }
+        h->out_stage = dev_alloc(need);
+        h->out_stage_bytes = need;
+      }
+      tout = static_cast<double*>(h->out_stage);
+      muout = tout + (size_t)nz * max_out;
       RTCC_CUDA(cudaMemsetAsync(tout, 0, sizeof(double) * nz * max_out, s));
       RTCC_CUDA(cudaMemsetAsync(muout, 0, sizeof(double) * nz * max_out * 6, s));
     }
