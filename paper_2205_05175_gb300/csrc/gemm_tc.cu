@@ -7,13 +7,16 @@
 //
 // Persistent, warp-specialised: one CTA per SM walks work items (batch, output plane or both
 // planes, split-K slice, 128 x BN tile in grouped order):
-//   warp 0 lane 0 : TMA producer (cp.async.bulk.tensor, 128-byte swizzle, mbarrier tx count)
+//   warp 0 lane 0 : TMA producer (cp.async.bulk.tensor, 128-byte swizzle, mbarrier tx count;
+//                   one K block per stage, or two through 4-D tensor maps)
 //   warp 1 lane 0 : MMA issuer (tcgen05.mma kind::tf32, or kind::f16 with bf16 inputs; the
 //                   instruction descriptor's negate-A bit gives -Ai Bi), tcgen05.commit
 //                   releases smem stages and hands a finished accumulator to the epilogue
 //   warps 2..     : epilogue (tcgen05.ld 32x32b over the warp's TMEM lane quarter, batched
 //                   read-modify-write of C, shared-memory transpose when C is unit-stride in n);
-//                   four warps, or eight that split the tile's columns for narrow tiles
+//                   four warps, or eight that split the tile's columns
+// In the split precision modes the MMAs accumulate bounded chunks of the K loop in TMEM slots and
+// the epilogue folds them into the tile's sum with round-to-nearest float32 adds (see chunk_of).
 // Two TMEM accumulator sets overlap the epilogue of one tile with the main loop of the next.
 // When the K loop is short the epilogue dominates, so one item then covers both planes of a
 // complex output and writes whole 16-byte elements once.  Every mbarrier wait is bounded (2 s
