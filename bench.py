@@ -693,7 +693,6 @@ def run_gpu(args, rank, world, local):
     H = rtcc.Handle(f, B, mu, o, v, ntraj=nz, prec=prec)
     ecorr, mu0 = H.ground_state(tol=args.gs_tol, maxiter=300)
     t_setup = time.perf_counter() - t_setup
-    y0 = np.stack([H.get_state(z)[0] for z in range(nz)])
     integ = rtcc.make_integrator(rtcc.CK, h=0.01, tol=1e-6, nsteps=args.warmup)
     max_out = args.steps + args.warmup + 2
     tout = torch.zeros((nz, max_out), dtype=torch.float64, device="cuda")
@@ -701,6 +700,8 @@ def run_gpu(args, rank, world, local):
     # warm-up: W accepted steps per trajectory (continues from the ground state)
     H.propagate(fields, integ, max_out, tout, mout)
     torch.cuda.synchronize()
+    # the states and times where the timed segment starts: the end-to-end run below replays it
+    snap = None if args.skip_e2e else [H.get_state(z)[:2] for z in range(nz)]
     # timed region: K accepted Cash-Karp steps of every trajectory, every launch timed by CUDA events
     integ = rtcc.make_integrator(rtcc.CK, h=0.01, tol=1e-6, nsteps=args.steps)
     barrier(world)
@@ -753,8 +754,12 @@ def run_gpu(args, rank, world, local):
     if args.skip_e2e:
         acc_e2e, ms_e2e, h2d, d2h = acc, ms_max, 0.0, 0.0
     else:
-        # end to end: initial states from pinned host memory, dipoles back to the host, inside the timed region
-        yh = torch.from_numpy(y0.view(np.float64).copy()).pin_memory()
+        # end to end: the same segment again (same start states and times, same steps), with the
+        # start states copied in from pinned host memory and the dipoles copied back to the host
+        # inside the timed region
+        yh = torch.from_numpy(np.stack([sn[0] for sn in snap]).view(np.float64)).pin_memory()
+        tz = [sn[1] for sn in snap]
+        snap = None
         th = np.zeros((nz, max_out))
         mh = np.zeros((nz, max_out, 3), complex)
         torch.cuda.synchronize()
@@ -762,7 +767,7 @@ def run_gpu(args, rank, world, local):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for z in range(nz):
-            H.set_state(z, yh[z].numpy().view(np.complex128), 0.0, 0.0)
+            H.set_state(z, yh[z].numpy().view(np.complex128), tz[z], 0.0)
         H.propagate(fields, integ, max_out, th, mh)
         e1.record()
         torch.cuda.synchronize()
