@@ -145,6 +145,26 @@ def test_gauss_legendre_newton_beyond_the_fixed_point_limit_matches_oracle():
         assert e.value.status == "INVALID_ARG"
 
 
+def test_gauss_legendre_newton_trajectories_solve_independent_systems():
+    """Two trajectories with different fields in one handle: every Krylov inner product, rotation
+    and back substitution is per trajectory, so each equals the same trajectory run alone."""
+    from paper_2205_05175_gb300 import rtcc
+    o, v = 1, 4
+    f, B, mu = system(o, v)
+    s = rk.RTCC(f, B, mu, o)
+    y0, _, _ = s.ground_state(tol=1e-11)
+    fields = [rtcc.make_field(E0=0.05, t0=0.5), rtcc.make_field(E0=0.5, omega=0.9, t0=0.3, pol=(1.0, 0.0, 0.0))]
+    # the strong field needs more simplified-Newton iterations than the default six (the Jacobian
+    # is frozen at the step's start): twelve bring h max|dK_2| to ~1e-16 at this step
+    integ = rtcc.make_integrator(rtcc.GL2_NEWTON, h=0.4, nsteps=3, tol=1e-10, sweeps=12)
+    _, mb, nb, _ = _gpu_traj(o, v, f, B, mu, fields, integ, 8, prec=0, y0=y0)
+    for z in range(2):
+        _, m1, n1, _ = _gpu_traj(o, v, f, B, mu, [fields[z]], integ, 8, prec=0, y0=y0)
+        assert nb[z] == n1[0] == 4
+        assert np.abs(mb[z, :4] - m1[0, :4]).max() < 1e-12
+    assert np.abs(mb[0, :4] - mb[1, :4]).max() > 1e-4
+
+
 @pytest.mark.last
 def test_gauss_legendre_newton_at_o2_v6_matches_the_stored_oracle_record():
     """o = 2, v = 6, h = 0.4 (the sweeps diverge there): the device's Newton-Krylov steps against the
